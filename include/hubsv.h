@@ -1,0 +1,218 @@
+/*
+ * hubsv.h -- C ABI of the GB300 statevector engine for Hubbard-model VQE.
+ *
+ * The library applies the layered Hamiltonian variational ansatz (HVA) of
+ * Eq. 7 (the PQC of Eq. 3) to a dense 2^n amplitude vector of the
+ * Jordan-Wigner-mapped Fermi-Hubbard model (Eqs. 1, 2, 15, 16; one qubit per
+ * spin-orbital, Sec. 2.2.1), and evaluates the energy of Eq. 4 and its
+ * parameter gradient by the adjoint recursion of Sec. 2.1.  n <= 32 qubits.
+ *
+ * Conventions (fixed here because the paper leaves them open):
+ *  - Qubit k of the amplitude index x is fermionic mode k.  a_k|x> =
+ *    (-1)^popcount(x & (2^k - 1)) |x ^ 2^k> for occupied k; |x> = a+_{k1}
+ *    a+_{k2}..|vac> with k1 < k2 < ...  The site -> mode maps are inputs
+ *    (default: up spin of site i on mode i, down spin on mode L + i).
+ *  - H = -sum_sigma sum_{i != j} t_ij a+_{i sigma} a_{j sigma}
+ *        - sum_{i,sigma} t_ii n_{i sigma} + sum_i U_i n_{i up} n_{i dn}
+ *        + sum_{i<j} V_ij n_i n_j,            n_i = n_{i up} + n_{i dn}.
+ *    The hopping sum runs over both orders of each pair; the diagonal of t is
+ *    the on-site potential of Eq. 15; each V pair is counted once.
+ *  - Each ansatz group g applies U_g = exp(-i theta_p G_g) (the sign of the
+ *    exponent is read as -i; Eq. 7 writes +i, which mirrors the landscape).
+ *    G_g is the group's Hamiltonian terms with coefficients and signs:
+ *      HUB_G_HOP     -sum_{(i,j) in terms} t_ij sum_sigma (a+_i a_j + h.c.)
+ *      HUB_G_ONSITE  sum_{i in terms} U_i n_{i up} n_{i dn}
+ *      HUB_G_NN_V    sum_{(i,j) in terms} V_ij n_i n_j
+ *      HUB_G_POT     -sum_{i in terms} t_ii (n_{i up} + n_{i dn})
+ *      HUB_G_RZ      sum_{k in terms} (1/2 - n_k)  (= Z_k / 2, modes k)
+ *    The terms of one group must commute: hop bonds of a group touch
+ *    disjoint sites.
+ *  - Gradient: dE/dtheta_p = sum over groups g with parameter p of
+ *    2 Im <lambda_g| G_g |psi_g>, psi_g the state after group g and
+ *    lambda_g = U_{g+1}^+ ... U_K^+ H psi_K (Sec. 2.1, standard form of the
+ *    recursion).
+ *
+ * Memory and streams: the caller owns every amplitude, parameter and output
+ * buffer (device pointers unless stated).  The library owns its handles and
+ * small device tables (gate lists, coefficient tables, Slater-determinant
+ * tables, reduction scratch), which the destroy calls free.  Compute calls
+ * are asynchronous on the given stream and never synchronise the device;
+ * host-side argument checks return an error status before anything is
+ * launched.  Launch errors are reported by the call; errors raised later by
+ * the device are reported by the next call or by hub_sync.  The library
+ * never aborts and never prints.  Amplitudes: HUB_C64 = interleaved float
+ * (re, im), HUB_C128 = interleaved double; batch b occupies amplitudes
+ * [b * 2^n, (b+1) * 2^n).  theta, energies and gradients are double in both
+ * precisions; reductions accumulate in double.
+ */
+#ifndef HUBSV_H
+#define HUBSV_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HUB_API __attribute__((visibility("default")))
+#else
+#define HUB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hub_model* hub_t;
+typedef struct hub_ansatz* ans_t;
+typedef struct CUstream_st* hub_stream_t;   /* == cudaStream_t; NULL = default */
+
+typedef enum {
+  HUB_OK = 0,
+  HUB_EINVAL = 1,        /* bad argument: null pointer, size, index, group */
+  HUB_EUNSUPPORTED = 2,  /* valid but outside what this build supports     */
+  HUB_ENOMEM = 3,        /* a library-owned allocation failed              */
+  HUB_ECUDA = 4,         /* a CUDA call or kernel launch failed            */
+  HUB_ETIMEOUT = 5       /* a bounded device wait ran out                  */
+} hub_status;
+
+typedef enum { HUB_C64 = 0, HUB_C128 = 1 } hub_dtype;
+
+typedef enum {
+  HUB_G_HOP = 0, HUB_G_ONSITE = 1, HUB_G_NN_V = 2, HUB_G_POT = 3, HUB_G_RZ = 4
+} hub_gkind;
+
+typedef enum { HUB_PREP_SLATER = 0, HUB_PREP_NEEL = 1 } hub_prep;
+
+/* Flags of energy / energy_grad. */
+#define HUB_FLAG_PREP_FUSED 1u   /* psi is workspace: the initial state is the
+                                    one set by the last state_prepare call
+                                    and is generated inside the first sweep   */
+#define HUB_FLAG_KEEP_STATE 2u   /* energy: leave the final state psi_K in psi */
+
+/* Lattice: sites 0..n_sites-1, undirected bonds (pairs of sites).  mode_up /
+ * mode_dn map a site to its two qubits; both NULL = blocked order (up i -> i,
+ * dn i -> n_sites + i).  Every mode in [0, 2 n_sites) must be used once.  */
+typedef struct {
+  int32_t n_sites;
+  int32_t n_bonds;
+  const int32_t* bonds;     /* [n_bonds][2], host */
+  const int32_t* mode_up;   /* [n_sites] or NULL, host */
+  const int32_t* mode_dn;   /* [n_sites] or NULL, host */
+} hub_lattice;
+
+/* One ansatz group (one factor of Eq. 7).  terms (host): bond indices of the
+ * lattice for HOP and NN_V, site indices for ONSITE and POT, mode indices for
+ * RZ.  param indexes theta; groups may share a parameter.                    */
+typedef struct {
+  int32_t kind;             /* hub_gkind */
+  int32_t n_terms;
+  const int32_t* terms;
+  int32_t param;
+} hub_group;
+
+/* Open nx x ny square lattice (Sec. 3: open boundary conditions) and its HVA
+ * bond classes (Eq. 7).  Rows x = 0..nx-1, columns y = 0..ny-1; site number
+ * x*ny + y (order 0, row-major as in Sec. 2.2.1) or with odd rows reversed
+ * (order 1, "snake").  Bonds: all horizontal bonds in row order, then all
+ * vertical ones; each stored with the smaller site first.  bond_class (may be
+ * NULL): 0 = h1 (horizontal, even y), 1 = h2 (horizontal, odd y), 2 = v1
+ * (vertical, even x), 3 = v2 (vertical, odd x).  bonds must hold
+ * 2 * (nx*(ny-1) + ny*(nx-1)) ints; *n_bonds receives the count.            */
+HUB_API hub_status hub_square_lattice(int32_t nx, int32_t ny, int32_t order,
+                              int32_t* bonds, int32_t* bond_class,
+                              int32_t* n_bonds);
+
+/* Hamiltonian (Eqs. 1, 2, 15, 16).  t_ij: [L*L] host, symmetric, t_ij != 0
+ * only on lattice bonds off the diagonal; its diagonal is the on-site
+ * potential.  U_i: [L] host or NULL (= 0).  V_ij: [L*L] host or NULL,
+ * symmetric, nonzero only on bonds.  n_up, n_dn: particle numbers of the
+ * sector.  Requires 2 <= 2L <= 32.                                            */
+HUB_API hub_status hub_create(const hub_lattice* lat, const double* t_ij,
+                      const double* U_i, const double* V_ij,
+                      int32_t n_up, int32_t n_dn, hub_t* out);
+HUB_API void hub_destroy(hub_t model);
+
+/* Ansatz: n_layers * groups_per_layer groups applied in array order.
+ * ans_create takes one model; ans_create_multi takes several instances that
+ * share lattice, mode maps and particle numbers; they may
+ * differ in t, U, V.  Batch element b of every compute call uses instance
+ * b % n_models.  The ansatz keeps pointers to the models, which must
+ * outlive it.                                                               */
+HUB_API hub_status ans_create(hub_t model, int32_t n_layers, int32_t groups_per_layer,
+                      const hub_group* groups, ans_t* out);
+HUB_API hub_status ans_create_multi(const hub_t* models, int32_t n_models,
+                            int32_t n_layers, int32_t groups_per_layer,
+                            const hub_group* groups, ans_t* out);
+HUB_API void ans_destroy(ans_t ans);
+HUB_API int32_t ans_num_params(ans_t ans);   /* -1 for a NULL handle */
+HUB_API int32_t ans_num_qubits(ans_t ans);   /* -1 for a NULL handle */
+
+/* Initial state |psi_0>.  HUB_PREP_SLATER: the U = 0 Slater determinant of
+ * each instance: the lowest n_up / n_dn eigenvectors Phi of h = -t + P
+ * (P = orb_perturb, [L*L] host symmetric, or NULL), FP64, each eigenvector's
+ * largest-magnitude entry (lowest index on a tie) made positive; psi_0 =
+ * prod_m b+_{m,up} prod_m b+_{m,dn} |vac>, b+_m = sum_i Phi_im a+_{mode(i)},
+ * i.e. det(Phi_up[occ_up]) det(Phi_dn[occ_dn]) times the sign of ordering
+ * the creators by mode.  HUB_PREP_NEEL: the checkerboard state of Sec. 2.1,
+ * up on site i when neel_up[i] != 0 (host [L]) and down otherwise.
+ * Writes batch * 2^n amplitudes to psi (may be NULL: only the tables used by
+ * HUB_FLAG_PREP_FUSED are set).                                               */
+HUB_API hub_status state_prepare(ans_t ans, int32_t kind, const double* orb_perturb,
+                         const int32_t* neel_up, void* psi, int32_t dtype,
+                         int64_t batch, hub_stream_t stream);
+
+/* Energy E(theta) = <psi|H|psi> of Eq. 4 for each batch element.
+ * theta: device double [batch][P].  psi: device [batch][2^n] amplitudes; on
+ * entry the initial state (unless HUB_FLAG_PREP_FUSED), on return clobbered.
+ * E: device double [batch].  The sum over H's terms is fused into the last
+ * sweeps; H|psi> is never written.                                          */
+HUB_API hub_status energy(ans_t ans, const double* theta, void* psi, double* E,
+                  int32_t dtype, int64_t batch, uint32_t flags,
+                  hub_stream_t stream);
+
+/* Energy and adjoint gradient (Sec. 2.1).  lam: device workspace of the same
+ * size as psi.  ckpt: NULL, or device workspace of the same size as psi for
+ * one mid-circuit checkpoint of psi (bounds the rounding drift of the
+ * backward un-computation).  grad: device double [batch][P], overwritten.
+ * psi and lam are clobbered.                                                */
+HUB_API hub_status energy_grad(ans_t ans, const double* theta, void* psi, void* lam,
+                       void* ckpt, double* E, double* grad, int32_t dtype,
+                       int64_t batch, uint32_t flags, hub_stream_t stream);
+
+/* lam = H psi for each batch element (Eq. 4's operator; used by tests and
+ * by callers that need the residual).  psi is read only.                    */
+HUB_API hub_status hub_apply_h(ans_t ans, const void* psi, void* lam, int32_t dtype,
+                       int64_t batch, hub_stream_t stream);
+
+/* Plan statistics for the last-planned configuration of a call kind (0 =
+ * energy, 1 = energy_grad): number of sweeps and HBM bytes moved per batch
+ * element (reads + writes of amplitude vectors).                            */
+HUB_API hub_status ans_plan_stats(ans_t ans, int32_t which, int32_t dtype,
+                          uint32_t flags, int32_t* n_sweeps,
+                          double* bytes_per_state);
+
+/* Schedule of a call kind (0 energy, 1 energy_grad, 2 apply_h) for checking
+ * by tests: buf receives [n_sweeps, then per sweep: tile-bit mask, sweep
+ * flags, n_ops, the sequence index of each op in execution order].  The
+ * sequence is: the ansatz factors in order (one per hop term and spin, one
+ * per diagonal group); then the H terms (one per bond and spin, bonds in
+ * lattice order, up before down) and H's diagonal; then (energy_grad) for
+ * each factor in reverse order its gradient step followed by its inverse.
+ * With buf == NULL only *len is set.                                        */
+HUB_API hub_status ans_plan_describe(ans_t ans, int32_t which, int32_t dtype,
+                                     uint32_t flags, int64_t* buf, int32_t cap,
+                                     int32_t* len);
+
+/* Tile size override (log2 amplitudes per tile; 0 = automatic).  Used by the
+ * autotuner.                                                                */
+HUB_API hub_status ans_set_tile(ans_t ans, int32_t dtype, int32_t log2_tile);
+
+/* Wait for the stream and report any asynchronous device error.            */
+HUB_API hub_status hub_sync(hub_stream_t stream);
+
+/* Message of the last error on the calling thread ("" if none).             */
+HUB_API const char* hub_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HUBSV_H */

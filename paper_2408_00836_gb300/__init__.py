@@ -1,0 +1,277 @@
+"""GB300 statevector engine for Hubbard-model VQE (arxiv 2408.00836).
+
+Python face of libhubsv.so: the C ABI of include/hubsv.h with the same names,
+PyTorch used only for device memory and streams.  Every amplitude operation
+runs in the sm_103a kernels; there is no CPU or PyTorch fallback.
+
+Main entry points (all take and return torch CUDA tensors):
+
+* ``square_lattice(nx, ny, order)`` -- open grid bonds and HVA bond classes.
+* ``Model`` -- the Hamiltonian of Eqs. 1, 2, 15, 16 (``hub_create``).
+* ``Ansatz`` -- the layered HVA of Eq. 7 (``ans_create``) with
+  ``state_prepare``, ``energy``, ``energy_grad`` and ``apply_h``.
+* ``energy_fn`` -- ``torch.autograd`` function whose backward is the adjoint
+  gradient of Sec. 2.1.
+"""
+
+from __future__ import annotations
+
+import ctypes
+from typing import Sequence
+
+import numpy as np
+
+from ._lib import HubError, HubGroup, HubLattice, check, lib  # noqa: F401
+from . import workloads  # noqa: F401
+
+C64, C128 = 0, 1
+HOP, ONSITE, NN_V, POT, RZ = 0, 1, 2, 3, 4
+PREP_SLATER, PREP_NEEL = 0, 1
+FLAG_PREP_FUSED = 1
+FLAG_KEEP_STATE = 2
+CLASS_IDS = {"h1": 0, "h2": 1, "v1": 2, "v2": 3, "even": 0, "odd": 1}
+
+
+def _i32(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _f64(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def square_lattice(nx: int, ny: int, order: str = "rowmajor"):
+    """Open nx x ny grid: (bonds [(i, j)], classes ['h1'|'h2'|'v1'|'v2'])."""
+    o = {"rowmajor": 0, "snake": 1}[order]
+    nb = ctypes.c_int32(0)
+    check(lib().hub_square_lattice(nx, ny, o, None, None, ctypes.byref(nb)))
+    b = np.zeros(2 * nb.value, dtype=np.int32)
+    c = np.zeros(nb.value, dtype=np.int32)
+    check(lib().hub_square_lattice(nx, ny, o, b.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(nb)))
+    names = ["h1", "h2", "v1", "v2"]
+    return [(int(b[2 * i]), int(b[2 * i + 1])) for i in range(nb.value)], [names[k] for k in c]
+
+
+class Model:
+    """Hubbard Hamiltonian handle (``hub_create``)."""
+
+    def __init__(self, n_sites: int, bonds, t, U=None, V=None, n_up=None, n_dn=None,
+                 modes="blocked"):
+        L = n_sites
+        self.n_sites = L
+        self.bonds = [tuple(b) for b in bonds]
+        bnd, bp = _i32(np.array(self.bonds, dtype=np.int32).reshape(-1))
+        keep = [bnd]
+        if isinstance(modes, str):
+            if modes == "blocked":
+                up = dn = None
+            elif modes == "interleaved":
+                up, dn = np.arange(L) * 2, np.arange(L) * 2 + 1
+            else:
+                raise ValueError(modes)
+        else:
+            up, dn = modes
+        lat = HubLattice(L, len(self.bonds), bp, None, None)
+        if up is not None:
+            ua, upp = _i32(up)
+            da, dpp = _i32(dn)
+            keep += [ua, da]
+            lat.mode_up, lat.mode_dn = upp, dpp
+        ta, tp = _f64(np.asarray(t, dtype=np.float64).reshape(L, L))
+        Ua, Up = _f64(U) if U is not None else (None, None)
+        Va, Vp = _f64(np.asarray(V).reshape(L, L)) if V is not None else (None, None)
+        self.n_up = L // 2 if n_up is None else n_up
+        self.n_dn = L // 2 if n_dn is None else n_dn
+        h = ctypes.c_void_p()
+        check(lib().hub_create(ctypes.byref(lat), tp, Up, Vp, self.n_up, self.n_dn, ctypes.byref(h)))
+        self._h = h
+        del keep, ta, Ua, Va
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and h.value and _lib_loaded():
+            lib().hub_destroy(h)
+            self._h = None
+
+
+def _lib_loaded():
+    from . import _lib as m
+    return m._lib is not None
+
+
+def hva_groups(bonds, classes, n_sites: int, n_layers: int, layer: Sequence[str]):
+    """Groups of a layered HVA in application order (Eq. 7): one parameter per
+    entry of ``layer`` ('U', 'V', 'pot' or a bond class), index l*len + g."""
+    out = []
+    G = len(layer)
+    for l in range(n_layers):
+        for g, name in enumerate(layer):
+            p = l * G + g
+            if name == "U":
+                out.append((ONSITE, list(range(n_sites)), p))
+            elif name == "V":
+                out.append((NN_V, list(range(len(bonds))), p))
+            elif name == "pot":
+                out.append((POT, list(range(n_sites)), p))
+            else:
+                cid = CLASS_IDS[name]
+                terms = [i for i, c in enumerate(classes) if CLASS_IDS[c] == cid]
+                out.append((HOP, terms, p))
+    return out
+
+
+def _ptr(t, nbytes: int, what: str):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if t.numel() * t.element_size() < nbytes:
+        raise ValueError(f"{what} holds {t.numel() * t.element_size()} bytes, needs {nbytes}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Ansatz:
+    """Layered HVA handle (``ans_create`` / ``ans_create_multi``)."""
+
+    def __init__(self, models, groups, n_layers: int = 1):
+        if isinstance(models, Model):
+            models = [models]
+        self.models = list(models)
+        self.groups = list(groups)
+        arrs = []
+        garr = (HubGroup * max(1, len(self.groups)))()
+        for i, (kind, terms, param) in enumerate(self.groups):
+            a, p = _i32(terms if len(terms) else [0])
+            arrs.append(a)
+            garr[i] = HubGroup(kind, len(terms), p, param)
+        G = len(self.groups)
+        if G % n_layers:
+            raise ValueError("number of groups must be a multiple of n_layers")
+        h = ctypes.c_void_p()
+        hs = (ctypes.c_void_p * len(self.models))(*[m.handle.value for m in self.models])
+        check(lib().ans_create_multi(hs, len(self.models), n_layers, G // n_layers, garr, ctypes.byref(h)))
+        self._h = h
+        del arrs
+        self.P = lib().ans_num_params(h)
+        self.n = lib().ans_num_qubits(h)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and h.value and _lib_loaded():
+            lib().ans_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def amp_bytes(self, dtype: int) -> int:
+        return (8 if dtype == C64 else 16) << self.n
+
+    def state_prepare(self, kind=PREP_SLATER, orb_perturb=None, neel_up=None, psi=None,
+                      dtype=C64, batch: int = 1, stream=None):
+        pa, pp = _f64(orb_perturb) if orb_perturb is not None else (None, None)
+        na, npp = _i32(neel_up) if neel_up is not None else (None, None)
+        ptr = _ptr(psi, batch * self.amp_bytes(dtype), "psi")
+        check(lib().state_prepare(self._h, kind, pp, npp, ptr, dtype, batch, _stream(stream)))
+        del pa, na
+
+    def energy(self, theta, psi, E, dtype=C64, batch: int = 1, fused: bool = True,
+               keep_state: bool = False, stream=None):
+        flags = (FLAG_PREP_FUSED if fused else 0) | (FLAG_KEEP_STATE if keep_state else 0)
+        check(lib().energy(self._h, _ptr(theta, 8 * batch * self.P, "theta"),
+                           _ptr(psi, batch * self.amp_bytes(dtype), "psi"), _ptr(E, 8 * batch, "E"),
+                           dtype, batch, flags, _stream(stream)))
+        return E
+
+    def energy_grad(self, theta, psi, lam, E, grad, ckpt=None, dtype=C64, batch: int = 1,
+                    fused: bool = True, stream=None):
+        nb = batch * self.amp_bytes(dtype)
+        check(lib().energy_grad(self._h, _ptr(theta, 8 * batch * self.P, "theta"), _ptr(psi, nb, "psi"),
+                                _ptr(lam, nb, "lam"), _ptr(ckpt, nb, "ckpt"), _ptr(E, 8 * batch, "E"),
+                                _ptr(grad, 8 * batch * self.P, "grad"), dtype, batch,
+                                FLAG_PREP_FUSED if fused else 0, _stream(stream)))
+        return E, grad
+
+    def apply_h(self, psi, lam, dtype=C64, batch: int = 1, stream=None):
+        nb = batch * self.amp_bytes(dtype)
+        check(lib().hub_apply_h(self._h, _ptr(psi, nb, "psi"), _ptr(lam, nb, "lam"), dtype, batch,
+                                _stream(stream)))
+        return lam
+
+    def plan_stats(self, which: int, dtype=C64, fused: bool = True):
+        ns = ctypes.c_int32(0)
+        by = ctypes.c_double(0.0)
+        check(lib().ans_plan_stats(self._h, which, dtype, FLAG_PREP_FUSED if fused else 0,
+                                   ctypes.byref(ns), ctypes.byref(by)))
+        return ns.value, by.value
+
+    def plan_describe(self, which: int, dtype=C64, flags: int = FLAG_PREP_FUSED):
+        """[(tile_mask, sweep_flags, [sequence indices])] of a call kind."""
+        n = ctypes.c_int32(0)
+        check(lib().ans_plan_describe(self._h, which, dtype, flags, None, 0, ctypes.byref(n)))
+        buf = (ctypes.c_int64 * n.value)()
+        check(lib().ans_plan_describe(self._h, which, dtype, flags, buf, n.value, ctypes.byref(n)))
+        v = list(buf)
+        out, i = [], 1
+        for _ in range(v[0]):
+            tile, fl, cnt = v[i], v[i + 1], v[i + 2]
+            out.append((tile, fl, v[i + 3:i + 3 + cnt]))
+            i += 3 + cnt
+        return out
+
+    def set_tile(self, dtype: int, log2_tile: int):
+        check(lib().ans_set_tile(self._h, dtype, log2_tile))
+
+
+def sync(stream=None):
+    check(lib().hub_sync(_stream(stream)))
+
+
+def empty_state(n_qubits: int, dtype=C64, batch: int = 1, device="cuda"):
+    import torch
+    td = torch.complex64 if dtype == C64 else torch.complex128
+    return torch.empty((batch, 1 << n_qubits), dtype=td, device=device)
+
+
+class _EnergyFn:
+    """Builds the torch.autograd.Function lazily (torch imported on use)."""
+    fn = None
+
+
+def energy_fn(ans: Ansatz, theta, psi, lam, dtype=C64, batch: int = 1, ckpt=None):
+    """E(theta) with autograd: forward runs energy_grad (the adjoint pass of
+    Sec. 2.1) and keeps the gradient; backward scales it by dL/dE."""
+    import torch
+    if _EnergyFn.fn is None:
+        class EnergyFunction(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, th, a, ps, lm, dt, bt, ck):
+                E = torch.empty(bt, dtype=torch.float64, device=th.device)
+                g = torch.empty(bt, a.P, dtype=torch.float64, device=th.device)
+                a.energy_grad(th.detach().contiguous(), ps, lm, E, g, ckpt=ck, dtype=dt, batch=bt)
+                ctx.save_for_backward(g)
+                return E
+
+            @staticmethod
+            def backward(ctx, gE):
+                (g,) = ctx.saved_tensors
+                return gE[:, None] * g, None, None, None, None, None, None
+        _EnergyFn.fn = EnergyFunction
+    return _EnergyFn.fn.apply(theta, ans, psi, lam, dtype, batch, ckpt)

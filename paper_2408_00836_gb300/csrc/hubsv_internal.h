@@ -1,0 +1,136 @@
+// Internal data structures shared by the host planner (hubsv_host.cpp) and
+// the sm_103a kernels (hubsv_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hubsv {
+
+constexpr int kMaxQubits = 32;
+constexpr int kMaxTileBits = 14;
+constexpr int kThreads = 256;
+
+// One operation applied to a tile.  Operations are the factors of the ansatz
+// (Eq. 7), the terms of H (Eqs. 1, 2, 15, 16) and the adjoint steps of
+// Sec. 2.1, each restricted to what one tile holds.
+enum OpKind : uint8_t {
+  OP_GIV = 0,        // Givens factor exp(-i theta G_term) of one hop term
+  OP_DIAG = 1,       // diagonal factor exp(-i theta G_diag)
+  OP_MEAS_HOP = 2,   // E += <psi| h_term |psi>
+  OP_MEAS_DIAG = 3,  // E += sum_x D(x) |psi_x|^2, N += |psi_x|^2
+  OP_LAM_HOP = 4,    // lam += h_term psi, E += <psi| h_term |psi>
+  OP_LAM_DIAG = 5,   // lam += D psi, E += ..., N += ...
+  OP_GRAD_HOP = 6,   // acc[slot] += 2 Im <lam| G_term |psi>
+  OP_GRAD_DIAG = 7,  // acc[slot] += 2 Im <lam| G_diag |psi>
+};
+
+enum OpFlag : uint8_t {
+  OPF_INV = 1,   // apply the inverse factor
+  OPF_LAM = 2,   // apply the factor to lam as well as psi
+};
+
+struct OpDev {
+  uint8_t kind, flags, p, q;    // p < q: tile-local bit positions (hop ops)
+  uint32_t bmask_local;         // Jordan-Wigner string on tile-local bits
+  uint64_t bmask_global;        // Jordan-Wigner string on non-tile bits
+  int32_t gate;                 // OP_GIV: coefficient-table column
+  int32_t hterm;                // hop ops: column of the -t table (per instance)
+  int32_t slot;                 // OP_GRAD_*: accumulator slot (parameter)
+  int32_t diag;                 // diagonal ops: index into the DiagOp array
+};
+
+// A diagonal operator d(x) = sum_bytes X[byte of x] + sum_bytes Y[byte of y]
+//                            + sum_bonds v_b n_i n_j,
+// with y = x & (x >> s) & upmask (bit up(i) of y set iff site i is doubly
+// occupied).  Real values (per instance) are used for energies and
+// gradients; phase tables exp(-i theta d) are generated per batch element.
+struct DiagOpDev {
+  int32_t has_x, has_y;          // number of x / y byte tables in use (0..4)
+  int32_t n_vb;                  // bonds with V terms
+  int32_t v_uniform;             // 1: all v_b equal -> phase from K = sum n_i n_j
+  int32_t real_off;              // offset of the real tables (per instance)
+  int32_t phase_off;             // offset of the phase tables (per batch elem)
+  int32_t param;                 // theta column for phases; -1 for H's diagonal
+  int32_t vb_up[64];             // up-mode of bond end i
+  int32_t vb_up2[64];            // up-mode of bond end j
+};
+// Real table layout at real_off: [4][256] X, [4][256] Y, [n_vb] v_b.
+// Phase table layout at phase_off: [4][256] X, [4][256] Y, then either
+// [4*n_vb+1] K-table (v_uniform) or [n_vb][5] per-bond powers.
+
+enum SweepFlag : uint32_t {
+  SW_PREP = 1u,        // generate psi_0 instead of reading psi
+  SW_READ_PSI = 2u,
+  SW_WRITE_PSI = 4u,
+  SW_HAS_LAM = 8u,     // the tile carries lam
+  SW_READ_LAM = 16u,   // else lam starts at zero in the tile
+  SW_WRITE_LAM = 32u,
+  SW_CKPT_WRITE = 64u, // also store psi to the checkpoint buffer
+  SW_CKPT_READ = 128u, // read psi from the checkpoint buffer
+};
+
+struct SweepDev {
+  int32_t op_begin, op_end;
+  int32_t k;                      // log2 tile size
+  int32_t c;                      // low contiguous bits (tile bits 0..c-1)
+  int32_t h1;                     // bits in the first offset table
+  uint32_t flags;
+  int8_t tbits[kMaxTileBits];     // tile bit positions, ascending
+  int8_t nbits[kMaxQubits];       // non-tile bit positions, ascending
+  int32_t n_nontile;
+};
+
+struct PrepDev {
+  int32_t kind;            // 0 Slater, 1 Neel
+  int32_t L, s;            // sites, dn-mode offset (dn(i) = up(i) + s)
+  int32_t layout;          // 0 blocked (s == L), 1 interleaved (s == 1)
+  uint64_t neel_x0;
+  const double* sd;        // [n_inst][2][2^L] determinant tables
+};
+
+struct KernelArgs {
+  void* psi;
+  void* lam;
+  void* ckpt;
+  const OpDev* ops;
+  const DiagOpDev* diag_ops;
+  const double* theta;
+  int32_t P;                       // parameters per batch element
+  const void* coef;                // [batch][n_gates] (cos, sin), R2
+  int32_t n_gates;
+  const double* hcoef;             // [n_inst][n_hterms]: -t of each hop term
+  int32_t n_hterms;
+  const double* real_tabs;         // [n_inst][real_stride]
+  int32_t real_stride;
+  const void* phase_tabs;          // [batch][phase_stride] R2
+  int32_t phase_stride;
+  int32_t n_inst;
+  int32_t n;                       // qubits
+  int32_t s;                       // dn-mode offset
+  uint64_t upmask;
+  int64_t batch;
+  uint64_t n_tiles;
+  double* acc;                     // [batch][n_slots]
+  int32_t n_slots;
+  int32_t slot_E, slot_N;
+  PrepDev prep;
+};
+
+}  // namespace hubsv
+
+// Launchers implemented in hubsv_kernels.cu (C++ linkage, internal).
+namespace hubsv {
+cudaError_t launch_sweep(int dtype, const SweepDev& sw, const KernelArgs& a,
+                         int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_coef(int dtype, const double* theta, int P, const int32_t* gate_param,
+                        const double* gate_t, int n_gates, void* coef,
+                        const int32_t* tab_param, const double* tab_val,
+                        int n_tab, int n_inst_tab, void* phase_tabs,
+                        int64_t batch, int n_inst, cudaStream_t st);
+cudaError_t launch_zero(double* p, int64_t n, cudaStream_t st);
+cudaError_t launch_finalize(const double* acc, int n_slots, int P, int slot_E,
+                            double* E, double* grad, int64_t batch, cudaStream_t st);
+int sweep_max_smem_optin();
+cudaError_t sweep_set_smem(int dtype, int nv, size_t smem);
+int device_sm_count();
+}  // namespace hubsv

@@ -1,0 +1,72 @@
+"""Shared test helpers: build the same problem on the CUDA path and in the
+oracle from the same seeded inputs, and compare results.
+
+Tolerances (relative to the scale of the quantity):
+  energies     c128 1e-10, c64 1e-6   (the stated parity targets)
+  gradients    c128 1e-10, c64 1e-6   (relative to max(1, |grad|_inf))
+  state        c128 1e-10, c64 1e-6   (relative L2 error of the vector)
+"""
+
+import numpy as np
+
+import oracle as O
+import paper_2408_00836_gb300 as H
+
+TOL = {H.C128: 1e-10, H.C64: 1e-6}
+
+
+class Problem:
+    def __init__(self, nx, ny, order="rowmajor", modes="blocked", t=None, U=None, V=None,
+                 n_up=None, n_dn=None, layers=2, classes=("U", "h1", "v1", "h2", "v2"),
+                 perturb=None, instances=None):
+        import torch  # noqa: F401  (CUDA side only)
+        self.nx, self.ny, self.L = nx, ny, nx * ny
+        self.bonds, self.cls = H.square_lattice(nx, ny, order)
+        self.lat = O.square_lattice(nx, ny, order)
+        L = self.L
+        self.n_up = L // 2 if n_up is None else n_up
+        self.n_dn = L // 2 if n_dn is None else n_dn
+        # instances: list of (t, U, V)
+        if instances is None:
+            instances = [(t, U, V)]
+        self.instances = instances
+        self.models = [H.Model(L, self.bonds, ti, Ui, Vi, self.n_up, self.n_dn, modes=modes)
+                       for (ti, Ui, Vi) in instances]
+        self.groups = H.hva_groups(self.bonds, self.cls, L, layers, list(classes))
+        self.ans = H.Ansatz(self.models, self.groups, layers)
+        self.P = self.ans.P
+        self.n = 2 * L
+        self.omodels = [O.make_model(self.lat, ti, Ui, Vi, self.n_up, self.n_dn, modes=modes)
+                        for (ti, Ui, Vi) in instances]
+        self.ogroups = O.hva_groups(self.lat, layers, list(classes))
+        self.basis = O.sector_basis(self.omodels[0])
+        self.perturb = perturb
+        self._psi0 = {}
+        self._H = {}
+
+    def psi0(self, r=0):
+        if r not in self._psi0:
+            pu, pd, _ = O.orbitals(self.omodels[r], self.perturb)
+            self._psi0[r] = O.slater_state(self.omodels[r], pu, pd)
+        return self._psi0[r]
+
+    def Hmat(self, r=0):
+        if r not in self._H:
+            self._H[r] = O.hamiltonian(self.omodels[r], self.basis)
+        return self._H[r]
+
+    def full(self, vec):
+        out = np.zeros(1 << self.n, dtype=np.complex128)
+        out[self.basis.astype(np.int64)] = vec
+        return out
+
+    def oracle_energy_grad(self, theta, r=0):
+        return O.energy_and_gradient(self.omodels[r], self.basis, self.ogroups, theta, self.psi0(r),
+                                     self.Hmat(r))
+
+    def oracle_state(self, theta, r=0):
+        return O.ansatz_state(self.omodels[r], self.basis, self.ogroups, theta, self.psi0(r))
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))

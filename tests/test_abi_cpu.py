@@ -1,0 +1,169 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads and
+exports every declared entry point, the lattice helper agrees with the
+oracle's geometry, argument validation, and the planner's schedules are
+valid reorderings of the operation sequence."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2408_00836_gb300 as H
+from paper_2408_00836_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    with open(os.path.join(ROOT, "include", "hubsv.h")) as f:
+        hdr = f.read()
+    declared = set(re.findall(r"^HUB_API\s+[\w\s\*]+?\b(\w+)\s*\(", hdr, flags=re.M))
+    assert len(declared) >= 17
+    L = _lib.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+    assert declared == set(_lib.EXPORTS)
+
+
+@pytest.mark.parametrize("nx,ny,order", [(1, 4, "rowmajor"), (2, 4, "snake"), (3, 4, "rowmajor"),
+                                         (2, 7, "rowmajor"), (4, 4, "rowmajor"), (4, 4, "snake")])
+def test_lattice_matches_oracle(nx, ny, order):
+    bonds, cls = H.square_lattice(nx, ny, order)
+    lat = O.square_lattice(nx, ny, order)
+    assert bonds == lat.bonds
+    assert cls == lat.bond_class
+
+
+def _model(nx=2, ny=3, **kw):
+    bonds, cls = H.square_lattice(nx, ny)
+    L = nx * ny
+    t = np.zeros((L, L))
+    for (i, j) in bonds:
+        t[i, j] = t[j, i] = 1.0
+    return bonds, cls, t
+
+
+def test_model_validation():
+    bonds, cls, t = _model()
+    H.Model(6, bonds, t, np.full(6, 4.0), None, 3, 3)
+    bad = t.copy()
+    bad[0, 1] = 2.0  # not symmetric
+    with pytest.raises(H.HubError) as e:
+        H.Model(6, bonds, bad, None, None, 3, 3)
+    assert e.value.status == _lib.HUB_EINVAL
+    bad = t.copy()
+    bad[0, 5] = bad[5, 0] = 1.0  # hop off the bond list
+    with pytest.raises(H.HubError):
+        H.Model(6, bonds, bad, None, None, 3, 3)
+    with pytest.raises(H.HubError):
+        H.Model(6, bonds + [(0, 1)], t, None, None, 3, 3)  # repeated bond
+    with pytest.raises(H.HubError):
+        H.Model(6, bonds, t, None, None, 7, 3)  # too many particles
+    with pytest.raises(H.HubError) as e:
+        H.Model(6, bonds, t, None, None, 3, 3, modes=(np.arange(6), np.arange(6) + 5))
+    assert e.value.status == _lib.HUB_EINVAL
+    with pytest.raises(H.HubError) as e:  # a valid but unsupported permutation
+        H.Model(6, bonds, t, None, None, 3, 3, modes=(np.arange(6)[::-1].copy(), np.arange(6) + 6))
+    assert e.value.status == _lib.HUB_EUNSUPPORTED
+
+
+def test_ansatz_validation():
+    bonds, cls, t = _model()
+    m = H.Model(6, bonds, t, np.full(6, 4.0), None, 3, 3)
+    with pytest.raises(H.HubError):   # two bonds sharing a site in one hop group
+        H.Ansatz(m, [(H.HOP, [0, 1], 0)])
+    with pytest.raises(H.HubError):
+        H.Ansatz(m, [(H.HOP, [99], 0)])
+    with pytest.raises(H.HubError):
+        H.Ansatz(m, [(H.ONSITE, [0], -1)])
+    a = H.Ansatz(m, [(H.HOP, [0], 0), (H.ONSITE, list(range(6)), 3)])
+    assert a.P == 4 and a.n == 12
+
+
+# ---------------------------------------------------------------------------
+# schedule validity
+# ---------------------------------------------------------------------------
+
+def _sequence(a_groups, bonds, L, which):
+    """The operation sequence the planner receives (see ans_plan_describe):
+    entries (kind, modes, diagonal, cls) with blocked modes."""
+    up = lambda i: i
+    dn = lambda i: L + i
+    seq = []
+    for (kind, terms, p) in a_groups:
+        if kind == H.HOP:
+            for b in terms:
+                i, j = bonds[b]
+                for m in (up, dn):
+                    seq.append(("giv", {m(i), m(j)}, False, 0))
+        else:
+            if kind == H.ONSITE:
+                sup = {up(i) for i in terms} | {dn(i) for i in terms}
+            elif kind == H.NN_V:
+                sup = set()
+                for b in terms:
+                    for s in bonds[b]:
+                        sup |= {up(s), dn(s)}
+            else:
+                sup = set(range(2 * L))
+            seq.append(("diag", sup, True, 0))
+    fwd = list(seq)
+    cls = 1 if which == 0 else 2
+    for (i, j) in bonds:
+        for m in (up, dn):
+            seq.append(("h", {m(i), m(j)}, False, cls))
+    seq.append(("hdiag", None, True, cls))   # support: every mode with a coefficient
+    if which == 1:
+        for op in reversed(fwd):
+            seq.append(("grad",) + op[1:3] + (3,))
+            seq.append(("inv",) + op[1:3] + (3,))
+    return seq
+
+
+def _check_schedule(plan, seq, n, k, c, all_modes):
+    seen = []
+    for tile, flags, ids in plan:
+        assert bin(tile).count("1") == k
+        assert tile & ((1 << c) - 1) == (1 << c) - 1, "coalescing bits missing"
+        for i in ids:
+            op = seq[i]
+            if not op[2]:
+                for m in op[1]:
+                    assert tile >> m & 1, "operation outside its tile"
+        seen.extend(ids)
+    assert sorted(seen) == list(range(len(seq))), "every operation exactly once"
+    pos = {idx: r for r, idx in enumerate(seen)}
+    sup = [all_modes if op[1] is None else op[1] for op in seq]
+    for a in range(len(seq)):
+        for b in range(a + 1, len(seq)):
+            commute = (seq[a][2] and seq[b][2]) or not (sup[a] & sup[b])
+            if not commute:
+                assert pos[a] < pos[b], f"order of non-commuting ops {a} {b} broken"
+    # lam-building steps never precede a forward factor
+    last_fwd = max((pos[i] for i, op in enumerate(seq) if op[3] == 0), default=-1)
+    for i, op in enumerate(seq):
+        if op[3] == 2:
+            assert pos[i] > last_fwd
+
+
+@pytest.mark.parametrize("number", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("which", [0, 1])
+def test_schedules_are_valid(number, which):
+    w = H.workloads.workload(number, batch_sets=1)
+    bonds, cls = H.square_lattice(w.nx, w.ny, w.order)
+    t, U, V = w.coefficients(bonds)
+    m = H.Model(w.n_sites, bonds, t, U, V if w.V else None, w.n_up, w.n_dn)
+    groups = H.hva_groups(bonds, cls, w.n_sites, w.layers, w.classes)
+    a = H.Ansatz(m, groups, w.layers)
+    seq = _sequence(groups, bonds, w.n_sites, which)
+    for dtype, k, c in [(H.C64, 13, 5), (H.C128, 12, 4)]:
+        k = min(k, w.n_qubits)
+        plan = a.plan_describe(which, dtype)
+        _check_schedule(plan, seq, w.n_qubits, k, min(c, k), set(range(w.n_qubits)))
+    for kk in (10, 14):
+        a.set_tile(H.C64, kk)
+        plan = a.plan_describe(which, H.C64)
+        _check_schedule(plan, seq, w.n_qubits, min(kk, w.n_qubits), min(5, kk, w.n_qubits),
+                        set(range(w.n_qubits)))

@@ -1,0 +1,170 @@
+"""GPU parity: the sm_103a path through the C ABI against the CPU oracle on
+the same seeded inputs, element by element where the oracle can, and by
+energies and gradients.  Sizes span one tile (8 qubits), several tiles with a
+ragged per-CTA split (12-16 qubits) and thousands of tiles (24 qubits)."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2408_00836_gb300 as H
+from paper_2408_00836_gb300 import workloads as W
+
+from helpers import TOL, Problem, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DT = {H.C64: torch.complex64, H.C128: torch.complex128}
+
+
+def _run(prob, theta, dtype, batch=1, grad=True, prep_kind=H.PREP_SLATER, neel_up=None,
+         keep_state=False):
+    dev = "cuda"
+    a = prob.ans
+    a.state_prepare(prep_kind, prob.perturb, neel_up, None, dtype, batch)
+    th = torch.tensor(np.asarray(theta, dtype=np.float64).reshape(batch, -1), device=dev)
+    psi = torch.empty((batch, 1 << prob.n), dtype=DT[dtype], device=dev)
+    E = torch.empty(batch, dtype=torch.float64, device=dev)
+    if grad:
+        lam = torch.empty_like(psi)
+        g = torch.empty((batch, a.P), dtype=torch.float64, device=dev)
+        a.energy_grad(th, psi, lam, E, g, dtype=dtype, batch=batch)
+        H.sync()
+        return E.cpu().numpy(), g.cpu().numpy(), None
+    a.energy(th, psi, E, dtype=dtype, batch=batch, keep_state=keep_state)
+    H.sync()
+    return E.cpu().numpy(), None, (psi.cpu().numpy() if keep_state else None)
+
+
+def _chain1x4():
+    w = W.workload(1)
+    bonds, _ = H.square_lattice(1, 4)
+    t, U, V = w.coefficients(bonds)
+    return Problem(1, 4, t=t, U=U, V=None, layers=2, classes=w.classes), w.theta()[0]
+
+
+@pytest.mark.parametrize("dtype", [H.C128, H.C64])
+def test_chain1x4_state_energy_gradient(dtype):
+    prob, theta = _chain1x4()
+    # initial state, element by element
+    psi = torch.empty((1, 1 << prob.n), dtype=DT[dtype], device="cuda")
+    prob.ans.state_prepare(H.PREP_SLATER, None, None, psi, dtype, 1)
+    H.sync()
+    ref0 = prob.full(prob.psi0())
+    got0 = psi.cpu().numpy()[0]
+    assert rel_err(got0, ref0) < TOL[dtype]
+    assert np.all(got0[ref0 == 0] == 0)
+    # final state
+    E, _, st = _run(prob, theta, dtype, grad=False, keep_state=True)
+    ref = prob.full(prob.oracle_state(theta))
+    assert rel_err(st[0], ref) < TOL[dtype]
+    assert np.all(st[0][ref == 0] == 0)       # no amplitude leaves the sector
+    # energy and gradient
+    Eo, go = prob.oracle_energy_grad(theta)
+    assert abs(E[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
+    E2, g, _ = _run(prob, theta, dtype)
+    assert abs(E2[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
+    assert np.max(np.abs(g[0] - go)) < TOL[dtype] * max(1.0, np.max(np.abs(go)))
+
+
+def _disordered_2x3(modes="blocked", V=0.4):
+    rng = np.random.default_rng(77)
+    bonds, _ = H.square_lattice(2, 3)
+    t = np.zeros((6, 6))
+    for (i, j) in bonds:
+        t[i, j] = t[j, i] = 1.0 + 0.8 * rng.standard_normal()
+    np.fill_diagonal(t, 0.8 * rng.standard_normal(6))   # on-site potential (Eq. 15)
+    U = 2.0 * (1 + 0.2 * rng.standard_normal(6))
+    Vm = np.zeros((6, 6))
+    for (i, j) in bonds:
+        Vm[i, j] = Vm[j, i] = V
+    return t, U, Vm
+
+
+@pytest.mark.parametrize("modes", ["blocked", "interleaved"])
+@pytest.mark.parametrize("dtype", [H.C128, H.C64])
+def test_disordered_extended_2x3_all_group_kinds(modes, dtype):
+    t, U, Vm = _disordered_2x3()
+    prob = Problem(2, 3, modes=modes, t=t, U=U, V=Vm, layers=2,
+                   classes=("U", "V", "pot", "h1", "v1", "h2", "v2"))
+    theta = np.random.default_rng(5).uniform(-math.pi, math.pi, prob.P)
+    E, _, st = _run(prob, theta, dtype, grad=False, keep_state=True)
+    assert rel_err(st[0], prob.full(prob.oracle_state(theta))) < TOL[dtype]
+    Eo, go = prob.oracle_energy_grad(theta)
+    assert abs(E[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
+    E2, g, _ = _run(prob, theta, dtype)
+    assert abs(E2[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
+    assert np.max(np.abs(g[0] - go)) < TOL[dtype] * max(1.0, np.max(np.abs(go)))
+    assert g[0][6] == 0.0 and g[0][13] == 0.0      # v2 is empty on two rows
+
+
+@pytest.mark.parametrize("dtype", [H.C128, H.C64])
+def test_neel_start(dtype):
+    t, U, Vm = _disordered_2x3()
+    prob = Problem(2, 3, t=t, U=U, V=Vm, layers=2, classes=("U", "V", "h1", "v1", "h2"))
+    neel = [1 if (x + y) % 2 == 0 else 0 for (x, y) in prob.lat.coords]
+    theta = np.random.default_rng(6).uniform(-math.pi, math.pi, prob.P)
+    om = prob.omodels[0]
+    psi0 = O.neel_state(om, prob.lat, prob.basis)
+    E0 = O.energy(om, prob.basis, prob.ogroups, np.zeros(prob.P), psi0, prob.Hmat())
+    assert abs(E0 - O.neel_energy(om)) < 1e-12
+    Eg, gg, _ = _run(prob, np.zeros(prob.P), dtype, prep_kind=H.PREP_NEEL, neel_up=neel)
+    assert abs(Eg[0] - O.neel_energy(om)) < TOL[dtype] * max(1.0, abs(E0))
+    Eg, gg, _ = _run(prob, theta, dtype, prep_kind=H.PREP_NEEL, neel_up=neel)
+    Eo, go = O.energy_and_gradient(om, prob.basis, prob.ogroups, theta, psi0, prob.Hmat())
+    assert abs(Eg[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
+    assert np.max(np.abs(gg[0] - go)) < TOL[dtype] * max(1.0, np.max(np.abs(go)))
+
+
+@pytest.mark.parametrize("dtype", [H.C64, H.C128])
+def test_grid2x4_batched_instances(dtype):
+    """Workload 2 shape (16 qubits, snake order, perturbed orbitals, four U
+    instances) with two seeded parameter sets: batch of 8 states."""
+    w = W.workload(2, batch_sets=2)
+    bonds, _ = H.square_lattice(2, 4, "snake")
+    inst = [w.coefficients(bonds, r) for r in range(4)]
+    inst = [(t, U, None) for (t, U, V) in inst]
+    prob = Problem(2, 4, order="snake", layers=4, classes=w.classes, perturb=w.orbital_perturbation(),
+                   instances=inst)
+    theta = w.theta()
+    E, g, _ = _run(prob, theta, dtype, batch=w.batch)
+    for b in range(w.batch):
+        Eo, go = prob.oracle_energy_grad(theta[b], r=b % 4)
+        assert abs(E[b] - Eo) < TOL[dtype] * max(1.0, abs(Eo)), b
+        assert np.max(np.abs(g[b] - go)) < TOL[dtype] * max(1.0, np.max(np.abs(go))), b
+    # energy-only path, same batch
+    E2, _, _ = _run(prob, theta, dtype, batch=w.batch, grad=False)
+    assert np.max(np.abs(E2 - E)) < TOL[dtype] * max(1.0, np.max(np.abs(E)))
+
+
+def test_apply_h_elementwise():
+    t, U, Vm = _disordered_2x3()
+    prob = Problem(2, 3, t=t, U=U, V=Vm, layers=1, classes=("h1",))
+    rng = np.random.default_rng(12)
+    v = rng.standard_normal(len(prob.basis)) + 1j * rng.standard_normal(len(prob.basis))
+    v /= np.linalg.norm(v)
+    full = prob.full(v)
+    ref = prob.full(prob.Hmat() @ v)
+    for dtype in (H.C128, H.C64):
+        psi = torch.tensor(full[None, :], dtype=DT[dtype], device="cuda")
+        lam = torch.empty_like(psi)
+        prob.ans.apply_h(psi, lam, dtype)
+        H.sync()
+        assert rel_err(lam.cpu().numpy()[0], ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [H.C64, H.C128])
+def test_grid3x4_24_qubits_against_oracle(dtype):
+    """Workload 3 (24 qubits, inhomogeneous t and U, V = 0.5 phases)."""
+    w = W.workload(3)
+    bonds, _ = H.square_lattice(3, 4)
+    t, U, V = w.coefficients(bonds)
+    prob = Problem(3, 4, t=t, U=U, V=V, layers=w.layers, classes=w.classes)
+    theta = w.theta()[0]
+    E, g, _ = _run(prob, theta, dtype)
+    Eo, go = prob.oracle_energy_grad(theta)
+    assert abs(E[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
+    assert np.max(np.abs(g[0] - go)) < TOL[dtype] * max(1.0, np.max(np.abs(go)))
