@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Benchmark: energy + adjoint-gradient evaluations per second of the
+Hubbard HVA statevector engine on one GB300 (replicas on N GPUs).
+
+Default workload: grid4x4 -- 4x4 open Hubbard lattice, 32 qubits (2^32
+amplitudes, 34.4 GB per complex64 vector), N_up = N_dn = 8, t and U with
+seeded +-10% inhomogeneity, U = 8, 4 HVA layers x 5 groups (20 parameters),
+U = 0 Slater-determinant start generated inside the first sweep, complex64
+amplitudes with FP64 reductions.  One step = one energy + adjoint gradient.
+
+Printed: one JSON line (rank 0).  ``value`` = evaluations/s over all ranks
+with inputs resident in HBM; ``e2e`` = the same through the C ABI with the
+parameters copied from pinned host memory and energy + gradient copied back
+every step; ``roofline`` = achieved HBM bandwidth of the dominant kernel
+(algorithmic bytes / CUDA-event duration of its launches in the timed
+region); ``cpu_baseline`` = the CPU oracle timed on a bounded sample.
+``--impl reference`` times the oracle alone (the reference arm).
+"""
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "energy+adjoint-grad evals/s and HBM TB/s at 24–32 qubits, c64 vs c128"
+WORKLOAD_TEXT = {
+    5: "grid4x4: 4x4 open Hubbard, 32 qubits, N=8+8, t and U with +-10% seeded inhomogeneity, U=8, "
+       "4 HVA layers x (U,h1,v1,h2,v2), Slater start, energy + adjoint gradient",
+    4: "grid2x7: 2x7 open Hubbard, 28 qubits, N=7+7, t=1, U=8, 8 HVA layers x (U,h1,v1,h2,v2), "
+       "Slater start, energy + adjoint gradient",
+    3: "grid3x4: 3x4 open extended Hubbard, 24 qubits, N=6+6, t=1+0.1N(0,1), U=4(1+0.1N(0,1)), V=0.5, "
+       "6 HVA layers x (U,V,h1,v1,h2,v2), Slater start, energy + adjoint gradient",
+}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for name in ("hubsv_kernels.cu", "hubsv_internal.h"):
+        with open(os.path.join(ROOT, "paper_2408_00836_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel_name, workload, dtype):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    e = d.get(f"{kernel_name}|{workload}|{dtype}")
+    if not e or e.get("kernel_hash") != _kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(number: int, down_configs: int = 64):
+    """Time the CPU oracle's operations of one energy + adjoint-gradient
+    evaluation on a sample of the sector rows and scale to a full evaluation.
+
+    The oracle's cost is one sparse-operator build per Hamiltonian term and
+    per ansatz term, and sparse mat-vecs, each linear in the number of rows.
+    Sample: all up-configurations times the first ``down_configs``
+    down-configurations (closed under up-spin hops) for up-spin terms, and
+    the mirror sample for down-spin terms.  Every operation kind of one
+    evaluation is timed on the sample; the estimate scales each by the row
+    ratio and by its count per evaluation.  Returns (seconds per evaluation,
+    description)."""
+    import numpy as np
+    import oracle as O
+    from paper_2408_00836_gb300 import workloads as W
+
+    w = W.workload(number, batch_sets=1)
+    lat = O.square_lattice(w.nx, w.ny, w.order)
+    t, U, V = w.coefficients(lat.bonds)
+    m = O.make_model(lat, t, U, V if w.V else None, w.n_up, w.n_dn)
+    L = m.n_sites
+    ups = O.hubbard._configs(m.up, m.n_up)
+    dns = O.hubbard._configs(m.dn, m.n_dn)
+    rows_full = len(ups) * len(dns)
+    nd = min(down_configs, len(dns))
+    basis_a = np.sort((ups[:, None] | dns[None, :nd]).ravel())     # closed under up hops
+    basis_b = np.sort((ups[None, :nd] | dns[:, None]).ravel())     # closed under down hops
+    rng = np.random.default_rng(0)
+    groups = O.hva_groups(lat, w.layers, ["eps" if c == "pot" else c for c in w.classes])
+    # per evaluation counts: builds (H terms + ansatz term cache) and mat-vecs per hop piece
+    n_hop_pieces = sum(2 * len(g.terms) for g in groups if g.kind == "hop")
+    n_diag_groups = sum(1 for g in groups if g.kind != "hop")
+    n_builds = 2 * 2 * len(lat.bonds)           # H terms, plus the ansatz cache of every term
+    n_mv = 2 * n_hop_pieces + 5 * n_hop_pieces  # forward exp (2), backward gen (1) + 2 exps (4)
+    t0 = time.perf_counter()
+    tb, tm = [], []
+    for basis, modes in ((basis_a, m.up), (basis_b, m.dn)):
+        psi = rng.standard_normal(len(basis)) + 1j * rng.standard_normal(len(basis))
+        for (i, j) in lat.bonds[:3]:
+            s = time.perf_counter()
+            T = O.hop_matrix(basis, int(modes[i]), int(modes[j]))
+            tb.append((time.perf_counter() - s) / len(basis))
+            s = time.perf_counter()
+            y = T @ psi
+            y = T @ y
+            tm.append((time.perf_counter() - s) / 2 / len(basis))
+    s = time.perf_counter()
+    d = O.hubbard.diagonal_energy(m, basis_a)
+    ph = np.exp(-1j * 0.3 * d) * psi[:len(basis_a)] if len(psi) >= len(basis_a) else None
+    t_diag = (time.perf_counter() - s) / len(basis_a)
+    del ph
+    per_row = n_builds * statistics.mean(tb) + n_mv * statistics.mean(tm) + (1 + 3 * n_diag_groups) * t_diag
+    est = per_row * rows_full
+    desc = (f"oracle ops timed on {len(basis_a)} of {rows_full} sector rows (all up x {nd} down "
+            f"configurations, and the mirror), scaled by row ratio and per-evaluation op counts "
+            f"({n_builds} operator builds, {n_mv} sparse mat-vecs, {1 + 3 * n_diag_groups} diagonal passes)")
+    return est, desc, time.perf_counter() - t0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def build_problem(number, H):
+    w = H.workloads.workload(number, batch_sets=1 if number == 2 else None)
+    bonds, cls = H.square_lattice(w.nx, w.ny, w.order)
+    models = []
+    for r in range(w.n_instances):
+        t, U, V = w.coefficients(bonds, r)
+        models.append(H.Model(w.n_sites, bonds, t, U, V if w.V else None, w.n_up, w.n_dn))
+    groups = H.hva_groups(bonds, cls, w.n_sites, w.layers, w.classes)
+    a = H.Ansatz(models, groups, w.layers)
+    return w, a
+
+
+def run_gpu(args, rank, world, dist):
+    import numpy as np
+    import torch
+    import paper_2408_00836_gb300 as H
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    dtype = H.C64 if args.dtype == "c64" else H.C128
+    tdt = torch.complex64 if dtype == H.C64 else torch.complex128
+    w, a = build_problem(args.workload, H)
+    batch = w.batch
+    a.state_prepare(H.PREP_SLATER, w.orbital_perturbation(), None, None, dtype, batch)
+    theta_h = torch.tensor(w.theta(), dtype=torch.float64).pin_memory()
+    theta = theta_h.to(dev)
+    psi = torch.empty((batch, 1 << w.n_qubits), dtype=tdt, device=dev)
+    lam = torch.empty_like(psi)
+    E = torch.empty(batch, dtype=torch.float64, device=dev)
+    g = torch.empty((batch, a.P), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        a.energy_grad(theta, psi, lam, E, g, dtype=dtype, batch=batch)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    n_sweeps, bytes_per_state = a.plan_stats(1, dtype)
+    clocks = Clocks(dev.index) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    H.profile(a, True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    recs = H.profile_read(a)
+    H.profile(a, False)
+    ck = clocks.stop() if clocks else None
+    if dist:
+        tt = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    value = world * batch * args.steps / (ms_total / 1e3)
+    E_val = float(E[0].item())
+
+    # roofline of the dominant kernel
+    names = {(1, 0): "sweep_kernel<float,1>", (2, 0): "sweep_kernel<float,2>",
+             (1, 1): "sweep_kernel<double,1>", (2, 1): "sweep_kernel<double,2>"}
+    agg = {}
+    for nv, dt, by, ms in recs:
+        k = names[(nv, dt)]
+        s = agg.setdefault(k, [0, 0.0, 0.0])
+        s[0] += 1
+        s[1] += by
+        s[2] += ms
+    tot_ms = sum(v[2] for v in agg.values()) or 1.0
+    dom = max(agg.items(), key=lambda kv: kv[1][2])
+    peak, peak_kind = _peaks()
+    ach = dom[1][1] / (dom[1][2] / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom[0], "achieved": round(ach, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": peak_kind,
+            "traffic": _traffic(dom[0], w.name, args.dtype),
+            "launches": dom[1][0], "share": round(dom[1][2] / tot_ms, 4),
+            "kernels": {k: {"launches": v[0], "ms": round(v[2], 3), "share": round(v[2] / tot_ms, 4),
+                            "GB/s": round(v[1] / (v[2] / 1e3) / 1e9, 1)} for k, v in agg.items()}}
+    hbm_tbs = bytes_per_state * batch * args.steps / (ms_total / 1e3) / 1e12
+
+    # end to end through the C ABI with host buffers
+    E_h = torch.empty(batch, dtype=torch.float64).pin_memory()
+    g_h = torch.empty((batch, a.P), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        theta.copy_(theta_h, non_blocking=True)
+        a.energy_grad(theta, psi, lam, E, g, dtype=dtype, batch=batch)
+        E_h.copy_(E, non_blocking=True)
+        g_h.copy_(g, non_blocking=True)
+        stream.synchronize()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e = {"value": round(world * batch * args.steps / (e2e_ms / 1e3), 4), "unit": "evals/s",
+           "h2d_bytes_per_step": int(theta_h.numel() * 8),
+           "d2h_bytes_per_step": int((E_h.numel() + g_h.numel()) * 8)}
+    launches = args.steps * (n_sweeps + 3)
+
+    out = {"metric": METRIC, "value": round(value, 4), "unit": "evals/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": args.dtype, "data": "synthetic (seeded inputs of the named workload)",
+           "config": {"workload": WORKLOAD_TEXT.get(args.workload, w.name), "qubits": w.n_qubits,
+                      "params": a.P, "batch_per_gpu": batch, "parallelism": f"replicas x{world}",
+                      "l2": "inputs larger than L2 (one vector = %.1f GB)" % (a.amp_bytes(dtype) / 1e9)},
+           "hbm_tbs": round(hbm_tbs, 3),
+           "plan": {"sweeps": n_sweeps, "bytes_per_eval": bytes_per_state},
+           "energy": E_val, "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+           "clocks": ck}
+    del psi, lam
+    torch.cuda.empty_cache()
+    if args.c128 and dtype == H.C64 and rank == 0:
+        out["c128"] = run_c128(args, w, a, H, torch, dev, theta, ms_step)
+    return out
+
+
+def run_c128(args, w, a, H, torch, dev, theta, ms_c64):
+    """The same evaluation in complex128 (psi + lam = 2 x 68.7 GB at 32
+    qubits), fewer steps: it is FP64-bound on this part."""
+    free, _ = torch.cuda.mem_get_info(dev)
+    need = 2 * a.amp_bytes(H.C128) * w.batch
+    if need > free * 0.95:
+        return {"skipped": f"needs {need / 1e9:.1f} GB, {free / 1e9:.1f} GB free"}
+    a.state_prepare(H.PREP_SLATER, w.orbital_perturbation(), None, None, H.C128, w.batch)
+    psi = torch.empty((w.batch, 1 << w.n_qubits), dtype=torch.complex128, device=dev)
+    lam = torch.empty_like(psi)
+    E = torch.empty(w.batch, dtype=torch.float64, device=dev)
+    g = torch.empty((w.batch, a.P), dtype=torch.float64, device=dev)
+    a.energy_grad(theta, psi, lam, E, g, dtype=H.C128, batch=w.batch)   # warm-up
+    torch.cuda.synchronize()
+    steps = max(1, args.c128_steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        a.energy_grad(theta, psi, lam, E, g, dtype=H.C128, batch=w.batch)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    del psi, lam
+    torch.cuda.empty_cache()
+    return {"value": round(w.batch * 1e3 / ms, 5), "unit": "evals/s", "ms_per_step": round(ms, 3),
+            "steps": steps, "warmup": 1, "energy": float(E[0].item()),
+            "c64_speedup": round(ms / ms_c64, 3)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", type=int, default=5, choices=[3, 4, 5])
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--no-c128", dest="c128", action="store_false")
+    ap.add_argument("--c128-steps", type=int, default=1)
+    ap.add_argument("--no-cpu", dest="cpu", action="store_false")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle  # noqa: F401
+        ests = []
+        desc = ""
+        for i in range(args.warmup + args.steps):
+            est, desc, _ = oracle_sample(args.workload)
+            if i >= args.warmup:
+                ests.append(est)
+        sec = statistics.mean(ests)
+        v = 1.0 / sec
+        out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+               "data": "synthetic (seeded inputs of the named workload)",
+               "config": {"workload": WORKLOAD_TEXT.get(args.workload, str(args.workload))},
+               "cpu_baseline": {"value": v, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                                "sample": desc, "host_cores": os.cpu_count()},
+               "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    out = run_gpu(args, rank, world, dist)
+    if rank == 0:
+        if args.cpu and world == 1:
+            est, desc, wall = oracle_sample(args.workload)
+            out["cpu_baseline"] = {"value": 1.0 / est, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                                   "sample": desc, "sample_wall_s": round(wall, 1),
+                                   "host_cores": os.cpu_count()}
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

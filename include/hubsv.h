@@ -201,6 +201,15 @@ HUB_API hub_status ans_plan_describe(ans_t ans, int32_t which, int32_t dtype,
                                      uint32_t flags, int64_t* buf, int32_t cap,
                                      int32_t* len);
 
+/* Per-launch timing: with profiling enabled every sweep launch is bracketed
+ * by CUDA events on its stream.  ans_profile_read waits for the recorded
+ * events, writes 4 doubles per launch [vectors in the tile (1 = psi,
+ * 2 = psi and lam), dtype, amplitude bytes moved (vector reads + writes),
+ * milliseconds] and clears the record; out == NULL sets only *n.          */
+HUB_API hub_status ans_profile(ans_t ans, int32_t enable);
+HUB_API hub_status ans_profile_read(ans_t ans, double* out, int32_t cap,
+                                    int32_t* n);
+
 /* Tile size override (log2 amplitudes per tile; 0 = automatic).  Used by the
  * autotuner.                                                                */
 HUB_API hub_status ans_set_tile(ans_t ans, int32_t dtype, int32_t log2_tile);

@@ -108,8 +108,11 @@ class Model:
 
 
 def _lib_loaded():
-    from . import _lib as m
-    return m._lib is not None
+    try:
+        from . import _lib as m
+        return m._lib is not None
+    except Exception:  # interpreter shutdown
+        return False
 
 
 def hva_groups(bonds, classes, n_sites: int, n_layers: int, layer: Sequence[str]):
@@ -275,3 +278,17 @@ def energy_fn(ans: Ansatz, theta, psi, lam, dtype=C64, batch: int = 1, ckpt=None
                 return gE[:, None] * g, None, None, None, None, None, None
         _EnergyFn.fn = EnergyFunction
     return _EnergyFn.fn.apply(theta, ans, psi, lam, dtype, batch, ckpt)
+
+
+def profile(ans: Ansatz, enable: bool = True):
+    """Enable (or disable) per-launch CUDA-event timing of the sweeps."""
+    check(lib().ans_profile(ans.handle, 1 if enable else 0))
+
+
+def profile_read(ans: Ansatz):
+    """[(vectors, dtype, bytes, ms)] of the sweep launches since enabling."""
+    n = ctypes.c_int32(0)
+    check(lib().ans_profile_read(ans.handle, None, 0, ctypes.byref(n)))
+    buf = (ctypes.c_double * max(1, 4 * n.value))()
+    check(lib().ans_profile_read(ans.handle, buf, 4 * n.value, ctypes.byref(n)))
+    return [(int(buf[4 * i]), int(buf[4 * i + 1]), buf[4 * i + 2], buf[4 * i + 3]) for i in range(n.value)]

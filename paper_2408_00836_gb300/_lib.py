@@ -21,7 +21,7 @@ EXPORTS = [
     "hub_square_lattice", "hub_create", "hub_destroy", "ans_create", "ans_create_multi",
     "ans_destroy", "ans_num_params", "ans_num_qubits", "state_prepare", "energy",
     "energy_grad", "hub_apply_h", "ans_plan_stats", "ans_set_tile", "hub_sync",
-    "hub_last_error", "ans_plan_describe",
+    "hub_last_error", "ans_plan_describe", "ans_profile", "ans_profile_read",
 ]
 
 
@@ -76,6 +76,8 @@ def lib():
         "ans_set_tile": (st, [c_void_p, c_int32, c_int32]),
         "ans_plan_describe": (st, [c_void_p, c_int32, c_int32, c_uint32, POINTER(c_int64), c_int32,
                                    POINTER(c_int32)]),
+        "ans_profile": (st, [c_void_p, c_int32]),
+        "ans_profile_read": (st, [c_void_p, POINTER(c_double), c_int32, POINTER(c_int32)]),
         "hub_sync": (st, [c_void_p]),
         "hub_last_error": (c_char_p, []),
     }

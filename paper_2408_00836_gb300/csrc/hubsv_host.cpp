@@ -221,7 +221,18 @@ struct hub_ansatz {
   std::map<int, Plan*> plans;
   int tile_override[2] = {0, 0};
   bool dev_ready = false;
-  ~hub_ansatz() { for (auto& kv : plans) delete kv.second; }
+  // optional per-launch timing (CUDA events around every sweep launch)
+  struct ProfRec { cudaEvent_t e0, e1; int nv, dtype; double bytes; };
+  bool prof = false;
+  std::vector<ProfRec> prof_recs;
+  void prof_clear() {
+    for (auto& r : prof_recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+    prof_recs.clear();
+  }
+  ~hub_ansatz() {
+    prof_clear();
+    for (auto& kv : plans) delete kv.second;
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -900,7 +911,24 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
     per_sm = std::max(per_sm, 1);
     uint64_t grid = (uint64_t)sms * per_sm;
     grid = std::min<uint64_t>(grid, ka.n_tiles);
+    hub_ansatz::ProfRec rec{};
+    if (a->prof) {
+      HUB_CUDA(cudaEventCreate(&rec.e0), "cudaEventCreate");
+      HUB_CUDA(cudaEventCreate(&rec.e1), "cudaEventCreate");
+      HUB_CUDA(cudaEventRecord(rec.e0, st), "cudaEventRecord");
+    }
     HUB_CUDA(launch_sweep(dtype, pl->sweeps[i], ka, (int)grid, smem, st), "sweep kernel launch");
+    if (a->prof) {
+      HUB_CUDA(cudaEventRecord(rec.e1, st), "cudaEventRecord");
+      const uint32_t f = pl->sweeps[i].flags;
+      const int nvec_io = ((f & SW_READ_PSI) ? 1 : 0) + ((f & SW_WRITE_PSI) ? 1 : 0) +
+                          ((f & SW_READ_LAM) ? 1 : 0) + ((f & SW_WRITE_LAM) ? 1 : 0) +
+                          ((f & SW_CKPT_WRITE) ? 1 : 0) + ((f & SW_CKPT_READ) ? 1 : 0);
+      rec.nv = nv;
+      rec.dtype = dtype;
+      rec.bytes = (double)nvec_io * (double)(dtype == HUB_C64 ? 8 : 16) * (double)(1ull << n) * (double)batch;
+      a->prof_recs.push_back(rec);
+    }
   }
   HUB_CUDA(launch_finalize((const double*)a->d_acc.p, n_slots, a->P, a->P, E, grad, batch, st), "finalize kernel");
   return HUB_OK;
@@ -1070,6 +1098,32 @@ extern "C" hub_status ans_plan_describe(ans_t a, int32_t which, int32_t dtype, u
     if (cap < (int32_t)out.size()) return fail(HUB_EINVAL, "ans_plan_describe: buffer too small");
     std::copy(out.begin(), out.end(), buf);
   }
+  return HUB_OK;
+}
+
+extern "C" hub_status ans_profile(ans_t a, int32_t enable) {
+  if (!a) return fail(HUB_EINVAL, "ans_profile: NULL ansatz");
+  a->prof_clear();
+  a->prof = enable != 0;
+  return HUB_OK;
+}
+
+extern "C" hub_status ans_profile_read(ans_t a, double* out, int32_t cap, int32_t* n) {
+  if (!a || !n) return fail(HUB_EINVAL, "ans_profile_read: bad arguments");
+  *n = (int32_t)a->prof_recs.size();
+  if (!out) return HUB_OK;
+  if (cap < 4 * *n) return fail(HUB_EINVAL, "ans_profile_read: buffer too small");
+  for (size_t i = 0; i < a->prof_recs.size(); ++i) {
+    auto& r = a->prof_recs[i];
+    float ms = 0.f;
+    HUB_CUDA(cudaEventSynchronize(r.e1), "cudaEventSynchronize");
+    HUB_CUDA(cudaEventElapsedTime(&ms, r.e0, r.e1), "cudaEventElapsedTime");
+    out[4 * i + 0] = r.nv;
+    out[4 * i + 1] = r.dtype;
+    out[4 * i + 2] = r.bytes;
+    out[4 * i + 3] = ms;
+  }
+  a->prof_clear();
   return HUB_OK;
 }
 

@@ -383,6 +383,32 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
 // coefficient and phase tables (one thread per entry, FP64 trig)
 // ---------------------------------------------------------------------------
 
+// Round the unit complex number (c, s) to the precision of R.  For FP32 the
+// pair is chosen among the neighbouring representable values as the one
+// closest to the unit circle, so a rotation or phase with these entries
+// changes norms by ~1e-8 instead of ~1e-7 (this drift would otherwise add
+// up over the forward factors and their inverses in the adjoint pass).
+template <typename R>
+__device__ __forceinline__ typename CT<R>::T2 unit_round(double c, double s);
+template <>
+__device__ __forceinline__ double2 unit_round<double>(double c, double s) {
+  return make_double2(c, s);
+}
+template <>
+__device__ __forceinline__ float2 unit_round<float>(double c, double s) {
+  const float c0 = (float)c, s0 = (float)s;
+  float bc = c0, bs = s0;
+  double be = fabs((double)c0 * c0 + (double)s0 * s0 - 1.0);
+  const float cs[3] = {nextafterf(c0, -2.f), c0, nextafterf(c0, 2.f)};
+  const float ss[3] = {nextafterf(s0, -2.f), s0, nextafterf(s0, 2.f)};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const double e = fabs((double)cs[i] * cs[i] + (double)ss[j] * ss[j] - 1.0);
+      if (e < be) { be = e; bc = cs[i]; bs = ss[j]; }
+    }
+  return make_float2(bc, bs);
+}
+
 template <typename R>
 __global__ void coef_kernel(const double* __restrict__ theta, int P,
                             const int32_t* __restrict__ gate_param,
@@ -403,7 +429,7 @@ __global__ void coef_kernel(const double* __restrict__ theta, int P,
       const double al = theta[b * P + gate_param[j]] * gate_t[(int64_t)inst * n_gates + j];
       double s, c;
       sincos(al, &s, &c);
-      coef[b * n_gates + j] = mk<T2, R>((R)c, (R)s);
+      coef[b * n_gates + j] = unit_round<R>(c, s);
     } else {
       const int64_t e = j - n_gates;
       const int pp = tab_param[e];
@@ -411,7 +437,7 @@ __global__ void coef_kernel(const double* __restrict__ theta, int P,
       const double al = -th * tab_val[(int64_t)inst * n_tab + e];
       double s, c;
       sincos(al, &s, &c);
-      phase[b * n_tab + e] = mk<T2, R>((R)c, (R)s);
+      phase[b * n_tab + e] = unit_round<R>(c, s);
     }
   }
 }

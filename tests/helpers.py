@@ -38,7 +38,8 @@ class Problem:
         self.n = 2 * L
         self.omodels = [O.make_model(self.lat, ti, Ui, Vi, self.n_up, self.n_dn, modes=modes)
                         for (ti, Ui, Vi) in instances]
-        self.ogroups = O.hva_groups(self.lat, layers, list(classes))
+        # the oracle names the on-site potential group 'eps'
+        self.ogroups = O.hva_groups(self.lat, layers, ["eps" if c == "pot" else c for c in classes])
         self.basis = O.sector_basis(self.omodels[0])
         self.perturb = perturb
         self._psi0 = {}
