@@ -36,6 +36,8 @@ WORKLOAD_TEXT = {
        "4 HVA layers x (U,h1,v1,h2,v2), Slater start, energy + adjoint gradient",
     4: "grid2x7: 2x7 open Hubbard, 28 qubits, N=7+7, t=1, U=8, 8 HVA layers x (U,h1,v1,h2,v2), "
        "Slater start, energy + adjoint gradient",
+    6: "grid3x4u: 3x4 open Hubbard, 24 qubits, N=6+6, t=1, U=8, 4 HVA layers x (U,h1,v1,h2,v2), "
+       "Slater start, energy + adjoint gradient (profiling proxy of grid4x4)",
     3: "grid3x4: 3x4 open extended Hubbard, 24 qubits, N=6+6, t=1+0.1N(0,1), U=4(1+0.1N(0,1)), V=0.5, "
        "6 HVA layers x (U,V,h1,v1,h2,v2), Slater start, energy + adjoint gradient",
 }
@@ -53,7 +55,7 @@ def _peaks():
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for name in ("hubsv_kernels.cu", "hubsv_internal.h"):
+    for name in ("hubsv_sweep.cuh", "hubsv_internal.h"):
         with open(os.path.join(ROOT, "paper_2408_00836_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -355,7 +357,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", type=int, default=5, choices=[3, 4, 5])
+    ap.add_argument("--workload", type=int, default=5, choices=[3, 4, 5, 6])
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--no-c128", dest="c128", action="store_false")
     ap.add_argument("--c128-steps", type=int, default=1)

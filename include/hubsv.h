@@ -191,7 +191,8 @@ HUB_API hub_status ans_plan_stats(ans_t ans, int32_t which, int32_t dtype,
 
 /* Schedule of a call kind (0 energy, 1 energy_grad, 2 apply_h) for checking
  * by tests: buf receives [n_sweeps, then per sweep: tile-bit mask, sweep
- * flags, n_ops, the sequence index of each op in execution order].  The
+ * flags (bits 0-15) | register phases (bits 16-31), n_ops, the sequence
+ * index of each op in execution order].  The
  * sequence is: the ansatz factors in order (one per hop term and spin, one
  * per diagonal group); then the H terms (one per bond and spin, bonds in
  * lattice order, up before down) and H's diagonal; then (energy_grad) for

@@ -15,7 +15,8 @@ INC = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libhubsv.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["hubsv_host.cpp", "hubsv_kernels.cu"]
+SOURCES = ["hubsv_api.cpp", "hubsv_plan.cpp", "hubsv_tables.cu", "hubsv_sweep_f1.cu",
+           "hubsv_sweep_f2.cu", "hubsv_sweep_d1.cu", "hubsv_sweep_d2.cu"]
 
 
 def _nvcc():

@@ -1,9 +1,8 @@
-// Host side of the Hubbard VQE statevector engine: model and ansatz handles,
-// the FP64 one-body diagonalisation for the Slater-determinant initial
-// state, the sweep planner and the C-ABI entry points of hubsv.h.
-#include "hubsv.h"
-#include "hubsv_internal.h"
-
+// C-ABI entry points of the Hubbard VQE statevector engine (hubsv.h): model
+// and ansatz handles with their coefficient tables, the FP64 one-body
+// diagonalisation and determinant tables of the Slater-determinant initial
+// state, plan execution and the profiling hooks.  The planner lives in
+// hubsv_plan.cpp, the kernels in hubsv_kernels.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -12,11 +11,16 @@
 #include <string>
 #include <vector>
 
+#include "hubsv_host.h"
+
 using namespace hubsv;
 
 namespace {
-
 thread_local std::string g_err;
+inline int popc64(uint64_t x) { return __builtin_popcountll(x); }
+}  // namespace
+
+namespace hubsv {
 
 hub_status fail(hub_status s, const std::string& m) {
   g_err = m;
@@ -27,21 +31,36 @@ hub_status cuda_fail(cudaError_t e, const char* what) {
   return fail(HUB_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define HUB_CUDA(call, what)                       \
-  do {                                             \
-    cudaError_t e_ = (call);                       \
-    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-  } while (0)
+hub_status DevBuf::ensure(size_t n, const char* what) {
+  if (n <= bytes && p) return HUB_OK;
+  if (p) { cudaFree(p); p = nullptr; bytes = 0; }
+  if (n == 0) n = 16;
+  cudaError_t e = cudaMalloc(&p, n);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    return fail(HUB_ENOMEM, std::string("cudaMalloc failed for ") + what);
+  }
+  bytes = n;
+  return HUB_OK;
+}
 
-inline int popc64(uint64_t x) { return __builtin_popcountll(x); }
+}  // namespace hubsv
 
-uint64_t between_mask(int p, int q) {  // bits strictly between p < q
-  return ((1ull << q) - 1ull) & ~((1ull << (p + 1)) - 1ull);
+void hub_ansatz::prof_clear() {
+  for (auto& r : prof_recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+  prof_recs.clear();
+}
+
+hub_ansatz::~hub_ansatz() {
+  prof_clear();
+  for (auto& kv : plans) delete kv.second;
 }
 
 // ---------------------------------------------------------------------------
 // FP64 symmetric eigensolver (cyclic Jacobi) and determinants
 // ---------------------------------------------------------------------------
+
+namespace {
 
 void jacobi_eigh(int n, std::vector<double> a, std::vector<double>& w, std::vector<double>& v) {
   v.assign((size_t)n * n, 0.0);
@@ -122,118 +141,7 @@ double det_lu(int n, std::vector<double> m) {
   }
   return d;
 }
-
-// ---------------------------------------------------------------------------
-// device buffer helper
-// ---------------------------------------------------------------------------
-
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-  ~DevBuf() { if (p) cudaFree(p); }
-  hub_status ensure(size_t n, const char* what) {
-    if (n <= bytes && p) return HUB_OK;
-    if (p) { cudaFree(p); p = nullptr; bytes = 0; }
-    if (n == 0) n = 16;
-    cudaError_t e = cudaMalloc(&p, n);
-    if (e != cudaSuccess) {
-      p = nullptr;
-      return fail(HUB_ENOMEM, std::string("cudaMalloc failed for ") + what);
-    }
-    bytes = n;
-    return HUB_OK;
-  }
-  template <typename T>
-  hub_status upload(const std::vector<T>& v, const char* what) {
-    hub_status s = ensure(std::max<size_t>(v.size() * sizeof(T), 16), what);
-    if (s != HUB_OK) return s;
-    if (!v.empty()) HUB_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), what);
-    return HUB_OK;
-  }
-};
-
 }  // namespace
-
-// ---------------------------------------------------------------------------
-// handles
-// ---------------------------------------------------------------------------
-
-struct hub_model {
-  int L = 0, n = 0, s = 0, layout = 0;
-  std::vector<int> up, dn;
-  std::vector<std::pair<int, int>> bonds;
-  std::vector<double> t, U, V;
-  int n_up = 0, n_dn = 0;
-};
-
-namespace {
-
-// Host-level operation before tiling.
-struct SeqOp {
-  uint8_t kind = 0, flags = 0;
-  int p = -1, q = -1;       // modes (hop-type)
-  int gate = -1, hterm = -1, slot = -1, diag = -1;
-  uint64_t support = 0;
-  bool diagonal = false;
-  int cls = 0;              // 0 forward, 1 measure, 2 lam, 3 backward
-};
-
-struct Plan {
-  std::vector<SweepDev> sweeps;
-  std::vector<int> nvec;    // 1 or 2 per sweep
-  std::vector<OpDev> hops;  // host copy of the operations
-  std::vector<uint64_t> tiles;
-  std::vector<std::vector<int>> seq_ids;   // sequence index of each op, per sweep
-  bool uploaded = false;
-  DevBuf ops;
-  int k = 0, c = 0;
-  double bytes_per_state = 0;
-};
-
-}  // namespace
-
-struct hub_ansatz {
-  std::vector<hub_model*> models;
-  int n_inst = 0, L = 0, n = 0, P = 0, s = 0, layout = 0;
-  uint64_t upmask = 0;
-  // forward sequence and H terms
-  std::vector<SeqOp> fwd;
-  struct HTerm { int p, q; };
-  std::vector<HTerm> hterms;
-  int h_diag = -1;                       // DiagOp index of H's diagonal
-  std::vector<DiagOpDev> diag_ops;
-  // static device tables
-  std::vector<int32_t> gate_param;
-  std::vector<double> gate_t;            // [n_inst][n_gates]
-  std::vector<int32_t> tab_param;        // [n_tab]
-  std::vector<double> tab_val;           // [n_inst][n_tab]
-  std::vector<double> hcoef;             // [n_inst][n_hterms]
-  std::vector<double> real_tabs;         // [n_inst][real_stride]
-  int n_gates = 0, n_tab = 0, real_stride = 0;
-  DevBuf d_gate_param, d_gate_t, d_tab_param, d_tab_val, d_hcoef, d_real, d_diag;
-  // initial state
-  DevBuf d_sd;
-  int prep_kind = -1;
-  uint64_t neel_x0 = 0;
-  // per-call scratch
-  DevBuf d_coef[2], d_phase[2], d_acc;
-  // plans: key = which*16 + dtype*4 + flags
-  std::map<int, Plan*> plans;
-  int tile_override[2] = {0, 0};
-  bool dev_ready = false;
-  // optional per-launch timing (CUDA events around every sweep launch)
-  struct ProfRec { cudaEvent_t e0, e1; int nv, dtype; double bytes; };
-  bool prof = false;
-  std::vector<ProfRec> prof_recs;
-  void prof_clear() {
-    for (auto& r : prof_recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
-    prof_recs.clear();
-  }
-  ~hub_ansatz() {
-    prof_clear();
-    for (auto& kv : plans) delete kv.second;
-  }
-};
 
 // ---------------------------------------------------------------------------
 // lattice helper and model
@@ -344,8 +252,6 @@ extern "C" void hub_destroy(hub_t m) { delete m; }
 
 namespace {
 
-// Register a diagonal operator given per-mode X coefficients (and a constant),
-// per-site Y (double occupancy) coefficients and V bonds, each per instance.
 int add_diag_op(hub_ansatz* a, const std::vector<std::vector<double>>& xcoef,
                 const std::vector<double>& xconst,
                 const std::vector<std::vector<double>>& ycoef,
@@ -428,8 +334,11 @@ int add_diag_op(hub_ansatz* a, const std::vector<std::vector<double>>& xcoef,
   a->diag_ops.push_back(d);
   return (int)a->diag_ops.size() - 1;
 }
+}  // namespace
 
-uint64_t diag_support(hub_ansatz* a, int di) {
+namespace hubsv {
+
+uint64_t diag_support(const hub_ansatz* a, int di) {
   // modes that the diagonal operator reads
   const DiagOpDev& d = a->diag_ops[di];
   uint64_t m = 0;
@@ -450,7 +359,7 @@ uint64_t diag_support(hub_ansatz* a, int di) {
   return m;
 }
 
-}  // namespace
+}  // namespace hubsv
 
 extern "C" hub_status ans_create_multi(const hub_t* models, int32_t n_models, int32_t n_layers,
                                        int32_t groups_per_layer, const hub_group* groups, ans_t* out) {
@@ -624,14 +533,8 @@ extern "C" hub_status ans_set_tile(ans_t a, int32_t dtype, int32_t log2_tile) {
   return HUB_OK;
 }
 
-// ---------------------------------------------------------------------------
-// planner
-// ---------------------------------------------------------------------------
-
 namespace {
 
-// Static tables go to the device on the first compute call (ans_create
-// itself touches no GPU, so the host logic runs anywhere).
 hub_status ensure_device(hub_ansatz* a) {
   if (a->dev_ready) return HUB_OK;
   hub_status st;
@@ -641,193 +544,13 @@ hub_status ensure_device(hub_ansatz* a) {
       (st = a->d_tab_val.upload(a->tab_val, "phase values")) != HUB_OK ||
       (st = a->d_hcoef.upload(a->hcoef, "hop coefficients")) != HUB_OK ||
       (st = a->d_real.upload(a->real_tabs, "diagonal tables")) != HUB_OK ||
+      (st = a->d_real32.upload(std::vector<float>(a->real_tabs.begin(), a->real_tabs.end()),
+                               "diagonal tables (FP32)")) != HUB_OK ||
       (st = a->d_diag.upload(a->diag_ops, "diagonal operators")) != HUB_OK)
     return st;
   a->dev_ready = true;
   return HUB_OK;
 }
-
-int default_tile_bits(int dtype) { return dtype == HUB_C64 ? 13 : 12; }
-int coalesce_bits(int dtype) { return dtype == HUB_C64 ? 5 : 4; }   // 256-byte runs
-
-// Build the operation sequence of a call kind: 0 energy, 1 energy + gradient,
-// 2 apply H.
-std::vector<SeqOp> build_sequence(hub_ansatz* a, int which) {
-  std::vector<SeqOp> seq;
-  if (which != 2) seq = a->fwd;
-  const uint64_t hsup = diag_support(a, a->h_diag);
-  for (size_t t = 0; t < a->hterms.size(); ++t) {
-    SeqOp op;
-    op.kind = which == 0 ? OP_MEAS_HOP : OP_LAM_HOP;
-    op.p = a->hterms[t].p;
-    op.q = a->hterms[t].q;
-    op.hterm = (int)t;
-    op.support = (1ull << op.p) | (1ull << op.q);
-    op.cls = which == 0 ? 1 : 2;
-    seq.push_back(op);
-  }
-  {
-    SeqOp op;
-    op.kind = which == 0 ? OP_MEAS_DIAG : OP_LAM_DIAG;
-    op.diag = a->h_diag;
-    op.diagonal = true;
-    op.support = hsup;
-    op.cls = which == 0 ? 1 : 2;
-    seq.push_back(op);
-  }
-  if (which == 1) {
-    for (int i = (int)a->fwd.size() - 1; i >= 0; --i) {
-      SeqOp g = a->fwd[i];
-      g.kind = g.kind == OP_GIV ? OP_GRAD_HOP : OP_GRAD_DIAG;
-      g.cls = 3;
-      seq.push_back(g);
-      SeqOp v = a->fwd[i];
-      v.flags = OPF_INV | OPF_LAM;
-      v.cls = 3;
-      seq.push_back(v);
-    }
-  }
-  return seq;
-}
-
-bool modifies_psi(const SeqOp& op) { return op.kind == OP_GIV || op.kind == OP_DIAG; }
-bool uses_lam(const SeqOp& op) {
-  return op.kind == OP_LAM_HOP || op.kind == OP_LAM_DIAG || op.kind == OP_GRAD_HOP ||
-         op.kind == OP_GRAD_DIAG || (op.flags & OPF_LAM);
-}
-bool modifies_lam(const SeqOp& op) {
-  return op.kind == OP_LAM_HOP || op.kind == OP_LAM_DIAG || (modifies_psi(op) && (op.flags & OPF_LAM));
-}
-
-// Greedy sweep construction.  Operations are taken in sequence order; an
-// operation runs in the current sweep when it commutes with every operation
-// skipped before it in this sweep and its modes fit in the tile (diagonal
-// operations need no tile bits).  Operations on disjoint modes commute;
-// diagonal operations commute with each other.  Lam-building operations wait
-// until the whole forward circuit has run.
-hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*& out) {
-  const int n = a->n;
-  int k = a->tile_override[dtype] ? a->tile_override[dtype] : default_tile_bits(dtype);
-  k = std::min(k, n);
-  const int c = std::min(coalesce_bits(dtype), k);
-  const uint64_t cmask = (1ull << c) - 1ull;
-  std::vector<SeqOp> seq = build_sequence(a, which);
-  std::vector<int> remaining(seq.size());
-  for (size_t i = 0; i < seq.size(); ++i) remaining[i] = (int)i;
-  struct PS { uint64_t tile; std::vector<int> ops; };
-  std::vector<PS> sweeps;
-  while (!remaining.empty()) {
-    uint64_t tile = cmask;
-    uint64_t s_any = 0, s_diag = 0;
-    bool fwd_skipped = false;
-    std::vector<int> exec, rest;
-    for (int idx : remaining) {
-      const SeqOp& op = seq[idx];
-      bool conflict = (op.support & s_any) || (!op.diagonal && (op.support & s_diag));
-      if (op.cls == 2 && fwd_skipped) conflict = true;
-      bool ok = false;
-      if (!conflict) {
-        const uint64_t need = op.diagonal ? 0ull : ((1ull << op.p) | (1ull << op.q));
-        const uint64_t nt = tile | need;
-        if (popc64(nt) <= k) { tile = nt; ok = true; }
-      }
-      if (ok) {
-        exec.push_back(idx);
-      } else {
-        rest.push_back(idx);
-        if (op.diagonal) s_diag |= op.support; else s_any |= op.support;
-        if (op.cls == 0) fwd_skipped = true;
-      }
-    }
-    if (exec.empty()) return fail(HUB_EUNSUPPORTED, "planner made no progress");
-    // pad the tile with the lowest unused bits
-    for (int b = 0; b < n && popc64(tile) < k; ++b) tile |= 1ull << b;
-    sweeps.push_back({tile, exec});
-    remaining.swap(rest);
-  }
-  if (sweeps.empty()) {  // nothing to do (e.g. no H terms and no gates): one read sweep
-    uint64_t tile = (k >= 64) ? ~0ull : ((1ull << k) - 1ull);
-    sweeps.push_back({tile, {}});
-  }
-  // flags and device ops
-  Plan* pl = new Plan();
-  pl->k = k;
-  pl->c = c;
-  std::vector<OpDev> dops;
-  const bool prep = (flags & HUB_FLAG_PREP_FUSED) != 0;
-  const bool keep = (flags & HUB_FLAG_KEEP_STATE) != 0;
-  bool lam_live = false;
-  const double amp = dtype == HUB_C64 ? 8.0 : 16.0;
-  double bytes = 0.0;
-  for (size_t si = 0; si < sweeps.size(); ++si) {
-    const PS& ps = sweeps[si];
-    SweepDev sw;
-    std::memset(&sw, 0, sizeof(sw));
-    sw.k = k;
-    sw.c = c;
-    sw.h1 = (k - c + 1) / 2;
-    int nt = 0, nn = 0;
-    int localpos[64];
-    for (int b = 0; b < n; ++b) {
-      if (ps.tile >> b & 1) { localpos[b] = nt; sw.tbits[nt++] = (int8_t)b; }
-      else { localpos[b] = -1; sw.nbits[nn++] = (int8_t)b; }
-    }
-    sw.n_nontile = nn;
-    sw.op_begin = (int)dops.size();
-    bool mod_psi = false, use_lam = false, mod_lam = false;
-    for (int idx : ps.ops) {
-      const SeqOp& op = seq[idx];
-      OpDev d;
-      std::memset(&d, 0, sizeof(d));
-      d.kind = op.kind;
-      d.flags = op.flags;
-      d.gate = op.gate;
-      d.hterm = op.hterm;
-      d.slot = op.slot;
-      d.diag = op.diag;
-      if (!op.diagonal) {
-        d.p = (uint8_t)localpos[op.p];
-        d.q = (uint8_t)localpos[op.q];
-        const uint64_t bm = between_mask(op.p, op.q);
-        uint32_t bl = 0;
-        for (int b = 0; b < n; ++b)
-          if ((bm >> b & 1) && localpos[b] >= 0) bl |= 1u << localpos[b];
-        d.bmask_local = bl;
-        d.bmask_global = bm & ~ps.tile;
-      }
-      dops.push_back(d);
-      mod_psi = mod_psi || modifies_psi(op);
-      use_lam = use_lam || uses_lam(op);
-      mod_lam = mod_lam || modifies_lam(op);
-    }
-    sw.op_end = (int)dops.size();
-    const bool first = si == 0, last = si + 1 == sweeps.size();
-    uint32_t f = 0;
-    if (first && prep && which != 2) f |= SW_PREP; else f |= SW_READ_PSI;
-    if ((!last || keep) && (mod_psi || (f & SW_PREP))) f |= SW_WRITE_PSI;
-    if (which == 2 && !last) { /* psi is read only */ }
-    if (use_lam || (lam_live && mod_lam)) {
-      f |= SW_HAS_LAM;
-      if (lam_live) f |= SW_READ_LAM;
-      if (mod_lam && (!last || which == 2)) f |= SW_WRITE_LAM;
-      lam_live = true;
-    }
-    if (which == 2) f &= ~SW_WRITE_PSI;
-    sw.flags = f;
-    bytes += amp * (double)(1ull << n) *
-             (((f & SW_READ_PSI) ? 1 : 0) + ((f & SW_WRITE_PSI) ? 1 : 0) +
-              ((f & SW_READ_LAM) ? 1 : 0) + ((f & SW_WRITE_LAM) ? 1 : 0));
-    pl->sweeps.push_back(sw);
-    pl->nvec.push_back((f & SW_HAS_LAM) ? 2 : 1);
-    pl->tiles.push_back(ps.tile);
-    pl->seq_ids.push_back(ps.ops);
-  }
-  pl->bytes_per_state = bytes;
-  pl->hops = dops;
-  out = pl;
-  return HUB_OK;
-}
-
 hub_status get_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*& pl) {
   const int key = which * 16 + dtype * 4 + (int)(flags & 3u);  // PREP_FUSED | KEEP_STATE
   auto it = a->plans.find(key);
@@ -838,12 +561,6 @@ hub_status get_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*& 
   return HUB_OK;
 }
 
-size_t sweep_smem(const Plan* pl, int nv, int dtype, int n_slots) {
-  const int k = pl->k, c = pl->c, h1 = (k - c + 1) / 2, h2 = k - c - h1;
-  const size_t amp = dtype == HUB_C64 ? 8 : 16;
-  return (size_t)nv * (amp << k) + 8 * ((1u << h1) + (1u << h2)) + 8 * (size_t)n_slots;
-}
-
 hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, void* psi, void* lam,
                     void* ckpt, int64_t batch, double* E, double* grad, cudaStream_t st) {
   const int n = a->n;
@@ -852,6 +569,7 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
   if ((s = ensure_device(a)) != HUB_OK) return s;
   if (!pl->uploaded) {
     if ((s = pl->ops.upload(pl->hops.empty() ? std::vector<OpDev>(1) : pl->hops, "sweep ops")) != HUB_OK) return s;
+    if ((s = pl->phases.upload(pl->hphases, "sweep phases")) != HUB_OK) return s;
     pl->uploaded = true;
   }
   const size_t r2 = dtype == HUB_C64 ? 8 : 16;
@@ -872,6 +590,7 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
   ka.lam = lam;
   ka.ckpt = ckpt;
   ka.ops = (const OpDev*)pl->ops.p;
+  ka.phases = (const PhaseDev*)pl->phases.p;
   ka.diag_ops = (const DiagOpDev*)a->d_diag.p;
   ka.theta = theta;
   ka.P = a->P;
@@ -880,6 +599,7 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
   ka.hcoef = (const double*)a->d_hcoef.p;
   ka.n_hterms = (int)a->hterms.size();
   ka.real_tabs = (const double*)a->d_real.p;
+  ka.real_tabs32 = (const float*)a->d_real32.p;
   ka.real_stride = a->real_stride;
   ka.phase_tabs = a->d_phase[dtype].p;
   ka.phase_stride = a->n_tab;
@@ -889,6 +609,7 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
   ka.upmask = a->upmask;
   ka.batch = batch;
   ka.n_tiles = ((uint64_t)batch) << (n - pl->k);
+  if (ka.n_tiles >= (1ull << 31)) return fail(HUB_EUNSUPPORTED, "batch too large for one launch (2^31 tiles)");
   ka.acc = (double*)a->d_acc.p;
   ka.n_slots = n_slots;
   ka.slot_E = a->P;
@@ -899,15 +620,22 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
   ka.prep.layout = a->layout;
   ka.prep.neel_x0 = a->neel_x0;
   ka.prep.sd = (const double*)a->d_sd.p;
+  ka.prep.sd32 = (const float*)a->d_sd32.p;
   const int sms = device_sm_count();
   if (sms <= 0) return fail(HUB_ECUDA, "no CUDA device");
   const int optin = sweep_max_smem_optin();
   for (size_t i = 0; i < pl->sweeps.size(); ++i) {
+    const SweepDev& sw = pl->sweeps[i];
     const int nv = pl->nvec[i];
-    const size_t smem = sweep_smem(pl, nv, dtype, n_slots);
+    const int nph = sw.phase_end - sw.phase_begin;
+    const size_t smem = sweep_smem_bytes(dtype, nv, sw.k, n_slots, nph, sw.op_end - sw.op_begin);
     if ((int)smem > optin) return fail(HUB_EUNSUPPORTED, "tile does not fit in shared memory");
-    HUB_CUDA(sweep_set_smem(dtype, nv, smem), "cudaFuncSetAttribute");
-    int per_sm = (int)std::min<size_t>(8, (size_t)(228 * 1024) / (smem + 1024));
+    HUB_CUDA(sweep_set_smem(dtype, nv, sw.r, smem), "cudaFuncSetAttribute");
+    const int threads = 32 << sw.w;
+    const int regs = std::max(1, sweep_regs(dtype, nv, sw.r));
+    int per_sm = (int)((size_t)(228 * 1024) / (smem + 1024));
+    per_sm = std::min(per_sm, 2048 / threads);
+    per_sm = std::min(per_sm, 65536 / (regs * threads));
     per_sm = std::max(per_sm, 1);
     uint64_t grid = (uint64_t)sms * per_sm;
     grid = std::min<uint64_t>(grid, ka.n_tiles);
@@ -917,10 +645,10 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
       HUB_CUDA(cudaEventCreate(&rec.e1), "cudaEventCreate");
       HUB_CUDA(cudaEventRecord(rec.e0, st), "cudaEventRecord");
     }
-    HUB_CUDA(launch_sweep(dtype, pl->sweeps[i], ka, (int)grid, smem, st), "sweep kernel launch");
+    HUB_CUDA(launch_sweep(dtype, sw, ka, (int)grid, smem, st), "sweep kernel launch");
     if (a->prof) {
       HUB_CUDA(cudaEventRecord(rec.e1, st), "cudaEventRecord");
-      const uint32_t f = pl->sweeps[i].flags;
+      const uint32_t f = sw.flags;
       const int nvec_io = ((f & SW_READ_PSI) ? 1 : 0) + ((f & SW_WRITE_PSI) ? 1 : 0) +
                           ((f & SW_READ_LAM) ? 1 : 0) + ((f & SW_WRITE_LAM) ? 1 : 0) +
                           ((f & SW_CKPT_WRITE) ? 1 : 0) + ((f & SW_CKPT_READ) ? 1 : 0);
@@ -945,10 +673,6 @@ hub_status check_call(hub_ansatz* a, int32_t dtype, int64_t batch) {
 }
 
 }  // namespace
-
-// ---------------------------------------------------------------------------
-// initial state
-// ---------------------------------------------------------------------------
 
 extern "C" hub_status state_prepare(ans_t a, int32_t kind, const double* orb_perturb, const int32_t* neel_up,
                                     void* psi, int32_t dtype, int64_t batch, hub_stream_t stream) {
@@ -997,37 +721,22 @@ extern "C" hub_status state_prepare(ans_t a, int32_t kind, const double* orb_per
       }
     }
     if ((s = a->d_sd.upload(sd, "determinant tables")) != HUB_OK) return s;
+    if ((s = a->d_sd32.upload(std::vector<float>(sd.begin(), sd.end()), "determinant tables (FP32)")) != HUB_OK)
+      return s;
     a->prep_kind = 0;
   } else {
     return fail(HUB_EINVAL, "state_prepare: unknown kind");
   }
   if (!psi) return HUB_OK;
   // one sweep with no operations: generate and store psi_0
-  Plan pl;
-  const int k = std::min(dtype == HUB_C64 ? 13 : 12, a->n);
-  pl.k = k;
-  pl.c = std::min(coalesce_bits(dtype), k);
-  SweepDev sw;
-  std::memset(&sw, 0, sizeof(sw));
-  sw.k = k;
-  sw.c = pl.c;
-  sw.h1 = (k - pl.c + 1) / 2;
-  for (int b = 0; b < k; ++b) sw.tbits[b] = (int8_t)b;
-  for (int b = k; b < a->n; ++b) sw.nbits[b - k] = (int8_t)b;
-  sw.n_nontile = a->n - k;
-  sw.flags = SW_PREP | SW_WRITE_PSI;
-  pl.sweeps.push_back(sw);
-  pl.nvec.push_back(1);
-  OpDev dummy;
-  std::memset(&dummy, 0, sizeof(dummy));
-  pl.hops.push_back(dummy);
-  return run_plan(a, &pl, dtype, nullptr, psi, nullptr, nullptr, batch, nullptr, nullptr, (cudaStream_t)stream);
+  Plan* pl;
+  if ((s = get_plan(a, 3, dtype, 0, pl)) != HUB_OK) return s;
+  return run_plan(a, pl, dtype, nullptr, psi, nullptr, nullptr, batch, nullptr, nullptr, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------
 // compute calls
 // ---------------------------------------------------------------------------
-
 extern "C" hub_status energy(ans_t a, const double* theta, void* psi, double* E, int32_t dtype, int64_t batch,
                              uint32_t flags, hub_stream_t stream) {
   hub_status s = check_call(a, dtype, batch);
@@ -1089,7 +798,8 @@ extern "C" hub_status ans_plan_describe(ans_t a, int32_t which, int32_t dtype, u
   out.push_back((int64_t)pl->sweeps.size());
   for (size_t i = 0; i < pl->sweeps.size(); ++i) {
     out.push_back((int64_t)pl->tiles[i]);
-    out.push_back((int64_t)pl->sweeps[i].flags);
+    const int nph = pl->sweeps[i].phase_end - pl->sweeps[i].phase_begin;
+    out.push_back((int64_t)pl->sweeps[i].flags | ((int64_t)nph << 16));
     out.push_back((int64_t)pl->seq_ids[i].size());
     for (int id : pl->seq_ids[i]) out.push_back(id);
   }

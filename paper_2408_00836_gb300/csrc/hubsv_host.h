@@ -1,0 +1,108 @@
+// Host-side internal types of the Hubbard VQE statevector engine: handles,
+// the operation sequence handed to the planner, and plans.
+#pragma once
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "hubsv.h"
+#include "hubsv_internal.h"
+
+namespace hubsv {
+
+hub_status fail(hub_status s, const std::string& m);
+hub_status cuda_fail(cudaError_t e, const char* what);
+
+#define HUB_CUDA(call, what)                             \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return ::hubsv::cuda_fail(e_, what); \
+  } while (0)
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { if (p) cudaFree(p); }
+  hub_status ensure(size_t n, const char* what);
+  template <typename T>
+  hub_status upload(const std::vector<T>& v, const char* what) {
+    hub_status s = ensure(std::max<size_t>(v.size() * sizeof(T), 16), what);
+    if (s != HUB_OK) return s;
+    if (!v.empty()) HUB_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), what);
+    return HUB_OK;
+  }
+};
+
+// Host-level operation before tiling.
+struct SeqOp {
+  uint8_t kind = 0, flags = 0;
+  int p = -1, q = -1;       // modes (hop-type), p < q
+  int gate = -1, hterm = -1, slot = -1, diag = -1;
+  uint64_t support = 0;     // modes the operation reads or changes
+  bool diagonal = false;
+  int cls = 0;              // 0 forward, 1 measure, 2 lam, 3 backward
+};
+
+struct Plan {
+  std::vector<SweepDev> sweeps;
+  std::vector<int> nvec;                  // 1 or 2 per sweep
+  std::vector<OpDev> hops;                // operations of all phases
+  std::vector<PhaseDev> hphases;          // phases of all sweeps
+  std::vector<uint64_t> tiles;
+  std::vector<std::vector<int>> seq_ids;  // sequence index of each op, per sweep
+  bool uploaded = false;
+  DevBuf ops, phases;
+  int k = 0;
+  double bytes_per_state = 0;
+};
+
+}  // namespace hubsv
+
+struct hub_model {
+  int L = 0, n = 0, s = 0, layout = 0;
+  std::vector<int> up, dn;
+  std::vector<std::pair<int, int>> bonds;
+  std::vector<double> t, U, V;
+  int n_up = 0, n_dn = 0;
+};
+
+struct hub_ansatz {
+  std::vector<hub_model*> models;
+  int n_inst = 0, L = 0, n = 0, P = 0, s = 0, layout = 0;
+  uint64_t upmask = 0;
+  std::vector<hubsv::SeqOp> fwd;         // forward factors in order
+  struct HTerm { int p, q; };
+  std::vector<HTerm> hterms;             // H hop terms: 2*bond + spin
+  int h_diag = -1;                       // DiagOp index of H's diagonal
+  std::vector<hubsv::DiagOpDev> diag_ops;
+  std::vector<int32_t> gate_param;
+  std::vector<double> gate_t;            // [n_inst][n_gates]
+  std::vector<int32_t> tab_param;        // [n_tab]
+  std::vector<double> tab_val;           // [n_inst][n_tab]
+  std::vector<double> hcoef;             // [n_inst][n_hterms]
+  std::vector<double> real_tabs;         // [n_inst][real_stride]
+  int n_gates = 0, n_tab = 0, real_stride = 0;
+  hubsv::DevBuf d_gate_param, d_gate_t, d_tab_param, d_tab_val, d_hcoef, d_real, d_diag;
+  hubsv::DevBuf d_real32;                // FP32 copy of real_tabs
+  hubsv::DevBuf d_sd, d_sd32;            // Slater determinant tables (FP64, FP32)
+  int prep_kind = -1;
+  uint64_t neel_x0 = 0;
+  hubsv::DevBuf d_coef[2], d_phase[2], d_acc;
+  std::map<int, hubsv::Plan*> plans;     // key = which*16 + dtype*4 + flags
+  int tile_override[2] = {0, 0};
+  bool dev_ready = false;
+  struct ProfRec { cudaEvent_t e0, e1; int nv, dtype; double bytes; };
+  bool prof = false;
+  std::vector<ProfRec> prof_recs;
+  void prof_clear();
+  ~hub_ansatz();
+};
+
+namespace hubsv {
+uint64_t diag_support(const hub_ansatz* a, int di);
+hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*& out);
+}  // namespace hubsv

@@ -8,7 +8,9 @@ namespace hubsv {
 
 constexpr int kMaxQubits = 32;
 constexpr int kMaxTileBits = 14;
-constexpr int kThreads = 256;
+constexpr int kLaneBits = 5;        // lanes of a warp <-> 5 tile bits
+constexpr int kMaxRegBits = 5;      // amplitudes per thread = 2^r, r <= 5
+constexpr int kMaxWarpBits = 5;
 
 // One operation applied to a tile.  Operations are the factors of the ansatz
 // (Eq. 7), the terms of H (Eqs. 1, 2, 15, 16) and the adjoint steps of
@@ -29,14 +31,36 @@ enum OpFlag : uint8_t {
   OPF_LAM = 2,   // apply the factor to lam as well as psi
 };
 
-struct OpDev {
-  uint8_t kind, flags, p, q;    // p < q: tile-local bit positions (hop ops)
-  uint32_t bmask_local;         // Jordan-Wigner string on tile-local bits
-  uint64_t bmask_global;        // Jordan-Wigner string on non-tile bits
-  int32_t gate;                 // OP_GIV: coefficient-table column
-  int32_t hterm;                // hop ops: column of the -t table (per instance)
+// An operation inside a register phase.  Hop-type operations act on the
+// register slots a < b (bit a / b of the per-thread element index e).  The
+// Jordan-Wigner string is split three ways: slots (bm_slots, over e), the
+// thread's other tile bits (bm_local, over the tile-local index) and the
+// non-tile bits (bm_global, over the state index).
+struct alignas(16) OpDev {      // 32 bytes: read as two 16-byte words
+  uint8_t kind, flags, a, b;
+  uint32_t sgn;                 // bit e = parity(e & JW string on the slots)
+  uint32_t bm_local;            // JW string on the thread's other tile bits
+  uint32_t bm_global;           // JW string on the non-tile bits (state index)
+  int32_t idx;                  // OP_GIV: coefficient column; other hop ops:
+                                // column of the -t table; diagonal ops: DiagOp
   int32_t slot;                 // OP_GRAD_*: accumulator slot (parameter)
-  int32_t diag;                 // diagonal ops: index into the DiagOp array
+  int32_t pad[2];
+};
+
+// A register phase: each thread holds the 2^r amplitudes whose tile-local
+// index is base(thread) | dep[e], dep[e] = the tile bits of the slots set in
+// e; base takes the lane bits from the lane index and the warp bits from the
+// warp index.  Per slot j the plan keeps the state-index bit (so[j]) and the
+// swizzled exchange index (ss[j]) of its tile bit; both maps are linear, so
+// an element's offsets are XORs of slot values and the thread's base part.
+struct PhaseDev {
+  int32_t op_begin, op_end;
+  uint8_t lane[kLaneBits];
+  uint8_t nwarp;
+  uint8_t warp[kMaxWarpBits + 1];
+  uint8_t pad[4];
+  uint32_t so[kMaxRegBits + 1];
+  uint32_t ss[kMaxRegBits + 1];
 };
 
 // A diagonal operator d(x) = sum_bytes X[byte of x] + sum_bytes Y[byte of y]
@@ -70,10 +94,11 @@ enum SweepFlag : uint32_t {
 };
 
 struct SweepDev {
-  int32_t op_begin, op_end;
+  int32_t phase_begin, phase_end;
+  int32_t op_begin, op_end;       // operations of all its phases
   int32_t k;                      // log2 tile size
-  int32_t c;                      // low contiguous bits (tile bits 0..c-1)
-  int32_t h1;                     // bits in the first offset table
+  int32_t r;                      // register bits per thread
+  int32_t w;                      // warp bits (threads = 32 << w)
   uint32_t flags;
   int8_t tbits[kMaxTileBits];     // tile bit positions, ascending
   int8_t nbits[kMaxQubits];       // non-tile bit positions, ascending
@@ -86,6 +111,7 @@ struct PrepDev {
   int32_t layout;          // 0 blocked (s == L), 1 interleaved (s == 1)
   uint64_t neel_x0;
   const double* sd;        // [n_inst][2][2^L] determinant tables
+  const float* sd32;       // the same in FP32 (complex64 path)
 };
 
 struct KernelArgs {
@@ -93,6 +119,7 @@ struct KernelArgs {
   void* lam;
   void* ckpt;
   const OpDev* ops;
+  const PhaseDev* phases;
   const DiagOpDev* diag_ops;
   const double* theta;
   int32_t P;                       // parameters per batch element
@@ -101,6 +128,7 @@ struct KernelArgs {
   const double* hcoef;             // [n_inst][n_hterms]: -t of each hop term
   int32_t n_hterms;
   const double* real_tabs;         // [n_inst][real_stride]
+  const float* real_tabs32;        // the same in FP32 (complex64 path)
   int32_t real_stride;
   const void* phase_tabs;          // [batch][phase_stride] R2
   int32_t phase_stride;
@@ -115,6 +143,25 @@ struct KernelArgs {
   int32_t slot_E, slot_N;
   PrepDev prep;
 };
+
+// Shared-memory layout of a sweep: exchange buffer(s) for the tile (none
+// when the sweep has a single phase), the CTA accumulators, and copies of
+// the sweep's phases and operations.
+inline size_t sweep_smem_bytes(int dtype, int nv, int k, int n_slots, int n_phases, int n_ops) {
+  const size_t amp = dtype == 0 ? 8 : 16;
+  const int nbuf = n_phases > 1 ? nv : 0;
+  size_t s = (size_t)nbuf * (amp << k) + 8 * (size_t)n_slots + sizeof(PhaseDev) * (size_t)n_phases;
+  s = (s + 15) & ~(size_t)15;                  // operations are read as 16-byte words
+  return s + sizeof(OpDev) * (size_t)n_ops;
+}
+
+// Swizzle of tile-local indices in the exchange buffer: XOR the low bits
+// with a fold of the higher nibbles, so that register phases whose lanes
+// run over high tile bits still hit distinct banks.
+__host__ __device__ inline uint32_t swz(uint32_t l, int dtype) {
+  const uint32_t f = (l >> 4) ^ (l >> 8) ^ (l >> 12);
+  return l ^ (f & (dtype == 0 ? 15u : 7u));
+}
 
 }  // namespace hubsv
 
@@ -131,6 +178,12 @@ cudaError_t launch_zero(double* p, int64_t n, cudaStream_t st);
 cudaError_t launch_finalize(const double* acc, int n_slots, int P, int slot_E,
                             double* E, double* grad, int64_t batch, cudaStream_t st);
 int sweep_max_smem_optin();
-cudaError_t sweep_set_smem(int dtype, int nv, size_t smem);
+cudaError_t sweep_set_smem(int dtype, int nv, int r, size_t smem);
+int sweep_regs(int dtype, int nv, int r);
 int device_sm_count();
+// Register bits the kernels are compiled for: r in [1, max_r(dtype, nv)].
+inline int max_reg_bits(int dtype, int nv) {
+  (void)nv;
+  return dtype == 0 ? 4 : 3;
+}
 }  // namespace hubsv

@@ -1,0 +1,392 @@
+// Planner of the Hubbard VQE statevector engine.
+//
+// The work of one call is a sequence of operations on amplitude vectors:
+// the ansatz factors of Eq. 7 in order, then the terms of H (energy of
+// Eq. 4, or lam = H psi), then for the gradient each factor's reduction
+// 2 Im <lam|G|psi> and its inverse, in reverse order (Sec. 2.1).  Two
+// operations commute when they act on disjoint modes (fermionic bilinears on
+// disjoint modes commute) or when both are diagonal.  The planner reorders
+// the sequence within those rules into
+//
+//   sweeps  -- passes over the vector; a sweep holds a tile of k index bits
+//              (always including the 5 lowest) and runs every operation whose
+//              modes lie in the tile;
+//   phases  -- within a sweep, groups of operations whose modes are r of the
+//              tile bits, run in registers (one thread holds 2^r amplitudes).
+//
+// Both levels use the same greedy scan: take operations in sequence order,
+// run one if it commutes with everything skipped before it and fits, skip it
+// otherwise.  For sweeps several candidate tiles are scanned and the one that
+// runs the most operations wins.
+#include <algorithm>
+#include <cstring>
+
+#include "hubsv_host.h"
+
+namespace hubsv {
+
+namespace {
+
+inline int popc64(uint64_t x) { return __builtin_popcountll(x); }
+
+uint64_t between_mask(int p, int q) {  // bits strictly between p < q
+  return ((1ull << q) - 1ull) & ~((1ull << (p + 1)) - 1ull);
+}
+
+// Call kinds: 0 energy, 1 energy + gradient, 2 lam = H psi, 3 initial state
+// only (no operations).
+std::vector<SeqOp> build_sequence(const hub_ansatz* a, int which) {
+  std::vector<SeqOp> seq;
+  if (which == 3) return seq;
+  if (which != 2) seq = a->fwd;
+  const uint64_t hsup = diag_support(a, a->h_diag);
+  for (size_t t = 0; t < a->hterms.size(); ++t) {
+    SeqOp op;
+    op.kind = which == 0 ? OP_MEAS_HOP : OP_LAM_HOP;
+    op.p = a->hterms[t].p;
+    op.q = a->hterms[t].q;
+    op.hterm = (int)t;
+    op.support = (1ull << op.p) | (1ull << op.q);
+    op.cls = which == 0 ? 1 : 2;
+    seq.push_back(op);
+  }
+  {
+    SeqOp op;
+    op.kind = which == 0 ? OP_MEAS_DIAG : OP_LAM_DIAG;
+    op.diag = a->h_diag;
+    op.diagonal = true;
+    op.support = hsup;
+    op.cls = which == 0 ? 1 : 2;
+    seq.push_back(op);
+  }
+  if (which == 1) {
+    for (int i = (int)a->fwd.size() - 1; i >= 0; --i) {
+      SeqOp g = a->fwd[i];
+      g.kind = g.kind == OP_GIV ? OP_GRAD_HOP : OP_GRAD_DIAG;
+      g.cls = 3;
+      seq.push_back(g);
+      SeqOp v = a->fwd[i];
+      v.flags = OPF_INV | OPF_LAM;
+      v.cls = 3;
+      seq.push_back(v);
+    }
+  }
+  return seq;
+}
+
+bool modifies_psi(const SeqOp& op) { return op.kind == OP_GIV || op.kind == OP_DIAG; }
+bool uses_lam(const SeqOp& op) {
+  return op.kind == OP_LAM_HOP || op.kind == OP_LAM_DIAG || op.kind == OP_GRAD_HOP ||
+         op.kind == OP_GRAD_DIAG || (op.flags & OPF_LAM);
+}
+bool modifies_lam(const SeqOp& op) {
+  return op.kind == OP_LAM_HOP || op.kind == OP_LAM_DIAG || (modifies_psi(op) && (op.flags & OPF_LAM));
+}
+
+struct Scan {
+  uint64_t tile = 0;
+  std::vector<int> exec, rest;
+};
+
+// One greedy scan.  need(op) gives the bits an operation needs (0 for
+// diagonal ones); the tile starts at init and may grow to `cap` bits using
+// only `allowed` bits.  Lam-building operations wait for the whole forward
+// circuit.
+template <typename NeedFn>
+Scan scan(const std::vector<SeqOp>& seq, const std::vector<int>& order, uint64_t init, uint64_t allowed,
+          int cap, NeedFn need) {
+  Scan s;
+  s.tile = init;
+  uint64_t s_any = 0, s_diag = 0;
+  bool fwd_skipped = false;
+  for (int idx : order) {
+    const SeqOp& op = seq[idx];
+    bool ok = !((op.support & s_any) || (!op.diagonal && (op.support & s_diag)));
+    if (op.cls == 2 && fwd_skipped) ok = false;
+    if (ok) {
+      const uint64_t nd = need(op);
+      if (nd & ~allowed) ok = false;
+      else {
+        const uint64_t nt = s.tile | nd;
+        if (popc64(nt) <= cap) s.tile = nt;
+        else ok = false;
+      }
+    }
+    if (ok) {
+      s.exec.push_back(idx);
+    } else {
+      s.rest.push_back(idx);
+      if (op.diagonal) s_diag |= op.support; else s_any |= op.support;
+      if (op.cls == 0) fwd_skipped = true;
+    }
+  }
+  return s;
+}
+
+// GF(2) rank of up to 5 columns of 4-bit values.
+int rank_gf2(std::vector<uint32_t> cols) {
+  int r = 0;
+  for (int bit = 3; bit >= 0; --bit) {
+    int piv = -1;
+    for (size_t i = 0; i < cols.size(); ++i)
+      if (cols[i] >> bit & 1) { piv = (int)i; break; }
+    if (piv < 0) continue;
+    const uint32_t pv = cols[piv];
+    cols.erase(cols.begin() + piv);
+    for (auto& c : cols)
+      if (c >> bit & 1) c ^= pv;
+    ++r;
+  }
+  return r;
+}
+
+// Lane bits of a middle phase: 5 of the free tile bits whose first 4 (c64)
+// or 3 (c128) columns of the swizzle map are independent, so a warp's
+// shared-memory accesses hit distinct banks.
+void choose_lanes(uint32_t free_bits, int dtype, uint8_t* lanes, uint8_t* warps, int& nwarp) {
+  std::vector<int> fb;
+  for (int b = 0; b < 32; ++b)
+    if (free_bits >> b & 1) fb.push_back(b);
+  const int need = dtype == 0 ? 4 : 3;
+  const uint32_t m = dtype == 0 ? 15u : 7u;
+  std::vector<int> best(fb.begin(), fb.begin() + kLaneBits);
+  const int nfb = (int)fb.size();
+  bool found = false;
+  // combinations of 5 of the free bits, the first `need` checked for rank
+  std::vector<int> idx(kLaneBits);
+  for (int i = 0; i < kLaneBits; ++i) idx[i] = i;
+  while (!found) {
+    std::vector<int> cand;
+    for (int i : idx) cand.push_back(fb[i]);
+    // try orderings that put an independent set first
+    std::vector<int> perm(cand);
+    std::sort(perm.begin(), perm.end());
+    do {
+      std::vector<uint32_t> cols;
+      for (int j = 0; j < need; ++j) cols.push_back(swz(1u << perm[j], dtype) & m);
+      if (rank_gf2(cols) == need) { best = perm; found = true; break; }
+    } while (std::next_permutation(perm.begin(), perm.end()));
+    // next combination
+    int i = kLaneBits - 1;
+    while (i >= 0 && idx[i] == nfb - kLaneBits + i) --i;
+    if (i < 0) break;
+    ++idx[i];
+    for (int j = i + 1; j < kLaneBits; ++j) idx[j] = idx[j - 1] + 1;
+  }
+  uint32_t used = 0;
+  for (int j = 0; j < kLaneBits; ++j) { lanes[j] = (uint8_t)best[j]; used |= 1u << best[j]; }
+  nwarp = 0;
+  for (int b : fb)
+    if (!(used >> b & 1)) warps[nwarp++] = (uint8_t)b;
+}
+
+}  // namespace
+
+hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*& out) {
+  const int n = a->n;
+  if (n < kLaneBits + 1) return fail(HUB_EUNSUPPORTED, "need at least 6 qubits (3 sites)");
+  int k = a->tile_override[dtype] ? a->tile_override[dtype] : (dtype == HUB_C64 ? 13 : 12);
+  k = std::min(k, n);
+  const uint64_t cmask = (1ull << kLaneBits) - 1ull;
+  const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
+  uint64_t upm = 0, dnm = 0;
+  for (int i = 0; i < a->L; ++i) {
+    upm |= 1ull << a->models[0]->up[i];
+    dnm |= 1ull << a->models[0]->dn[i];
+  }
+  std::vector<SeqOp> seq = build_sequence(a, which);
+  std::vector<int> remaining(seq.size());
+  for (size_t i = 0; i < seq.size(); ++i) remaining[i] = (int)i;
+  auto need_modes = [](const SeqOp& op) -> uint64_t {
+    return op.diagonal ? 0ull : ((1ull << op.p) | (1ull << op.q));
+  };
+  // candidate tiles: windows of consecutive modes, and of consecutive modes of one spin
+  std::vector<uint64_t> windows;
+  for (int s0 = 0; s0 < n; ++s0) {
+    uint64_t t = cmask;
+    for (int b = s0; b < n && popc64(t) < k; ++b) t |= 1ull << b;
+    windows.push_back(t);
+  }
+  for (uint64_t sm : {upm, dnm}) {
+    std::vector<int> ms;
+    for (int b = 0; b < n; ++b)
+      if (sm >> b & 1) ms.push_back(b);
+    for (size_t s0 = 0; s0 < ms.size(); ++s0) {
+      uint64_t t = cmask;
+      for (size_t j = s0; j < ms.size() && popc64(t) < k; ++j) t |= 1ull << ms[j];
+      windows.push_back(t);
+    }
+  }
+  struct PS { uint64_t tile; std::vector<int> ops; };
+  std::vector<PS> sweeps;
+  while (!remaining.empty()) {
+    Scan best = scan(seq, remaining, cmask, all, k, need_modes);
+    auto consider = [&](Scan&& s) { if (s.exec.size() > best.exec.size()) best = std::move(s); };
+    consider(scan(seq, remaining, cmask, cmask | upm, k, need_modes));
+    consider(scan(seq, remaining, cmask, cmask | dnm, k, need_modes));
+    for (uint64_t t : windows) consider(scan(seq, remaining, t, t, k, need_modes));
+    if (best.exec.empty()) return fail(HUB_EUNSUPPORTED, "planner made no progress");
+    uint64_t tile = best.tile;
+    for (int b = 0; b < n && popc64(tile) < k; ++b) tile |= 1ull << b;   // pad with low bits
+    sweeps.push_back({tile, best.exec});
+    remaining.swap(best.rest);
+  }
+  if (sweeps.empty()) sweeps.push_back({(1ull << k) - 1ull, {}});   // initial state only
+
+  Plan* pl = new Plan();
+  pl->k = k;
+  const bool prep = which == 3 || (flags & HUB_FLAG_PREP_FUSED) != 0;
+  const bool keep = which == 3 || (flags & HUB_FLAG_KEEP_STATE) != 0;
+  bool lam_live = false;
+  const double amp = dtype == HUB_C64 ? 8.0 : 16.0;
+  double bytes = 0.0;
+  for (size_t si = 0; si < sweeps.size(); ++si) {
+    const PS& ps = sweeps[si];
+    // sweep flags
+    bool mod_psi = false, use_lam = false, mod_lam = false;
+    for (int idx : ps.ops) {
+      mod_psi = mod_psi || modifies_psi(seq[idx]);
+      use_lam = use_lam || uses_lam(seq[idx]);
+      mod_lam = mod_lam || modifies_lam(seq[idx]);
+    }
+    const bool first = si == 0, last = si + 1 == sweeps.size();
+    uint32_t f = 0;
+    if (first && prep && which != 2) f |= SW_PREP; else f |= SW_READ_PSI;
+    if ((!last || keep) && (mod_psi || (f & SW_PREP)) && which != 2) f |= SW_WRITE_PSI;
+    if (use_lam || (lam_live && mod_lam)) {
+      f |= SW_HAS_LAM;
+      if (lam_live) f |= SW_READ_LAM;
+      if (mod_lam && (!last || which == 2)) f |= SW_WRITE_LAM;
+      lam_live = true;
+    }
+    const int nv = (f & SW_HAS_LAM) ? 2 : 1;
+    const int r = std::min(max_reg_bits(dtype, nv), k - kLaneBits);
+    SweepDev sw;
+    std::memset(&sw, 0, sizeof(sw));
+    sw.k = k;
+    sw.r = r;
+    sw.w = k - kLaneBits - r;
+    sw.flags = f;
+    int nt = 0, nn = 0;
+    int localpos[64];
+    for (int b = 0; b < n; ++b) {
+      if (ps.tile >> b & 1) { localpos[b] = nt; sw.tbits[nt++] = (int8_t)b; }
+      else { localpos[b] = -1; sw.nbits[nn++] = (int8_t)b; }
+    }
+    sw.n_nontile = nn;
+    // ---- register phases ----
+    const uint32_t low = (1u << kLaneBits) - 1u;
+    const uint32_t tmask = (k >= 32) ? ~0u : ((1u << k) - 1u);
+    auto need_local = [&](const SeqOp& op) -> uint64_t {
+      return op.diagonal ? 0ull : ((1ull << localpos[op.p]) | (1ull << localpos[op.q]));
+    };
+    struct PH { uint32_t S; std::vector<int> ops; };
+    std::vector<PH> phs;
+    std::vector<int> rem = ps.ops;
+    while (!rem.empty()) {
+      const uint32_t allowed = phs.empty() ? (tmask & ~low) : tmask;
+      Scan s = scan(seq, rem, 0, allowed, r, need_local);
+      // also try register sets seeded with each of the next operations' bits
+      int tried = 0;
+      for (size_t j = 0; j < rem.size() && tried < 16; ++j) {
+        const SeqOp& op = seq[rem[j]];
+        if (op.diagonal) continue;
+        const uint64_t sd = need_local(op);
+        if (sd & ~(uint64_t)allowed) continue;
+        ++tried;
+        Scan c = scan(seq, rem, sd, allowed, r, need_local);
+        if (c.exec.size() > s.exec.size()) s = std::move(c);
+      }
+      if (s.exec.empty()) {
+        if (phs.empty()) { phs.push_back({0u, {}}); continue; }   // first phase keeps the lanes low
+        delete pl;
+        return fail(HUB_EUNSUPPORTED, "phase planner made no progress");
+      }
+      phs.push_back({(uint32_t)s.tile, s.exec});
+      rem.swap(s.rest);
+    }
+    if (phs.empty()) phs.push_back({0u, {}});
+    if (phs.back().S & low) phs.push_back({0u, {}});
+    sw.phase_begin = (int)pl->hphases.size();
+    sw.op_begin = (int)pl->hops.size();
+    std::vector<int> exec_order;
+    for (const PH& P : phs) exec_order.insert(exec_order.end(), P.ops.begin(), P.ops.end());
+    for (size_t pi = 0; pi < phs.size(); ++pi) {
+      PH& P = phs[pi];
+      const bool edge = pi == 0 || pi + 1 == phs.size();
+      // pad the register set to r bits (never with the low bits in edge phases)
+      for (int bit = k - 1; bit >= 0 && popc64(P.S) < r; --bit)
+        if (!(P.S >> bit & 1) && !(edge && (low >> bit & 1))) P.S |= 1u << bit;
+      for (int bit = 0; bit < k && popc64(P.S) < r; ++bit) P.S |= 1u << bit;
+      PhaseDev pd;
+      std::memset(&pd, 0, sizeof(pd));
+      int slot_of[32];
+      int ns = 0;
+      std::vector<int> sb;
+      for (int bit = 0; bit < k; ++bit) {
+        slot_of[bit] = -1;
+        if (P.S >> bit & 1) { slot_of[bit] = ns++; sb.push_back(bit); }
+      }
+      for (int j = 0; j < r; ++j) {
+        pd.so[j] = 1u << sw.tbits[sb[j]];
+        pd.ss[j] = swz(1u << sb[j], dtype);
+      }
+      const uint32_t freeb = tmask & ~P.S;
+      int nw = 0;
+      if (edge && !(P.S & low)) {
+        for (int j = 0; j < kLaneBits; ++j) pd.lane[j] = (uint8_t)j;
+        for (int bit = kLaneBits; bit < k; ++bit)
+          if (freeb >> bit & 1) pd.warp[nw++] = (uint8_t)bit;
+      } else {
+        choose_lanes(freeb, dtype, pd.lane, pd.warp, nw);
+      }
+      pd.nwarp = (uint8_t)nw;
+      pd.op_begin = (int)pl->hops.size();
+      for (int idx : P.ops) {
+        const SeqOp& op = seq[idx];
+        OpDev d;
+        std::memset(&d, 0, sizeof(d));
+        d.kind = op.kind;
+        d.flags = op.flags;
+        d.idx = op.kind == OP_GIV ? op.gate : (op.diagonal ? op.diag : op.hterm);
+        d.slot = op.slot;
+        if (!op.diagonal) {
+          const int lp = localpos[op.p], lq = localpos[op.q];
+          d.a = (uint8_t)slot_of[lp];
+          d.b = (uint8_t)slot_of[lq];
+          const uint64_t bm = between_mask(op.p, op.q);
+          uint32_t bs = 0, bl = 0;
+          for (int b = 0; b < n; ++b) {
+            if (!(bm >> b & 1) || localpos[b] < 0) continue;
+            const int lb = localpos[b];
+            if (slot_of[lb] >= 0) bs |= 1u << slot_of[lb];
+            else bl |= 1u << lb;
+          }
+          d.bm_local = bl;
+          uint32_t sg = 0;
+          for (int e = 0; e < (1 << r); ++e)
+            if (__builtin_popcount((uint32_t)e & bs) & 1) sg |= 1u << e;
+          d.sgn = sg;
+          d.bm_global = (uint32_t)(bm & ~ps.tile);
+        }
+        pl->hops.push_back(d);
+      }
+      pd.op_end = (int)pl->hops.size();
+      pl->hphases.push_back(pd);
+    }
+    sw.phase_end = (int)pl->hphases.size();
+    sw.op_end = (int)pl->hops.size();
+    bytes += amp * (double)(1ull << n) *
+             (((f & SW_READ_PSI) ? 1 : 0) + ((f & SW_WRITE_PSI) ? 1 : 0) +
+              ((f & SW_READ_LAM) ? 1 : 0) + ((f & SW_WRITE_LAM) ? 1 : 0));
+    pl->sweeps.push_back(sw);
+    pl->nvec.push_back(nv);
+    pl->tiles.push_back(ps.tile);
+    pl->seq_ids.push_back(exec_order);
+  }
+  pl->bytes_per_state = bytes;
+  out = pl;
+  return HUB_OK;
+}
+
+}  // namespace hubsv

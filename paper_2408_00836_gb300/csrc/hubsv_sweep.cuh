@@ -1,0 +1,535 @@
+// The sweep kernel of the Hubbard VQE statevector engine (sm_103a),
+// included by the four instantiation units hubsv_sweep_{f1,f2,d1,d2}.cu.
+//
+// One kernel, sweep_kernel, does all amplitude work.  A sweep streams the
+// whole 2^n (x batch) amplitude vector once, one tile of 2^k amplitudes at a
+// time.  A tile holds every amplitude whose index agrees with the tile's
+// base on the non-tile bits; the tile bits always include the 5 lowest bits,
+// so a warp loads and stores runs of 32 contiguous amplitudes (256 B in c64).
+//
+// Inside a tile the amplitudes live in registers: in a register phase each
+// thread holds the 2^r amplitudes that differ in r chosen tile bits (its
+// register slots), and every operation whose bits are register slots runs
+// without touching memory.  Between phases the tile is exchanged through
+// shared memory (XOR-swizzled against bank conflicts) to bring other bits
+// into the register slots.  The first and last phase put the 5 low bits on
+// the lanes, so global loads and stores go straight to and from registers.
+//
+// Operations (chosen and ordered by the host planner):
+//  * OP_GIV: the factor exp(-i theta G) of one hopping term of Eq. 7,
+//    G = -t (a+_p a_q + h.c.).  On each pair (x, x') with b_p != b_q it is
+//    the 2x2 rotation [c, i s sigma; i s sigma, c], c = cos(theta t),
+//    sigma = sin(theta t), s = (-1)^popcount(x & bits strictly between p and
+//    q) -- the Jordan-Wigner string, from popcounts of masked indices.
+//  * OP_DIAG: the diagonal factors of Eq. 7 (on-site U, NN V, potential,
+//    Rz) as a phase looked up from per-byte tables.
+//  * OP_MEAS_* / OP_LAM_*: the energy of Eq. 4 term by term (and lam = H psi
+//    for the adjoint pass) without materialising H psi in HBM unless the
+//    gradient needs it.
+//  * OP_GRAD_*: the per-parameter reductions 2 Im <lam|G|psi> of the
+//    adjoint recursion of Sec. 2.1.
+//
+// Reductions accumulate per thread in the working precision within one tile,
+// are reduced per warp in FP64 and summed per CTA in shared memory; each CTA
+// adds its totals to the global FP64 accumulators once per batch element.
+#pragma once
+#include "hubsv_internal.h"
+
+namespace hubsv {
+
+template <typename R> struct CT;
+template <> struct CT<float> { using T2 = float2; static constexpr int DT = 0; };
+template <> struct CT<double> { using T2 = double2; static constexpr int DT = 1; };
+
+template <typename T2, typename R>
+__device__ __forceinline__ T2 mk(R x, R y) { T2 r; r.x = x; r.y = y; return r; }
+
+template <typename T2>
+__device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+  T2 r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+
+__device__ __forceinline__ uint32_t deposit_bits(uint32_t v, const int8_t* pos, int cnt) {
+  uint32_t r = 0;
+  for (int i = 0; i < cnt; ++i) r |= ((v >> i) & 1u) << pos[i];
+  return r;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Add a per-thread partial to acc[slot] (shared).  Called uniformly by the
+// whole CTA.
+__device__ __forceinline__ void cta_add(double* acc, int slot, double v) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(&acc[slot], v);
+}
+
+// XOR of the slot values m[j] over the set bits j of e (e is a constant
+// after unrolling, so this folds to at most a few logic operations).
+template <int RB>
+__device__ __forceinline__ uint32_t comb(const uint32_t (&m)[RB], int e) {
+  uint32_t v = 0;
+#pragma unroll
+  for (int j = 0; j < RB; ++j)
+    if ((e >> j) & 1) v ^= m[j];
+  return v;
+}
+
+// Real value of a diagonal operator at x (see DiagOpDev), in the working
+// precision R (tables stored in R).
+template <typename R>
+__device__ __forceinline__ R diag_real(const DiagOpDev& d, const R* tab, uint32_t x, int s,
+                                      uint32_t upmask) {
+  R v = 0;
+  for (int i = 0; i < d.has_x; ++i) v += tab[i * 256 + ((x >> (8 * i)) & 255u)];
+  const uint32_t y = x & (x >> s) & upmask;
+  for (int i = 0; i < d.has_y; ++i) v += tab[1024 + i * 256 + ((y >> (8 * i)) & 255u)];
+  const R* vb = tab + 2048;
+  for (int b = 0; b < d.n_vb; ++b) {
+    const int u1 = d.vb_up[b], u2 = d.vb_up2[b];
+    const int ni = (int)((x >> u1) & 1u) + (int)((x >> (u1 + s)) & 1u);
+    const int nj = (int)((x >> u2) & 1u) + (int)((x >> (u2 + s)) & 1u);
+    v += vb[b] * (R)(ni * nj);
+  }
+  return v;
+}
+
+// Phase exp(-i theta d(x)) from the per-batch-element phase tables.
+template <typename T2>
+__device__ __forceinline__ T2 diag_phase(const DiagOpDev& d, const T2* tab, uint32_t x, int s,
+                                         uint32_t upmask) {
+  T2 ph; ph.x = 1; ph.y = 0;
+  for (int i = 0; i < d.has_x; ++i) ph = cmul(ph, tab[i * 256 + ((x >> (8 * i)) & 255u)]);
+  const uint32_t y = x & (x >> s) & upmask;
+  for (int i = 0; i < d.has_y; ++i) ph = cmul(ph, tab[1024 + i * 256 + ((y >> (8 * i)) & 255u)]);
+  if (d.n_vb > 0) {
+    const T2* vt = tab + 2048;
+    if (d.v_uniform) {
+      int K = 0;
+      for (int b = 0; b < d.n_vb; ++b) {
+        const int u1 = d.vb_up[b], u2 = d.vb_up2[b];
+        const int ni = (int)((x >> u1) & 1u) + (int)((x >> (u1 + s)) & 1u);
+        const int nj = (int)((x >> u2) & 1u) + (int)((x >> (u2 + s)) & 1u);
+        K += ni * nj;
+      }
+      ph = cmul(ph, vt[K]);
+    } else {
+      for (int b = 0; b < d.n_vb; ++b) {
+        const int u1 = d.vb_up[b], u2 = d.vb_up2[b];
+        const int ni = (int)((x >> u1) & 1u) + (int)((x >> (u1 + s)) & 1u);
+        const int nj = (int)((x >> u2) & 1u) + (int)((x >> (u2 + s)) & 1u);
+        const int e = ni * nj;
+        if (e) ph = cmul(ph, vt[b * 5 + e]);
+      }
+    }
+  }
+  return ph;
+}
+
+// Compress the bits of x at positions 0, 2, 4, ... into consecutive bits.
+__device__ __forceinline__ uint32_t compress_even(uint32_t x) {
+  x &= 0x55555555u;
+  x = (x | (x >> 1)) & 0x33333333u;
+  x = (x | (x >> 2)) & 0x0f0f0f0fu;
+  x = (x | (x >> 4)) & 0x00ff00ffu;
+  x = (x | (x >> 8)) & 0x0000ffffu;
+  return x;
+}
+
+// Initial state amplitude at x (state-local index) for instance inst, from
+// the determinant tables stored in the working precision R.
+template <typename R>
+__device__ __forceinline__ R prep_amp(const PrepDev& p, const R* sdt, uint32_t x, int inst) {
+  if (p.kind == 1) return x == (uint32_t)p.neel_x0 ? (R)1 : (R)0;
+  uint32_t oa, ob;
+  int sign = 0;
+  if (p.layout == 0) {
+    oa = x & ((1u << p.L) - 1u);
+    ob = (uint32_t)((uint64_t)x >> p.L);
+  } else {
+    oa = compress_even(x);
+    ob = compress_even(x >> 1);
+    // ordering the creators a+(up, ascending) a+(dn, ascending) by mode:
+    // dn mode 2j+1 precedes up mode 2i iff j < i.
+    for (uint32_t m = oa; m; m &= m - 1) {
+      const int i = __ffs(m) - 1;
+      sign += __popc(ob & ((1u << i) - 1u));
+    }
+  }
+  const size_t tl = (size_t)1 << p.L;
+  const R* sd = sdt + (size_t)inst * 2 * tl;
+  const R v = sd[oa] * sd[tl + ob];
+  return (sign & 1) ? -v : v;
+}
+
+// ---------------------------------------------------------------------------
+// register-slot pair operations (A < B compile-time slots)
+// ---------------------------------------------------------------------------
+
+template <typename T2, typename R>
+__device__ __forceinline__ void rot(T2& u, T2& w, R c, R s) {
+  const T2 u0 = u, w0 = w;
+  u = mk<T2, R>(c * u0.x - s * w0.y, c * u0.y + s * w0.x);
+  w = mk<T2, R>(c * w0.x - s * u0.y, c * w0.y + s * u0.x);
+}
+
+// x with its sign flipped when bit e of m is set (m: per-op sign mask; e is
+// a constant after unrolling, so this is a shift and two logic ops).
+__device__ __forceinline__ float sflip(float x, uint32_t m, int e) {
+  return __int_as_float(__float_as_int(x) ^ ((m << (31 - e)) & 0x80000000u));
+}
+__device__ __forceinline__ double sflip(double x, uint32_t m, int e) {
+  return __hiloint2double(__double2hiint(x) ^ (int)((m << (31 - e)) & 0x80000000u), __double2loint(x));
+}
+
+template <int A, int B, int NE, typename T2, typename R>
+__device__ __forceinline__ void pair_giv(T2 (&v)[NE], R c, R s, uint32_t sm) {
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    if (((e >> A) & 1) == 0 && ((e >> B) & 1) == 1) {
+      constexpr int F = (1 << A) | (1 << B);
+      rot(v[e], v[e ^ F], c, sflip(s, sm, e));
+    }
+  }
+}
+
+// mode 0: energy term; 1: energy term + lam += h psi; 2: gradient term.
+template <int A, int B, int MODE, int NE, typename T2, typename R>
+__device__ __forceinline__ R pair_hop(T2 (&v)[NE], T2 (&l)[NE], R tc, uint32_t sm) {
+  R part = 0;
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    if (((e >> A) & 1) == 0 && ((e >> B) & 1) == 1) {
+      constexpr int F = (1 << A) | (1 << B);
+      const R ts = sflip(tc, sm, e);
+      const T2 u = v[e], w = v[e ^ F];
+      if (MODE == 2) {
+        const T2 lu = l[e], lw = l[e ^ F];
+        part += ts * ((lu.x * w.y - lu.y * w.x) + (lw.x * u.y - lw.y * u.x));
+      } else {
+        part += ts * (u.x * w.x + u.y * w.y);
+        if (MODE == 1) {
+          l[e].x += ts * w.x; l[e].y += ts * w.y;
+          l[e ^ F].x += ts * u.x; l[e ^ F].y += ts * u.y;
+        }
+      }
+    }
+  }
+  return part;
+}
+
+// Dispatch a runtime slot pair (a, b) to the compile-time functions.
+#define HUB_PAIR_SWITCH(a, b, CALL)                                   \
+  switch ((a) * 8 + (b)) {                                            \
+    case 0 * 8 + 1: CALL(0, 1); break;                                \
+    case 0 * 8 + 2: if constexpr (RB > 2) { CALL(0, 2); } break;      \
+    case 1 * 8 + 2: if constexpr (RB > 2) { CALL(1, 2); } break;      \
+    case 0 * 8 + 3: if constexpr (RB > 3) { CALL(0, 3); } break;      \
+    case 1 * 8 + 3: if constexpr (RB > 3) { CALL(1, 3); } break;      \
+    case 2 * 8 + 3: if constexpr (RB > 3) { CALL(2, 3); } break;      \
+    case 0 * 8 + 4: if constexpr (RB > 4) { CALL(0, 4); } break;      \
+    case 1 * 8 + 4: if constexpr (RB > 4) { CALL(1, 4); } break;      \
+    case 2 * 8 + 4: if constexpr (RB > 4) { CALL(2, 4); } break;      \
+    case 3 * 8 + 4: if constexpr (RB > 4) { CALL(3, 4); } break;      \
+    default: break;                                                   \
+  }
+
+// ---------------------------------------------------------------------------
+// the sweep kernel
+// ---------------------------------------------------------------------------
+
+template <typename R, int NV, int RB>
+__global__ void __launch_bounds__(512, 1)
+sweep_kernel(const SweepDev sw, const KernelArgs a) {
+  using T2 = typename CT<R>::T2;
+  constexpr int DT = CT<R>::DT;
+  constexpr int NE = 1 << RB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nph = sw.phase_end - sw.phase_begin;
+  const uint32_t tsize = 1u << sw.k;
+  const int nbuf = nph > 1 ? NV : 0;
+  T2* xb = reinterpret_cast<T2*>(smem_raw);
+  T2* xl = xb + tsize;
+  double* acc = reinterpret_cast<double*>(smem_raw + (size_t)nbuf * tsize * sizeof(T2));
+  PhaseDev* phs = reinterpret_cast<PhaseDev*>(acc + a.n_slots);
+  const size_t op_off = ((size_t)(reinterpret_cast<unsigned char*>(phs + nph) - smem_raw) + 15) & ~(size_t)15;
+  OpDev* sops = reinterpret_cast<OpDev*>(smem_raw + op_off) - sw.op_begin;   // indexed by global op id
+  __shared__ int8_t s_nbits[kMaxQubits];
+  __shared__ int8_t s_tbits[kMaxTileBits];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nth = blockDim.x;
+  const R* rtabs = reinterpret_cast<const R*>(DT == 0 ? (const void*)a.real_tabs32 : (const void*)a.real_tabs);
+  const R* sdt = reinterpret_cast<const R*>(DT == 0 ? (const void*)a.prep.sd32 : (const void*)a.prep.sd);
+  const uint32_t upm = (uint32_t)a.upmask;
+
+  if (tid == 0) {   // constant indices: no local copy of the parameter block
+#pragma unroll
+    for (int i = 0; i < kMaxQubits; ++i) s_nbits[i] = sw.nbits[i];
+#pragma unroll
+    for (int i = 0; i < kMaxTileBits; ++i) s_tbits[i] = sw.tbits[i];
+  }
+  for (int i = tid; i < a.n_slots; i += nth) acc[i] = 0.0;
+  {
+    const int* src = reinterpret_cast<const int*>(a.phases + sw.phase_begin);
+    int* dst = reinterpret_cast<int*>(phs);
+    const int nw = nph * (int)(sizeof(PhaseDev) / sizeof(int));
+    for (int i = tid; i < nw; i += nth) dst[i] = src[i];
+    const int* osrc = reinterpret_cast<const int*>(a.ops + sw.op_begin);
+    int* odst = reinterpret_cast<int*>(sops + sw.op_begin);
+    const int now = (sw.op_end - sw.op_begin) * (int)(sizeof(OpDev) / sizeof(int));
+    for (int i = tid; i < now; i += nth) odst[i] = osrc[i];
+  }
+  __syncthreads();
+
+  const uint32_t n_tiles = (uint32_t)a.n_tiles;
+  const uint32_t chunk = (n_tiles + gridDim.x - 1) / gridDim.x;
+  const uint32_t t0 = blockIdx.x * chunk;
+  const uint32_t t1 = min(t0 + chunk, n_tiles);
+  const uint32_t tl_mask = (uint32_t)((1ull << sw.n_nontile) - 1ull);
+  int cur_b = -1;
+  T2 v[NE];
+  T2 l[NE];
+
+  for (uint32_t tau = t0; tau < t1; ++tau) {
+    const int b = (int)(tau >> sw.n_nontile);
+    if (b != cur_b) {
+      if (cur_b >= 0) {
+        __syncthreads();
+        for (int i = tid; i < a.n_slots; i += nth) {
+          const double x = acc[i];
+          if (x != 0.0) atomicAdd(&a.acc[(size_t)cur_b * a.n_slots + i], x);
+          acc[i] = 0.0;
+        }
+        __syncthreads();
+      }
+      cur_b = b;
+    }
+    const int inst = b % a.n_inst;
+    // state-local indices fit in 32 bits (n <= 32)
+    const uint32_t sbase = deposit_bits(tau & tl_mask, s_nbits, sw.n_nontile);
+    const uint64_t gbase = ((uint64_t)b << a.n) | sbase;
+    R eacc = 0, nacc = 0, racc = 0;
+    int rslot = -1;
+    uint32_t base = 0;      // thread's tile-local base index in this phase
+    uint32_t sbw = 0;       // its swizzled exchange index
+    uint32_t gob = 0;       // its state-index bits
+    uint32_t so[RB], ss[RB];  // per-slot state-index bit and exchange index
+
+    for (int pi = 0; pi < nph; ++pi) {
+      const PhaseDev& ph = phs[pi];
+      if (pi > 0) {  // exchange through shared memory: old mapping out
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < NE; ++e) {
+          const uint32_t loc = sbw ^ comb<RB>(ss, e);
+          xb[loc] = v[e];
+          if (NV == 2) xl[loc] = l[e];
+        }
+        __syncthreads();
+      }
+      base = 0;
+      gob = 0;
+#pragma unroll
+      for (int i = 0; i < kLaneBits; ++i) {
+        const uint32_t bit = (uint32_t)((lane >> i) & 1);
+        base |= bit << ph.lane[i];
+        gob |= bit << s_tbits[ph.lane[i]];
+      }
+      for (int j = 0; j < ph.nwarp; ++j) {
+        const uint32_t bit = (uint32_t)((warp >> j) & 1);
+        base |= bit << ph.warp[j];
+        gob |= bit << s_tbits[ph.warp[j]];
+      }
+      sbw = swz(base, DT);
+#pragma unroll
+      for (int j = 0; j < RB; ++j) { so[j] = ph.so[j]; ss[j] = ph.ss[j]; }
+      if (pi == 0) {  // global load (the lanes are the 5 low tile bits)
+#pragma unroll
+        for (int e = 0; e < NE; ++e) {
+          const uint32_t off = gob | comb<RB>(so, e);
+          if (sw.flags & SW_PREP) {
+            v[e] = mk<T2, R>(prep_amp<R>(a.prep, sdt, sbase | off, inst), (R)0);
+          } else {
+            const T2* src = reinterpret_cast<const T2*>((sw.flags & SW_CKPT_READ) ? a.ckpt : a.psi);
+            v[e] = src[gbase + off];
+          }
+          if (NV == 2) {
+            if (sw.flags & SW_READ_LAM) l[e] = reinterpret_cast<const T2*>(a.lam)[gbase + off];
+            else l[e] = mk<T2, R>((R)0, (R)0);
+          }
+        }
+      } else {        // new mapping in
+#pragma unroll
+        for (int e = 0; e < NE; ++e) {
+          const uint32_t loc = sbw ^ comb<RB>(ss, e);
+          v[e] = xb[loc];
+          if (NV == 2) l[e] = xl[loc];
+        }
+      }
+
+      for (int oi = ph.op_begin; oi < ph.op_end; ++oi) {
+        const uint4* opw = reinterpret_cast<const uint4*>(sops + oi);
+        const uint4 w0 = opw[0];
+        const uint4 w1 = opw[1];
+        const int kind = (int)(w0.x & 255u), flags = (int)((w0.x >> 8) & 255u);
+        const int oa = (int)((w0.x >> 16) & 255u), ob = (int)(w0.x >> 24);
+        const int idx = (int)w1.x, slot = (int)w1.y;
+        if (kind == OP_GRAD_HOP || kind == OP_GRAD_DIAG) {
+          if (slot != rslot) {
+            if (rslot >= 0) cta_add(acc, rslot, (double)racc);
+            racc = 0;
+            rslot = slot;
+          }
+        }
+        // sign mask of the pairs: slot part from the plan, the rest from
+        // the thread's other tile bits and the tile's non-tile bits
+        const int tpar = (__popc(base & w0.z) + __popc(sbase & w0.w)) & 1;
+        const uint32_t sm = w0.y ^ (tpar ? 0xffffffffu : 0u);
+        switch (kind) {
+          case OP_GIV: {
+            const T2 cs = reinterpret_cast<const T2*>(a.coef)[(size_t)b * a.n_gates + idx];
+            const R sn = (flags & OPF_INV) ? -cs.y : cs.y;
+            const R cc = cs.x;
+            const bool dol = (NV == 2) && (flags & OPF_LAM);
+#define HUB_GIV(A, B)                       \
+  {                                         \
+    pair_giv<A, B>(v, cc, sn, sm);          \
+    if (dol) pair_giv<A, B>(l, cc, sn, sm); \
+  }
+            HUB_PAIR_SWITCH(oa, ob, HUB_GIV)
+#undef HUB_GIV
+            break;
+          }
+          case OP_MEAS_HOP:
+          case OP_LAM_HOP:
+          case OP_GRAD_HOP: {
+            const R tc = (R)a.hcoef[(size_t)inst * a.n_hterms + idx];
+            R part = 0;
+            if (kind == OP_MEAS_HOP) {
+#define HUB_M0(A, B) { part = pair_hop<A, B, 0>(v, l, tc, sm); }
+              HUB_PAIR_SWITCH(oa, ob, HUB_M0)
+#undef HUB_M0
+              eacc += (R)2 * part;
+            } else if (kind == OP_LAM_HOP) {
+              if (NV == 2) {
+#define HUB_M1(A, B) { part = pair_hop<A, B, 1>(v, l, tc, sm); }
+                HUB_PAIR_SWITCH(oa, ob, HUB_M1)
+#undef HUB_M1
+              }
+              eacc += (R)2 * part;
+            } else {
+              if (NV == 2) {
+#define HUB_M2(A, B) { part = pair_hop<A, B, 2>(v, l, tc, sm); }
+                HUB_PAIR_SWITCH(oa, ob, HUB_M2)
+#undef HUB_M2
+              }
+              racc += (R)2 * part;
+            }
+            break;
+          }
+          case OP_DIAG: {
+            const DiagOpDev& d = a.diag_ops[idx];
+            const T2* ptab = reinterpret_cast<const T2*>(a.phase_tabs) + (size_t)b * a.phase_stride + d.phase_off;
+            const bool inv = flags & OPF_INV;
+            const bool dol = (NV == 2) && (flags & OPF_LAM);
+            const uint32_t xb0 = sbase | gob;
+            if (d.has_x == 0 && d.n_vb == 0 && d.has_y <= 2) {
+              // on-site factor only: phase of the double-occupancy pattern
+              const T2* ty = ptab + 1024;
+              const bool two = d.has_y == 2;
+#pragma unroll
+              for (int e = 0; e < NE; ++e) {
+                const uint32_t x = xb0 | comb<RB>(so, e);
+                const uint32_t y = x & (x >> a.s) & upm;
+                T2 p = ty[y & 255u];
+                if (two) p = cmul(p, ty[256 + ((y >> 8) & 255u)]);
+                if (inv) p.y = -p.y;
+                v[e] = cmul(v[e], p);
+                if (dol) l[e] = cmul(l[e], p);
+              }
+              break;
+            }
+#pragma unroll
+            for (int e = 0; e < NE; ++e) {
+              T2 p = diag_phase<T2>(d, ptab, xb0 | comb<RB>(so, e), a.s, upm);
+              if (inv) p.y = -p.y;
+              v[e] = cmul(v[e], p);
+              if (dol) l[e] = cmul(l[e], p);
+            }
+            break;
+          }
+          case OP_MEAS_DIAG:
+          case OP_LAM_DIAG:
+          case OP_GRAD_DIAG: {
+            const DiagOpDev& d = a.diag_ops[idx];
+            const R* rtab = rtabs + (size_t)inst * a.real_stride + d.real_off;
+            R pe = 0, pn = 0;
+            const bool fast = d.has_x == 0 && d.n_vb == 0 && d.has_y <= 2;
+            const bool two = d.has_y == 2;
+            const uint32_t xb0 = sbase | gob;
+#pragma unroll
+            for (int e = 0; e < NE; ++e) {
+              const uint32_t x = xb0 | comb<RB>(so, e);
+              R dv;
+              if (fast) {   // on-site terms only
+                const uint32_t y = x & (x >> a.s) & upm;
+                dv = rtab[1024 + (y & 255u)];
+                if (two) dv += rtab[1280 + ((y >> 8) & 255u)];
+              } else {
+                dv = diag_real<R>(d, rtab, x, a.s, upm);
+              }
+              const T2 u = v[e];
+              if (kind == OP_GRAD_DIAG) {
+                if (NV == 2) pe += dv * (l[e].x * u.y - l[e].y * u.x);
+              } else {
+                const R m2 = u.x * u.x + u.y * u.y;
+                pe += dv * m2;
+                pn += m2;
+                if (NV == 2 && kind == OP_LAM_DIAG) {
+                  l[e].x += dv * u.x;
+                  l[e].y += dv * u.y;
+                }
+              }
+            }
+            if (kind == OP_GRAD_DIAG) racc += (R)2 * pe;
+            else { eacc += pe; nacc += pn; }
+            break;
+          }
+          default: break;
+        }
+      }
+    }
+    if (rslot >= 0) cta_add(acc, rslot, (double)racc);
+    cta_add(acc, a.slot_E, (double)eacc);
+    cta_add(acc, a.slot_N, (double)nacc);
+
+    // ---- store from registers (the last phase has the low bits on the lanes) ----
+    const bool wp = sw.flags & SW_WRITE_PSI, wc = sw.flags & SW_CKPT_WRITE;
+    const bool wl = (NV == 2) && (sw.flags & SW_WRITE_LAM);
+    if (wp || wc || wl) {
+#pragma unroll
+      for (int e = 0; e < NE; ++e) {
+        const uint64_t g = gbase + (gob | comb<RB>(so, e));
+        if (wp) reinterpret_cast<T2*>(a.psi)[g] = v[e];
+        if (wc) reinterpret_cast<T2*>(a.ckpt)[g] = v[e];
+        if (wl) reinterpret_cast<T2*>(a.lam)[g] = l[e];
+      }
+    }
+  }
+  __syncthreads();
+  if (cur_b >= 0) {
+    for (int i = tid; i < a.n_slots; i += nth) {
+      const double x = acc[i];
+      if (x != 0.0) atomicAdd(&a.acc[(size_t)cur_b * a.n_slots + i], x);
+    }
+  }
+}
+
+}  // namespace hubsv

@@ -1,0 +1,17 @@
+// Instantiations of the sweep kernel for float amplitudes, 2 vector(s)
+// per tile; compiled as a unit of its own so the builds run in parallel.
+#include "hubsv_sweep.cuh"
+
+namespace hubsv {
+
+const void* sweep_ptr_f2(int r) {
+  switch (r) {
+    case 1: return (const void*)sweep_kernel<float, 2, 1>;
+    case 2: return (const void*)sweep_kernel<float, 2, 2>;
+    case 3: return (const void*)sweep_kernel<float, 2, 3>;
+    case 4: return (const void*)sweep_kernel<float, 2, 4>;
+    default: return nullptr;
+  }
+}
+
+}  // namespace hubsv

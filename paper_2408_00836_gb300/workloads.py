@@ -146,6 +146,11 @@ def workload(number: int, batch_sets: int | None = None) -> Workload:
         w.draws["t_noise"] = rng.uniform(-0.1, 0.1, (16, 16))
         w.draws["U_noise"] = rng.uniform(-0.1, 0.1, 16)
         w.draws["theta"] = rng.uniform(-math.pi, math.pi, 20)
+    elif number == 6:
+        # profiling proxy of workload 5 at 24 qubits: 3x4 grid, N = 6+6,
+        # t = 1, U = 8, 4 layers of (U, h1, v1, h2, v2); theta ~ U(-pi, pi)
+        w = Workload("grid3x4u", 6, 3, 4, "rowmajor", 6, 6, 4, list(H), 1.0, [8.0], 0.0, 1)
+        w.draws["theta"] = rng.uniform(-math.pi, math.pi, 20)
     else:
         raise ValueError(number)
     return w
