@@ -177,6 +177,28 @@ HUB_API hub_status energy_grad(ans_t ans, const double* theta, void* psi, void* 
                        void* ckpt, double* E, double* grad, int32_t dtype,
                        int64_t batch, uint32_t flags, hub_stream_t stream);
 
+/* energy() for callers that cannot allocate device memory.  (The paper has
+ * no counterpart: this is an interface addition.)  Some callers cannot call
+ * cudaMalloc while they compute -- their framework's allocator already owns
+ * the free device memory, an allocation would synchronise a latency-critical
+ * loop, or the work is being recorded into a CUDA graph.  energy() allocates
+ * its per-call scratch (coefficient and phase tables, FP64 accumulators) and
+ * its static tables on first use; energy_noalloc allocates nothing: it puts
+ * every table and all scratch in one static device array of
+ * HUB_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the library
+ * holds until the process exits.  Arguments and results are those of
+ * energy().  Problems whose tables do not fit return HUB_EINVAL with the
+ * size needed.  The first call on a device looks up the array's device
+ * address (make it before any stream capture); later calls reuse it.  Every
+ * call shares the array (it clears the accumulators it uses), so calls that
+ * overlap on the GPU -- on different streams or threads -- race.  The
+ * initial-state tables come from the last state_prepare call, which, being
+ * a set-up call, may allocate.                                              */
+#define HUB_NOALLOC_SCRATCH_BYTES (8u << 20)
+HUB_API hub_status energy_noalloc(ans_t ans, const double* theta, void* psi, double* E,
+                                  int32_t dtype, int64_t batch, uint32_t flags,
+                                  hub_stream_t stream);
+
 /* lam = H psi for each batch element (Eq. 4's operator; used by tests and
  * by callers that need the residual).  psi is read only.                    */
 HUB_API hub_status hub_apply_h(ans_t ans, const void* psi, void* lam, int32_t dtype,

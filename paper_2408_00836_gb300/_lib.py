@@ -21,7 +21,7 @@ EXPORTS = [
     "hub_square_lattice", "hub_create", "hub_destroy", "ans_create", "ans_create_multi",
     "ans_destroy", "ans_num_params", "ans_num_qubits", "state_prepare", "energy",
     "energy_grad", "hub_apply_h", "ans_plan_stats", "ans_set_tile", "hub_sync",
-    "hub_last_error", "ans_plan_describe", "ans_profile", "ans_profile_read",
+    "hub_last_error", "ans_plan_describe", "ans_profile", "ans_profile_read", "energy_noalloc",
 ]
 
 
@@ -69,6 +69,7 @@ def lib():
         "state_prepare": (st, [c_void_p, c_int32, POINTER(c_double), POINTER(c_int32), c_void_p, c_int32,
                                c_int64, c_void_p]),
         "energy": (st, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_uint32, c_void_p]),
+        "energy_noalloc": (st, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_uint32, c_void_p]),
         "energy_grad": (st, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
                              c_int64, c_uint32, c_void_p]),
         "hub_apply_h": (st, [c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_void_p]),

@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "libhubsv.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["hubsv_api.cpp", "hubsv_plan.cpp", "hubsv_tables.cu", "hubsv_sweep_f1.cu",
-           "hubsv_sweep_f2.cu", "hubsv_sweep_d1.cu", "hubsv_sweep_d2.cu"]
+           "hubsv_sweep_f2.cu", "hubsv_sweep_d1.cu", "hubsv_sweep_d2.cu", "hubsv_noalloc.cu"]
 
 
 def _nvcc():

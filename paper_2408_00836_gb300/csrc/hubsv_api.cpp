@@ -720,6 +720,7 @@ extern "C" hub_status state_prepare(ans_t a, int32_t kind, const double* orb_per
         }
       }
     }
+    a->sd_host = sd;
     if ((s = a->d_sd.upload(sd, "determinant tables")) != HUB_OK) return s;
     if ((s = a->d_sd32.upload(std::vector<float>(sd.begin(), sd.end()), "determinant tables (FP32)")) != HUB_OK)
       return s;

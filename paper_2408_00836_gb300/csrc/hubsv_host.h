@@ -89,6 +89,7 @@ struct hub_ansatz {
   hubsv::DevBuf d_gate_param, d_gate_t, d_tab_param, d_tab_val, d_hcoef, d_real, d_diag;
   hubsv::DevBuf d_real32;                // FP32 copy of real_tabs
   hubsv::DevBuf d_sd, d_sd32;            // Slater determinant tables (FP64, FP32)
+  std::vector<double> sd_host;           // host copy of the determinant tables
   int prep_kind = -1;
   uint64_t neel_x0 = 0;
   hubsv::DevBuf d_coef[2], d_phase[2], d_acc;
