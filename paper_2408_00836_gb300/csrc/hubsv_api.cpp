@@ -450,8 +450,10 @@ extern "C" hub_status ans_create_multi(const hub_t* models, int32_t n_models, in
     a->h_diag = add_diag_op(a, xc, xk, yc, vb, vv, -1);
   }
   // forward sequence
+  a->n_layers = n_layers;
   for (int g = 0; g < G; ++g) {
     const hub_group& gr = groups[g];
+    if (groups_per_layer > 0 && g % groups_per_layer == 0) a->layer_begin.push_back((int)a->fwd.size());
     if (gr.kind == HUB_G_HOP) {
       for (int k = 0; k < gr.n_terms; ++k) {
         const int b = gr.terms[k];
@@ -552,7 +554,8 @@ hub_status ensure_device(hub_ansatz* a) {
   return HUB_OK;
 }
 hub_status get_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*& pl) {
-  const int key = which * 16 + dtype * 4 + (int)(flags & 3u);  // PREP_FUSED | KEEP_STATE
+  // flags: PREP_FUSED | KEEP_STATE | internal checkpoint bit (4)
+  const int key = which * 16 + dtype * 8 + (int)(flags & 7u);
   auto it = a->plans.find(key);
   if (it != a->plans.end()) { pl = it->second; return HUB_OK; }
   hub_status st = make_plan(a, which, dtype, flags, pl);
@@ -759,10 +762,11 @@ extern "C" hub_status energy_grad(ans_t a, const double* theta, void* psi, void*
   if (psi == lam) return fail(HUB_EINVAL, "energy_grad: psi and lam must be distinct");
   if ((flags & HUB_FLAG_PREP_FUSED) && a->prep_kind < 0)
     return fail(HUB_EINVAL, "energy_grad: HUB_FLAG_PREP_FUSED needs a prior state_prepare");
-  (void)ckpt;
+  if (ckpt && (ckpt == psi || ckpt == lam)) return fail(HUB_EINVAL, "energy_grad: ckpt must be a third buffer");
+  const uint32_t pf = (flags & 3u) | (ckpt ? kPlanCkpt : 0u);
   Plan* pl;
-  if ((s = get_plan(a, 1, dtype, flags, pl)) != HUB_OK) return s;
-  return run_plan(a, pl, dtype, theta, psi, lam, nullptr, batch, E, grad, (cudaStream_t)stream);
+  if ((s = get_plan(a, 1, dtype, pf, pl)) != HUB_OK) return s;
+  return run_plan(a, pl, dtype, theta, psi, lam, ckpt, batch, E, grad, (cudaStream_t)stream);
 }
 
 extern "C" hub_status hub_apply_h(ans_t a, const void* psi, void* lam, int32_t dtype, int64_t batch,

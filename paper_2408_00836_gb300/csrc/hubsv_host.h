@@ -11,6 +11,10 @@
 
 namespace hubsv {
 
+// Internal plan flag (beside HUB_FLAG_PREP_FUSED / HUB_FLAG_KEEP_STATE):
+// energy_grad with a checkpoint buffer.
+constexpr uint32_t kPlanCkpt = 4u;
+
 hub_status fail(hub_status s, const std::string& m);
 hub_status cuda_fail(cudaError_t e, const char* what);
 
@@ -75,6 +79,8 @@ struct hub_ansatz {
   int n_inst = 0, L = 0, n = 0, P = 0, s = 0, layout = 0;
   uint64_t upmask = 0;
   std::vector<hubsv::SeqOp> fwd;         // forward factors in order
+  std::vector<int> layer_begin;          // index in fwd of each layer's first factor
+  int n_layers = 0;
   struct HTerm { int p, q; };
   std::vector<HTerm> hterms;             // H hop terms: 2*bond + spin
   int h_diag = -1;                       // DiagOp index of H's diagonal

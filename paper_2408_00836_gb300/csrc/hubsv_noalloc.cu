@@ -78,7 +78,7 @@ extern "C" hub_status energy_noalloc(ans_t a, const double* theta, void* psi, do
   cudaError_t ce = cudaGetLastError();
   if (ce != cudaSuccess) return cuda_fail(ce, "energy_noalloc: earlier asynchronous error");
   // the plan (host data only; cached in the ansatz)
-  const int key = 0 * 16 + dtype * 4 + (int)(flags & 3u);
+  const int key = 0 * 16 + dtype * 8 + (int)(flags & 3u);   // the plan cache key of energy()
   Plan* pl = nullptr;
   auto it = a->plans.find(key);
   if (it != a->plans.end()) {

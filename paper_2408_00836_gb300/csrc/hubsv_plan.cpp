@@ -33,12 +33,36 @@ uint64_t between_mask(int p, int q) {  // bits strictly between p < q
   return ((1ull << q) - 1ull) & ~((1ull << (p + 1)) - 1ull);
 }
 
+// Checkpoint markers (host only, never sent to the device): barriers that
+// make a sweep store psi to the checkpoint buffer at its end (SAVE) or load
+// psi from it at its start (LOAD).
+constexpr uint8_t MARK_SAVE = 100, MARK_LOAD = 101;
+constexpr int CLS_MARK = 4;
+
+SeqOp marker(uint8_t kind) {
+  SeqOp m;
+  m.kind = kind;
+  m.support = ~0ull;
+  m.cls = CLS_MARK;
+  return m;
+}
+
 // Call kinds: 0 energy, 1 energy + gradient, 2 lam = H psi, 3 initial state
-// only (no operations).
-std::vector<SeqOp> build_sequence(const hub_ansatz* a, int which) {
+// only (no operations).  With a checkpoint (energy + gradient), psi is
+// saved after the first half of the layers and reloaded when the backward
+// pass has undone the second half.
+std::vector<SeqOp> build_sequence(const hub_ansatz* a, int which, uint32_t flags) {
   std::vector<SeqOp> seq;
   if (which == 3) return seq;
-  if (which != 2) seq = a->fwd;
+  const bool ck = which == 1 && (flags & kPlanCkpt) && a->n_layers >= 2 &&
+                  (int)a->layer_begin.size() == a->n_layers;
+  const int split = ck ? a->layer_begin[a->n_layers / 2] : -1;
+  if (which != 2) {
+    for (int i = 0; i < (int)a->fwd.size(); ++i) {
+      if (i == split) seq.push_back(marker(MARK_SAVE));
+      seq.push_back(a->fwd[i]);
+    }
+  }
   const uint64_t hsup = diag_support(a, a->h_diag);
   for (size_t t = 0; t < a->hterms.size(); ++t) {
     SeqOp op;
@@ -69,6 +93,7 @@ std::vector<SeqOp> build_sequence(const hub_ansatz* a, int which) {
       v.flags = OPF_INV | OPF_LAM;
       v.cls = 3;
       seq.push_back(v);
+      if (i == split) seq.push_back(marker(MARK_LOAD));
     }
   }
   return seq;
@@ -99,10 +124,22 @@ Scan scan(const std::vector<SeqOp>& seq, const std::vector<int>& order, uint64_t
   s.tile = init;
   uint64_t s_any = 0, s_diag = 0;
   bool fwd_skipped = false;
-  for (int idx : order) {
+  for (size_t oi = 0; oi < order.size(); ++oi) {
+    const int idx = order[oi];
     const SeqOp& op = seq[idx];
     bool ok = !((op.support & s_any) || (!op.diagonal && (op.support & s_diag)));
     if (op.cls == 2 && fwd_skipped) ok = false;
+    if (op.cls == CLS_MARK) {
+      if (op.kind == MARK_LOAD && !s.exec.empty()) ok = false;   // a load opens its sweep
+      if (ok) {
+        s.exec.push_back(idx);
+        if (op.kind == MARK_SAVE) {   // a save closes its sweep
+          s.rest.insert(s.rest.end(), order.begin() + oi + 1, order.end());
+          return s;
+        }
+        continue;
+      }
+    }
     if (ok) {
       const uint64_t nd = need(op);
       if (nd & ~allowed) ok = false;
@@ -186,6 +223,8 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
   const int n = a->n;
   if (n < kLaneBits + 1) return fail(HUB_EUNSUPPORTED, "need at least 6 qubits (3 sites)");
   int k = a->tile_override[dtype] ? a->tile_override[dtype] : (dtype == HUB_C64 ? 13 : 12);
+  // threads = 32 << (k - 5 - r) must stay <= 512 for every sweep
+  k = std::min(k, kLaneBits + 4 + std::min(max_reg_bits(dtype, 1), max_reg_bits(dtype, 2)));
   k = std::min(k, n);
   const uint64_t cmask = (1ull << kLaneBits) - 1ull;
   const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
@@ -194,7 +233,7 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
     upm |= 1ull << a->models[0]->up[i];
     dnm |= 1ull << a->models[0]->dn[i];
   }
-  std::vector<SeqOp> seq = build_sequence(a, which);
+  std::vector<SeqOp> seq = build_sequence(a, which, flags);
   std::vector<int> remaining(seq.size());
   for (size_t i = 0; i < seq.size(); ++i) remaining[i] = (int)i;
   auto need_modes = [](const SeqOp& op) -> uint64_t {
@@ -242,9 +281,16 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
   double bytes = 0.0;
   for (size_t si = 0; si < sweeps.size(); ++si) {
     const PS& ps = sweeps[si];
-    // sweep flags
-    bool mod_psi = false, use_lam = false, mod_lam = false;
+    // sweep flags; checkpoint markers become flags and leave the op list
+    bool mod_psi = false, use_lam = false, mod_lam = false, ck_save = false, ck_load = false;
+    std::vector<int> sweep_ops;
     for (int idx : ps.ops) {
+      if (seq[idx].cls == CLS_MARK) {
+        ck_save = ck_save || seq[idx].kind == MARK_SAVE;
+        ck_load = ck_load || seq[idx].kind == MARK_LOAD;
+        continue;
+      }
+      sweep_ops.push_back(idx);
       mod_psi = mod_psi || modifies_psi(seq[idx]);
       use_lam = use_lam || uses_lam(seq[idx]);
       mod_lam = mod_lam || modifies_lam(seq[idx]);
@@ -252,7 +298,9 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
     const bool first = si == 0, last = si + 1 == sweeps.size();
     uint32_t f = 0;
     if (first && prep && which != 2) f |= SW_PREP; else f |= SW_READ_PSI;
-    if ((!last || keep) && (mod_psi || (f & SW_PREP)) && which != 2) f |= SW_WRITE_PSI;
+    if (ck_load) f |= SW_CKPT_READ;          // psi comes from the checkpoint
+    if (ck_save) f |= SW_CKPT_WRITE;         // and a copy goes to it
+    if ((!last || keep) && (mod_psi || (f & (SW_PREP | SW_CKPT_READ))) && which != 2) f |= SW_WRITE_PSI;
     if (use_lam || (lam_live && mod_lam)) {
       f |= SW_HAS_LAM;
       if (lam_live) f |= SW_READ_LAM;
@@ -282,7 +330,7 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
     };
     struct PH { uint32_t S; std::vector<int> ops; };
     std::vector<PH> phs;
-    std::vector<int> rem = ps.ops;
+    std::vector<int> rem = sweep_ops;
     while (!rem.empty()) {
       const uint32_t allowed = phs.empty() ? (tmask & ~low) : tmask;
       Scan s = scan(seq, rem, 0, allowed, r, need_local);
@@ -378,7 +426,8 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
     sw.op_end = (int)pl->hops.size();
     bytes += amp * (double)(1ull << n) *
              (((f & SW_READ_PSI) ? 1 : 0) + ((f & SW_WRITE_PSI) ? 1 : 0) +
-              ((f & SW_READ_LAM) ? 1 : 0) + ((f & SW_WRITE_LAM) ? 1 : 0));
+              ((f & SW_READ_LAM) ? 1 : 0) + ((f & SW_WRITE_LAM) ? 1 : 0) +
+              ((f & SW_CKPT_WRITE) ? 1 : 0));
     pl->sweeps.push_back(sw);
     pl->nvec.push_back(nv);
     pl->tiles.push_back(ps.tile);

@@ -1,0 +1,160 @@
+"""VQE driver: host L-BFGS over the energy and adjoint gradient, the
+evaluation captured once in a CUDA graph and replayed per iteration.
+
+The optimiser follows Sec. 2.1: L-BFGS; stop when the change of the energy
+between the last two steps is below 1e-7, when the gradient (max norm) is
+below 1e-6, or after ``max_iter`` steps.  Everything on the amplitudes runs
+in the library's kernels; the host holds only the parameters, the L-BFGS
+history and the line search.
+"""
+
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import C64, C128, Ansatz
+
+
+class EnergyGradGraph:
+    """energy_grad on static buffers, captured into a CUDA graph.
+
+    Calling the object copies theta (host) into the static device buffer,
+    replays the graph and returns (E, grad) as host arrays.  The first call
+    of energy_grad (done here, outside the capture) makes every allocation
+    the call needs, so the captured graph contains kernel launches only.
+    """
+
+    def __init__(self, ans: Ansatz, dtype: int = C64, batch: int = 1, ckpt: bool = False,
+                 use_graph: bool = True):
+        import torch
+        self.torch = torch
+        self.ans, self.dtype, self.batch = ans, dtype, batch
+        td = torch.complex64 if dtype == C64 else torch.complex128
+        dev = torch.device("cuda", torch.cuda.current_device())
+        n = ans.n
+        self.theta_h = torch.zeros((batch, ans.P), dtype=torch.float64).pin_memory()
+        self.theta = torch.zeros((batch, ans.P), dtype=torch.float64, device=dev)
+        self.psi = torch.empty((batch, 1 << n), dtype=td, device=dev)
+        self.lam = torch.empty_like(self.psi)
+        self.ckpt = torch.empty_like(self.psi) if ckpt else None
+        self.E = torch.zeros(batch, dtype=torch.float64, device=dev)
+        self.g = torch.zeros((batch, ans.P), dtype=torch.float64, device=dev)
+        self.E_h = torch.zeros(batch, dtype=torch.float64).pin_memory()
+        self.g_h = torch.zeros((batch, ans.P), dtype=torch.float64).pin_memory()
+        self.graph = None
+        self.evals = 0
+        self._call()                        # warm-up: allocations happen here
+        torch.cuda.synchronize()
+        if use_graph:
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                self._call()                # second warm-up on the capture stream
+            torch.cuda.current_stream().wait_stream(s)
+            torch.cuda.synchronize()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph):
+                self._call()
+            torch.cuda.synchronize()
+
+    def _call(self):
+        self.ans.energy_grad(self.theta, self.psi, self.lam, self.E, self.g, ckpt=self.ckpt,
+                             dtype=self.dtype, batch=self.batch)
+
+    def __call__(self, theta: np.ndarray):
+        torch = self.torch
+        self.theta_h.copy_(torch.from_numpy(np.asarray(theta, dtype=np.float64).reshape(self.batch, -1)))
+        self.theta.copy_(self.theta_h, non_blocking=True)
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._call()
+        self.E_h.copy_(self.E, non_blocking=True)
+        self.g_h.copy_(self.g, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        self.evals += 1
+        return self.E_h.numpy().copy(), self.g_h.numpy().copy()
+
+
+@dataclass
+class VQEResult:
+    theta: np.ndarray
+    energy: float
+    grad_norm: float
+    iterations: int
+    evaluations: int
+    reason: str
+    history: list = field(default_factory=list)
+    seconds: float = 0.0
+
+
+def lbfgs(fun, x0, max_iter=1000, m=10, e_tol=1e-7, g_tol=1e-6, c1=1e-4, max_ls=30):
+    """Minimise fun(x) -> (f, grad) by L-BFGS (two-loop recursion) with a
+    backtracking line search (Armijo condition); stops as in Sec. 2.1."""
+    x = np.array(x0, dtype=np.float64)
+    f, g = fun(x)
+    S, Y, hist = [], [], [f]
+    reason = "max_iter"
+    it = 0
+    for it in range(1, max_iter + 1):
+        if np.max(np.abs(g)) < g_tol:
+            reason = "gradient"
+            it -= 1
+            break
+        q = g.copy()
+        alpha = []
+        for s, y in reversed(list(zip(S, Y))):
+            a = (s @ q) / (y @ s)
+            alpha.append(a)
+            q -= a * y
+        if S:
+            q *= (S[-1] @ Y[-1]) / (Y[-1] @ Y[-1])
+        for (s, y), a in zip(zip(S, Y), reversed(alpha)):
+            b = (y @ q) / (y @ s)
+            q += (a - b) * s
+        d = -q
+        gd = g @ d
+        if gd >= 0:                      # not a descent direction: restart
+            S, Y = [], []
+            d = -g
+            gd = g @ d
+        step = 1.0 if S else min(1.0, 1.0 / max(np.linalg.norm(g), 1e-12))
+        for _ in range(max_ls):
+            xn = x + step * d
+            fn, gn = fun(xn)
+            if fn <= f + c1 * step * gd:
+                break
+            step *= 0.5
+        s, y = xn - x, gn - g
+        if s @ y > 1e-12:
+            S.append(s)
+            Y.append(y)
+            if len(S) > m:
+                S.pop(0)
+                Y.pop(0)
+        df = abs(fn - f)
+        x, f, g = xn, fn, gn
+        hist.append(f)
+        if df < e_tol:
+            reason = "energy"
+            break
+    return x, f, g, it, reason, hist
+
+
+def run_vqe(ans: Ansatz, theta0, dtype: int = C64, max_iter: int = 200, ckpt: bool = False,
+            use_graph: bool = True) -> VQEResult:
+    """Energy-based VQE (Sec. 2.1) for one parameter set (batch 1): the
+    ansatz's initial state must have been set with state_prepare."""
+    fn = EnergyGradGraph(ans, dtype=dtype, batch=1, ckpt=ckpt, use_graph=use_graph)
+
+    def fun(x):
+        E, g = fn(x)
+        return float(E[0]), g[0]
+
+    t0 = time.perf_counter()
+    x, f, g, it, reason, hist = lbfgs(fun, theta0, max_iter=max_iter)
+    sec = time.perf_counter() - t0
+    return VQEResult(x, f, float(np.max(np.abs(g))), it, fn.evals, reason, hist, sec)

@@ -165,5 +165,6 @@ def test_schedules_are_valid(number, which):
     for kk in (10, 14):
         a.set_tile(H.C64, kk)
         plan = a.plan_describe(which, H.C64)
-        _check_schedule(plan, seq, w.n_qubits, min(kk, w.n_qubits), min(5, kk, w.n_qubits),
-                        set(range(w.n_qubits)))
+        # the planner caps c64 tiles at 13 bits (512 threads x 16 amplitudes)
+        k_eff = min(kk, 13, w.n_qubits)
+        _check_schedule(plan, seq, w.n_qubits, k_eff, min(5, k_eff), set(range(w.n_qubits)))

@@ -1,0 +1,100 @@
+"""GPU tests of the layers above the kernels: the CUDA-graph-captured
+energy + gradient, the L-BFGS VQE driver, the tile autotuner and the
+checkpointed adjoint pass."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2408_00836_gb300 as H
+from paper_2408_00836_gb300 import workloads as W
+from paper_2408_00836_gb300.autotune import autotune
+from paper_2408_00836_gb300.vqe import EnergyGradGraph, run_vqe
+
+from helpers import TOL, Problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _problem_2x3():
+    bonds, _ = H.square_lattice(2, 3)
+    t = np.zeros((6, 6))
+    for (i, j) in bonds:
+        t[i, j] = t[j, i] = 1.0
+    return Problem(2, 3, t=t, U=np.full(6, 4.0), V=None, layers=3, classes=("U", "h1", "v1", "h2"))
+
+
+@pytest.mark.parametrize("dtype", [H.C64, H.C128])
+def test_graph_replay_matches_direct_calls(dtype):
+    prob = _problem_2x3()
+    prob.ans.state_prepare(H.PREP_SLATER, None, None, None, dtype, 1)
+    fn = EnergyGradGraph(prob.ans, dtype=dtype, use_graph=True)
+    for seed in (1, 2):
+        th = W.random_theta(seed, 1, prob.P)[0]
+        E, g = fn(th)
+        Eo, go = prob.oracle_energy_grad(th)
+        assert abs(E[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
+        assert np.max(np.abs(g[0] - go)) < TOL[dtype] * max(1.0, np.max(np.abs(go)))
+
+
+def test_vqe_lbfgs_decreases_energy_above_ground_state():
+    prob = _problem_2x3()
+    prob.ans.state_prepare(H.PREP_SLATER, None, None, None, H.C128, 1)
+    th0 = np.random.default_rng(5).normal(0.0, np.sqrt(1e-5), prob.P)
+    e_start = prob.oracle_energy_grad(th0)[0]
+    res = run_vqe(prob.ans, th0, dtype=H.C128, max_iter=60)
+    e0, _ = O.lanczos_ground(prob.Hmat())
+    assert res.energy < e_start - 0.1
+    assert res.energy >= e0 - 1e-9
+    assert all(b <= a + 1e-12 for a, b in zip(res.history, res.history[1:]))
+    assert abs(prob.oracle_energy_grad(res.theta)[0] - res.energy) < 1e-9 * max(1.0, abs(res.energy))
+
+
+def test_autotune_keeps_results():
+    w = W.workload(2, batch_sets=1)
+    bonds, cls = H.square_lattice(2, 4, "snake")
+    t, U, _ = w.coefficients(bonds, 3)
+    m = H.Model(8, bonds, t, U, None, 4, 4)
+    a = H.Ansatz(m, H.hva_groups(bonds, cls, 8, w.layers, w.classes), w.layers)
+    a.state_prepare(H.PREP_SLATER, w.orbital_perturbation(), None, None, H.C64, 1)
+    th = torch.tensor(w.theta()[:1], device="cuda")
+    psi = torch.empty((1, 1 << 16), dtype=torch.complex64, device="cuda")
+    lam = torch.empty_like(psi)
+    E = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty((1, a.P), dtype=torch.float64, device="cuda")
+    ref = None
+    for k in (11, 12, 13):
+        a.set_tile(H.C64, k)
+        a.energy_grad(th, psi, lam, E, g, dtype=H.C64)
+        H.sync()
+        cur = (float(E[0]), g.cpu().numpy()[0])
+        if ref is None:
+            ref = cur
+        else:
+            assert abs(cur[0] - ref[0]) < TOL[H.C64] * max(1.0, abs(ref[0]))
+            assert np.max(np.abs(cur[1] - ref[1])) < TOL[H.C64] * max(1.0, np.max(np.abs(ref[1])))
+    best, times = autotune(a, H.C64, batch=1, which=1, candidates=(11, 12, 13), theta=w.theta()[:1])
+    assert best in times and len(times) == 3
+
+
+def test_checkpointed_gradient_matches_oracle_24q():
+    """Workload 6 shape (24 qubits): the adjoint pass with a checkpoint of
+    psi at the middle layer boundary against the oracle's gradient."""
+    w = W.workload(6)
+    bonds, _ = H.square_lattice(3, 4)
+    t, U, _ = w.coefficients(bonds)
+    prob = Problem(3, 4, t=t, U=U, V=None, layers=w.layers, classes=w.classes)
+    theta = w.theta()[0]
+    a = prob.ans
+    a.state_prepare(H.PREP_SLATER, None, None, None, H.C64, 1)
+    th = torch.tensor(theta[None, :], device="cuda")
+    psi = torch.empty((1, 1 << 24), dtype=torch.complex64, device="cuda")
+    lam, ck = torch.empty_like(psi), torch.empty_like(psi)
+    E = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty((1, a.P), dtype=torch.float64, device="cuda")
+    a.energy_grad(th, psi, lam, E, g, ckpt=ck, dtype=H.C64)
+    H.sync()
+    Eo, go = prob.oracle_energy_grad(theta)
+    assert abs(float(E[0]) - Eo) < TOL[H.C64] * max(1.0, abs(Eo))
+    assert np.max(np.abs(g.cpu().numpy()[0] - go)) < TOL[H.C64] * max(1.0, np.max(np.abs(go)))
