@@ -220,6 +220,14 @@ def run_gpu(args, rank, world, dist):
     w, a = build_problem(args.workload, H)
     batch = w.batch
     a.state_prepare(H.PREP_SLATER, w.orbital_perturbation(), None, None, dtype, batch)
+    tune = None
+    if args.autotune:
+        from paper_2408_00836_gb300.autotune import autotune
+        best, times = autotune(a, dtype, batch=batch, which=1, candidates=(11, 12, 13), reps=1,
+                               warmup=1, theta=w.theta())
+        tune = {"best_log2_tile": best, "ms": {str(k): round(v, 2) for k, v in times.items()}}
+    elif args.tile:
+        a.set_tile(dtype, args.tile)
     theta_h = torch.tensor(w.theta(), dtype=torch.float64).pin_memory()
     theta = theta_h.to(dev)
     psi = torch.empty((batch, 1 << w.n_qubits), dtype=tdt, device=dev)
@@ -315,6 +323,10 @@ def run_gpu(args, rank, world, dist):
            "plan": {"sweeps": n_sweeps, "bytes_per_eval": bytes_per_state},
            "energy": E_val, "roofline": roof, "e2e": e2e, "gpu_launches": launches,
            "clocks": ck}
+    if tune:
+        out["autotune"] = tune
+    elif args.tile:
+        out["config"]["log2_tile"] = args.tile
     del psi, lam
     torch.cuda.empty_cache()
     if args.c128 and dtype == H.C64 and rank == 0:
@@ -362,6 +374,8 @@ def main():
     ap.add_argument("--no-c128", dest="c128", action="store_false")
     ap.add_argument("--c128-steps", type=int, default=1)
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
+    ap.add_argument("--tile", type=int, default=0, help="log2 tile override (0 = planner default)")
+    ap.add_argument("--autotune", action="store_true", help="pick the tile size by timing first")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

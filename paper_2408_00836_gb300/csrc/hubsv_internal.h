@@ -24,6 +24,8 @@ enum OpKind : uint8_t {
   OP_LAM_DIAG = 5,   // lam += D psi, E += ..., N += ...
   OP_GRAD_HOP = 6,   // acc[slot] += 2 Im <lam| G_term |psi>
   OP_GRAD_DIAG = 7,  // acc[slot] += 2 Im <lam| G_diag |psi>
+  OP_GRADINV_HOP = 8,   // OP_GRAD_HOP then the inverse factor on psi and lam
+  OP_GRADINV_DIAG = 9,  // OP_GRAD_DIAG then the inverse factor on psi and lam
 };
 
 enum OpFlag : uint8_t {
@@ -41,10 +43,12 @@ struct alignas(16) OpDev {      // 32 bytes: read as two 16-byte words
   uint32_t sgn;                 // bit e = parity(e & JW string on the slots)
   uint32_t bm_local;            // JW string on the thread's other tile bits
   uint32_t bm_global;           // JW string on the non-tile bits (state index)
-  int32_t idx;                  // OP_GIV: coefficient column; other hop ops:
-                                // column of the -t table; diagonal ops: DiagOp
-  int32_t slot;                 // OP_GRAD_*: accumulator slot (parameter)
-  int32_t pad[2];
+  int32_t idx;                  // OP_GIV / OP_GRADINV_HOP: coefficient column;
+                                // other hop ops: column of the -t table;
+                                // diagonal ops: DiagOp
+  int32_t slot;                 // OP_GRAD*: accumulator slot (parameter)
+  int32_t idx2;                 // OP_GRADINV_HOP: column of the -t table
+  int32_t pad;
 };
 
 // A register phase: each thread holds the 2^r amplitudes whose tile-local
@@ -61,6 +65,10 @@ struct PhaseDev {
   uint8_t pad[4];
   uint32_t so[kMaxRegBits + 1];
   uint32_t ss[kMaxRegBits + 1];
+  // a thread's base part, looked up by lane and by warp index: tile-local
+  // bits (bl, bw) and state-index bits (gl, gw)
+  uint32_t bl[32], gl[32];
+  uint32_t bw[16], gw[16];
 };
 
 // A diagonal operator d(x) = sum_bytes X[byte of x] + sum_bytes Y[byte of y]

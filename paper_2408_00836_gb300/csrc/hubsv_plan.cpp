@@ -389,8 +389,21 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
         choose_lanes(freeb, dtype, pd.lane, pd.warp, nw);
       }
       pd.nwarp = (uint8_t)nw;
+      for (int v = 0; v < 32; ++v)
+        for (int j = 0; j < kLaneBits; ++j)
+          if (v >> j & 1) {
+            pd.bl[v] |= 1u << pd.lane[j];
+            pd.gl[v] |= 1u << sw.tbits[pd.lane[j]];
+          }
+      for (int v = 0; v < 16; ++v)
+        for (int j = 0; j < nw; ++j)
+          if (v >> j & 1) {
+            pd.bw[v] |= 1u << pd.warp[j];
+            pd.gw[v] |= 1u << sw.tbits[pd.warp[j]];
+          }
       pd.op_begin = (int)pl->hops.size();
-      for (int idx : P.ops) {
+      for (size_t oj = 0; oj < P.ops.size(); ++oj) {
+        const int idx = P.ops[oj];
         const SeqOp& op = seq[idx];
         OpDev d;
         std::memset(&d, 0, sizeof(d));
@@ -398,6 +411,23 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
         d.flags = op.flags;
         d.idx = op.kind == OP_GIV ? op.gate : (op.diagonal ? op.diag : op.hterm);
         d.slot = op.slot;
+        // a gradient step directly followed by its own inverse factor: fuse
+        if ((op.kind == OP_GRAD_HOP || op.kind == OP_GRAD_DIAG) && oj + 1 < P.ops.size()) {
+          const SeqOp& nx = seq[P.ops[oj + 1]];
+          const bool same = (op.kind == OP_GRAD_HOP) ? (nx.kind == OP_GIV && nx.gate == op.gate)
+                                                     : (nx.kind == OP_DIAG && nx.diag == op.diag);
+          if (same && (nx.flags & OPF_INV) && (nx.flags & OPF_LAM)) {
+            if (op.kind == OP_GRAD_HOP) {
+              d.kind = OP_GRADINV_HOP;
+              d.idx = op.gate;
+              d.idx2 = op.hterm;
+            } else {
+              d.kind = OP_GRADINV_DIAG;
+            }
+            d.flags = nx.flags;
+            ++oj;   // the inverse is folded into this operation
+          }
+        }
         if (!op.diagonal) {
           const int lp = localpos[op.p], lq = localpos[op.q];
           d.a = (uint8_t)slot_of[lp];

@@ -225,6 +225,26 @@ __device__ __forceinline__ R pair_hop(T2 (&v)[NE], T2 (&l)[NE], R tc, uint32_t s
   return part;
 }
 
+// Gradient term 2 Im <lam|G_term|psi> of one hop term, then its inverse
+// factor on psi and lam (the reduction uses the values before the inverse;
+// the factor commutes with its own generator, so either order is exact).
+template <int A, int B, int NE, typename T2, typename R>
+__device__ __forceinline__ R pair_gradinv(T2 (&v)[NE], T2 (&l)[NE], R c, R s, R tc, uint32_t sm) {
+  R part = 0;
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    if (((e >> A) & 1) == 0 && ((e >> B) & 1) == 1) {
+      constexpr int F = (1 << A) | (1 << B);
+      const T2 u = v[e], w = v[e ^ F], lu = l[e], lw = l[e ^ F];
+      part += sflip(tc, sm, e) * ((lu.x * w.y - lu.y * w.x) + (lw.x * u.y - lw.y * u.x));
+      const R ss = sflip(s, sm, e);
+      rot(v[e], v[e ^ F], c, ss);
+      rot(l[e], l[e ^ F], c, ss);
+    }
+  }
+  return part;
+}
+
 // Dispatch a runtime slot pair (a, b) to the compile-time functions.
 #define HUB_PAIR_SWITCH(a, b, CALL)                                   \
   switch ((a) * 8 + (b)) {                                            \
@@ -334,30 +354,19 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
         }
         __syncthreads();
       }
-      base = 0;
-      gob = 0;
-#pragma unroll
-      for (int i = 0; i < kLaneBits; ++i) {
-        const uint32_t bit = (uint32_t)((lane >> i) & 1);
-        base |= bit << ph.lane[i];
-        gob |= bit << s_tbits[ph.lane[i]];
-      }
-      for (int j = 0; j < ph.nwarp; ++j) {
-        const uint32_t bit = (uint32_t)((warp >> j) & 1);
-        base |= bit << ph.warp[j];
-        gob |= bit << s_tbits[ph.warp[j]];
-      }
+      base = ph.bl[lane] | ph.bw[warp];
+      gob = ph.gl[lane] | ph.gw[warp];
       sbw = swz(base, DT);
 #pragma unroll
       for (int j = 0; j < RB; ++j) { so[j] = ph.so[j]; ss[j] = ph.ss[j]; }
       if (pi == 0) {  // global load (the lanes are the 5 low tile bits)
+        const T2* src = reinterpret_cast<const T2*>((sw.flags & SW_CKPT_READ) ? a.ckpt : a.psi);
 #pragma unroll
         for (int e = 0; e < NE; ++e) {
           const uint32_t off = gob | comb<RB>(so, e);
           if (sw.flags & SW_PREP) {
             v[e] = mk<T2, R>(prep_amp<R>(a.prep, sdt, sbase | off, inst), (R)0);
           } else {
-            const T2* src = reinterpret_cast<const T2*>((sw.flags & SW_CKPT_READ) ? a.ckpt : a.psi);
             v[e] = src[gbase + off];
           }
           if (NV == 2) {
@@ -381,7 +390,7 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
         const int kind = (int)(w0.x & 255u), flags = (int)((w0.x >> 8) & 255u);
         const int oa = (int)((w0.x >> 16) & 255u), ob = (int)(w0.x >> 24);
         const int idx = (int)w1.x, slot = (int)w1.y;
-        if (kind == OP_GRAD_HOP || kind == OP_GRAD_DIAG) {
+        if (kind == OP_GRAD_HOP || kind == OP_GRAD_DIAG || kind == OP_GRADINV_HOP || kind == OP_GRADINV_DIAG) {
           if (slot != rslot) {
             if (rslot >= 0) cta_add(acc, rslot, (double)racc);
             racc = 0;
@@ -405,6 +414,54 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
   }
             HUB_PAIR_SWITCH(oa, ob, HUB_GIV)
 #undef HUB_GIV
+            break;
+          }
+          case OP_GRADINV_HOP: {
+            if (NV == 2) {
+              const T2 cs = reinterpret_cast<const T2*>(a.coef)[(size_t)b * a.n_gates + idx];
+              const R tc = (R)a.hcoef[(size_t)inst * a.n_hterms + (int)w1.z];
+              const R cc = cs.x, sn = -cs.y;
+              R part = 0;
+#define HUB_GI(A, B) { part = pair_gradinv<A, B>(v, l, cc, sn, tc, sm); }
+              HUB_PAIR_SWITCH(oa, ob, HUB_GI)
+#undef HUB_GI
+              racc += (R)2 * part;
+            }
+            break;
+          }
+          case OP_GRADINV_DIAG: {
+            if (NV == 2) {
+              const DiagOpDev& d = a.diag_ops[idx];
+              const R* rtab = rtabs + (size_t)inst * a.real_stride + d.real_off;
+              const T2* ptab = reinterpret_cast<const T2*>(a.phase_tabs) + (size_t)b * a.phase_stride + d.phase_off;
+              const bool fast = d.has_x == 0 && d.n_vb == 0 && d.has_y <= 2;
+              const bool two = d.has_y == 2;
+              const uint32_t xb0 = sbase | gob;
+              R pe = 0;
+#pragma unroll
+              for (int e = 0; e < NE; ++e) {
+                const uint32_t x = xb0 | comb<RB>(so, e);
+                R dv;
+                T2 p;
+                if (fast) {
+                  const uint32_t y = x & (x >> a.s) & upm;
+                  dv = rtab[1024 + (y & 255u)];
+                  p = ptab[1024 + (y & 255u)];
+                  if (two) {
+                    dv += rtab[1280 + ((y >> 8) & 255u)];
+                    p = cmul(p, ptab[1280 + ((y >> 8) & 255u)]);
+                  }
+                } else {
+                  dv = diag_real<R>(d, rtab, x, a.s, upm);
+                  p = diag_phase<T2>(d, ptab, x, a.s, upm);
+                }
+                pe += dv * (l[e].x * v[e].y - l[e].y * v[e].x);
+                p.y = -p.y;
+                v[e] = cmul(v[e], p);
+                l[e] = cmul(l[e], p);
+              }
+              racc += (R)2 * pe;
+            }
             break;
           }
           case OP_MEAS_HOP:
