@@ -133,7 +133,7 @@ class Clocks:
 # CPU oracle on a bounded sample (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(number: int, down_configs: int = 64):
+def oracle_sample(number: int, down_configs: int = 512):
     """Time the CPU oracle's operations of one energy + adjoint-gradient
     evaluation on a sample of the sector rows and scale to a full evaluation.
 
