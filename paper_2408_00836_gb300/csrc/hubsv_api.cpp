@@ -412,6 +412,7 @@ extern "C" hub_status ans_create_multi(const hub_t* models, int32_t n_models, in
       }
     }
   }
+  if (P + 2 > kMaxSlots) return bad("too many parameters (accumulator slots are 16-bit)");
   a->P = P;
   // H hop terms: every bond, both spins; term index 2*bond + spin
   for (int b = 0; b < nb; ++b)
@@ -613,6 +614,9 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
   ka.batch = batch;
   ka.n_tiles = ((uint64_t)batch) << (n - pl->k);
   if (ka.n_tiles >= (1ull << 31)) return fail(HUB_EUNSUPPORTED, "batch too large for one launch (2^31 tiles)");
+  if ((uint64_t)batch * (uint64_t)a->n_tab >= (1ull << 31) ||
+      (uint64_t)a->n_inst * (uint64_t)a->real_stride >= (1ull << 31))
+    return fail(HUB_EUNSUPPORTED, "batch too large for one launch (32-bit table offsets)");
   ka.acc = (double*)a->d_acc.p;
   ka.n_slots = n_slots;
   ka.slot_E = a->P;

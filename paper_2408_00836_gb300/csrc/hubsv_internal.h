@@ -152,15 +152,51 @@ struct KernelArgs {
   PrepDev prep;
 };
 
+// A sweep's operations as the kernel reads them from shared memory: OpDev
+// with its table lookups done for the current batch element (coefficients,
+// table offsets) and one dense case code, so that an operation costs two
+// (c64) or three (c128) 16-byte shared loads and one indirect branch.
+//   w0 = {code | aux << 8 | slot << 16, sgn, bm_local, bm_global}
+//   hop ops, c64:  w1 = {c, s, tc, 0} (FP32)
+//   hop ops, c128: w1 = {c, s}, w2 = {tc, 0} (FP64)
+//   diagonal ops:  w1 = {phase-table offset, real-table offset, DiagOp, 0}
+// c, s: the factor's cos / sin (s negated for an inverse factor); tc: -t of
+// the matching Hamiltonian term.
+constexpr int kMaxSlots = 65535;     // slot is stored in 16 bits
+inline int res_words(int dtype) { return dtype == 0 ? 2 : 3; }
+enum ResCode : int {
+  RC_NOP = 0,
+  RC_GIV = 1,          // + pair index (0..9): factor on psi
+  RC_GIV_L = 11,       // + pair index: factor on psi and lam
+  RC_GRADINV = 21,     // + pair index: OP_GRADINV_HOP
+  RC_MEAS = 31,        // + pair index: OP_MEAS_HOP
+  RC_LAM = 41,         // + pair index: OP_LAM_HOP
+  RC_GRAD = 51,        // + pair index: OP_GRAD_HOP
+  RC_DIAG = 61,
+  RC_GRADINV_DIAG = 62,
+  RC_MEAS_DIAG = 63,
+  RC_LAM_DIAG = 64,
+  RC_GRAD_DIAG = 65,
+};
+enum ResAux : int {
+  RA_NY = 3,       // diagonal ops: number of y tables when only on-site terms (1, 2), else 0
+  RA_INV = 4,      // diagonal factor: inverse
+  RA_LAM = 8,      // diagonal factor: also on lam
+  RA_GRAD = 128,   // reduces into the accumulator slot
+};
+// Register slot pair (a < b) -> dense index 0..9.
+__host__ __device__ inline int pair_index(int a, int b) { return b * (b - 1) / 2 + a; }
+
 // Shared-memory layout of a sweep: exchange buffer(s) for the tile (none
-// when the sweep has a single phase), the CTA accumulators, and copies of
-// the sweep's phases and operations.
+// when the sweep has a single phase), the CTA accumulators, copies of the
+// sweep's phases, and its resolved operations plus one spare record (the
+// kernel loads one operation ahead).
 inline size_t sweep_smem_bytes(int dtype, int nv, int k, int n_slots, int n_phases, int n_ops) {
   const size_t amp = dtype == 0 ? 8 : 16;
   const int nbuf = n_phases > 1 ? nv : 0;
   size_t s = (size_t)nbuf * (amp << k) + 8 * (size_t)n_slots + sizeof(PhaseDev) * (size_t)n_phases;
   s = (s + 15) & ~(size_t)15;                  // operations are read as 16-byte words
-  return s + sizeof(OpDev) * (size_t)n_ops;
+  return s + 16 * (size_t)res_words(dtype) * (size_t)(n_ops + 1);
 }
 
 // Swizzle of tile-local indices in the exchange buffer: XOR the low bits

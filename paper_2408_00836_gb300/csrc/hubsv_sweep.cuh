@@ -245,21 +245,103 @@ __device__ __forceinline__ R pair_gradinv(T2 (&v)[NE], T2 (&l)[NE], R c, R s, R 
   return part;
 }
 
-// Dispatch a runtime slot pair (a, b) to the compile-time functions.
-#define HUB_PAIR_SWITCH(a, b, CALL)                                   \
-  switch ((a) * 8 + (b)) {                                            \
-    case 0 * 8 + 1: CALL(0, 1); break;                                \
-    case 0 * 8 + 2: if constexpr (RB > 2) { CALL(0, 2); } break;      \
-    case 1 * 8 + 2: if constexpr (RB > 2) { CALL(1, 2); } break;      \
-    case 0 * 8 + 3: if constexpr (RB > 3) { CALL(0, 3); } break;      \
-    case 1 * 8 + 3: if constexpr (RB > 3) { CALL(1, 3); } break;      \
-    case 2 * 8 + 3: if constexpr (RB > 3) { CALL(2, 3); } break;      \
-    case 0 * 8 + 4: if constexpr (RB > 4) { CALL(0, 4); } break;      \
-    case 1 * 8 + 4: if constexpr (RB > 4) { CALL(1, 4); } break;      \
-    case 2 * 8 + 4: if constexpr (RB > 4) { CALL(2, 4); } break;      \
-    case 3 * 8 + 4: if constexpr (RB > 4) { CALL(3, 4); } break;      \
-    default: break;                                                   \
+// Case labels of the ten register slot pairs (a, b), a < b, for one
+// operation class starting at code BASE (see ResCode / pair_index).
+#define HUB_PAIRS(BASE, CALL)                                       \
+  case (BASE) + 0: { CALL(0, 1) } break;                            \
+  case (BASE) + 1: if constexpr (RB > 2) { CALL(0, 2) } break;      \
+  case (BASE) + 2: if constexpr (RB > 2) { CALL(1, 2) } break;      \
+  case (BASE) + 3: if constexpr (RB > 3) { CALL(0, 3) } break;      \
+  case (BASE) + 4: if constexpr (RB > 3) { CALL(1, 3) } break;      \
+  case (BASE) + 5: if constexpr (RB > 3) { CALL(2, 3) } break;      \
+  case (BASE) + 6: if constexpr (RB > 4) { CALL(0, 4) } break;      \
+  case (BASE) + 7: if constexpr (RB > 4) { CALL(1, 4) } break;      \
+  case (BASE) + 8: if constexpr (RB > 4) { CALL(2, 4) } break;      \
+  case (BASE) + 9: if constexpr (RB > 4) { CALL(3, 4) } break;
+
+__device__ __forceinline__ uint32_t f2u(float x) { return __float_as_uint(x); }
+
+// Write the resolved form of the sweep's operations for batch element b
+// (instance inst) into shared memory, plus one zero record at the end.
+// Called by the whole CTA; the caller synchronises afterwards.
+template <typename R>
+__device__ void resolve_ops(const SweepDev& sw, const KernelArgs& a, uint4* sres, int b, int inst,
+                            int* s_meas) {
+  using T2 = typename CT<R>::T2;
+  constexpr int DT = CT<R>::DT;
+  constexpr int NW = DT == 0 ? 2 : 3;
+  const int nops = sw.op_end - sw.op_begin;
+  const T2* coef = reinterpret_cast<const T2*>(a.coef) + (size_t)b * a.n_gates;
+  const double* hc = a.hcoef + (size_t)inst * a.n_hterms;
+  for (int i = threadIdx.x; i <= nops; i += blockDim.x) {
+    uint4 w[3];
+    w[0] = w[1] = w[2] = make_uint4(0u, 0u, 0u, 0u);
+    if (i < nops) {
+      const OpDev o = a.ops[sw.op_begin + i];
+      const int pidx = pair_index(o.a, o.b);
+      int code = RC_NOP, aux = 0, slot = 0;
+      bool hop = true;
+      R c = 0, s = 0, tc = 0;
+      switch (o.kind) {
+        case OP_GIV: {
+          const T2 cs = coef[o.idx];
+          c = cs.x;
+          s = (o.flags & OPF_INV) ? -cs.y : cs.y;
+          code = ((o.flags & OPF_LAM) ? RC_GIV_L : RC_GIV) + pidx;
+          break;
+        }
+        case OP_GRADINV_HOP: {
+          const T2 cs = coef[o.idx];
+          c = cs.x;
+          s = -cs.y;
+          tc = (R)hc[o.idx2];
+          code = RC_GRADINV + pidx;
+          aux = RA_GRAD;
+          slot = o.slot;
+          break;
+        }
+        case OP_MEAS_HOP: tc = (R)hc[o.idx]; code = RC_MEAS + pidx; break;
+        case OP_LAM_HOP: tc = (R)hc[o.idx]; code = RC_LAM + pidx; break;
+        case OP_GRAD_HOP: tc = (R)hc[o.idx]; code = RC_GRAD + pidx; aux = RA_GRAD; slot = o.slot; break;
+        default: {
+          hop = false;
+          const DiagOpDev& d = a.diag_ops[o.idx];
+          const bool onsite = d.has_x == 0 && d.n_vb == 0 && (d.has_y == 1 || d.has_y == 2);
+          aux = onsite ? d.has_y : 0;
+          switch (o.kind) {
+            case OP_DIAG:
+              code = RC_DIAG;
+              aux |= ((o.flags & OPF_INV) ? RA_INV : 0) | ((o.flags & OPF_LAM) ? RA_LAM : 0);
+              break;
+            case OP_GRADINV_DIAG: code = RC_GRADINV_DIAG; aux |= RA_GRAD; slot = o.slot; break;
+            case OP_MEAS_DIAG: code = RC_MEAS_DIAG; break;
+            case OP_LAM_DIAG: code = RC_LAM_DIAG; break;
+            case OP_GRAD_DIAG: code = RC_GRAD_DIAG; aux |= RA_GRAD; slot = o.slot; break;
+            default: code = RC_NOP; break;
+          }
+          w[1] = make_uint4((uint32_t)((size_t)b * a.phase_stride + d.phase_off),
+                            (uint32_t)((size_t)inst * a.real_stride + d.real_off), (uint32_t)o.idx, 0u);
+          break;
+        }
+      }
+      if (o.kind == OP_MEAS_HOP || o.kind == OP_LAM_HOP || o.kind == OP_MEAS_DIAG || o.kind == OP_LAM_DIAG)
+        *s_meas = 1;
+      w[0] = make_uint4((uint32_t)code | ((uint32_t)aux << 8) | ((uint32_t)slot << 16), o.sgn, o.bm_local,
+                        o.bm_global);
+      if (hop) {
+        if constexpr (DT == 0) {
+          w[1] = make_uint4(f2u((float)c), f2u((float)s), f2u((float)tc), 0u);
+        } else {
+          w[1] = make_uint4((uint32_t)__double2loint((double)c), (uint32_t)__double2hiint((double)c),
+                            (uint32_t)__double2loint((double)s), (uint32_t)__double2hiint((double)s));
+          w[2] = make_uint4((uint32_t)__double2loint((double)tc), (uint32_t)__double2hiint((double)tc), 0u, 0u);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NW; ++j) sres[(size_t)NW * i + j] = w[j];
   }
+}
 
 // ---------------------------------------------------------------------------
 // the sweep kernel
@@ -271,6 +353,7 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
   using T2 = typename CT<R>::T2;
   constexpr int DT = CT<R>::DT;
   constexpr int NE = 1 << RB;
+  constexpr int NW = DT == 0 ? 2 : 3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nph = sw.phase_end - sw.phase_begin;
   const uint32_t tsize = 1u << sw.k;
@@ -280,12 +363,14 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
   double* acc = reinterpret_cast<double*>(smem_raw + (size_t)nbuf * tsize * sizeof(T2));
   PhaseDev* phs = reinterpret_cast<PhaseDev*>(acc + a.n_slots);
   const size_t op_off = ((size_t)(reinterpret_cast<unsigned char*>(phs + nph) - smem_raw) + 15) & ~(size_t)15;
-  OpDev* sops = reinterpret_cast<OpDev*>(smem_raw + op_off) - sw.op_begin;   // indexed by global op id
+  uint4* sres = reinterpret_cast<uint4*>(smem_raw + op_off);   // indexed by local op index
   __shared__ int8_t s_nbits[kMaxQubits];
   __shared__ int8_t s_tbits[kMaxTileBits];
+  __shared__ int s_meas;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nth = blockDim.x;
   const R* rtabs = reinterpret_cast<const R*>(DT == 0 ? (const void*)a.real_tabs32 : (const void*)a.real_tabs);
+  const T2* ptabs = reinterpret_cast<const T2*>(a.phase_tabs);
   const R* sdt = reinterpret_cast<const R*>(DT == 0 ? (const void*)a.prep.sd32 : (const void*)a.prep.sd);
   const uint32_t upm = (uint32_t)a.upmask;
 
@@ -294,6 +379,7 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
     for (int i = 0; i < kMaxQubits; ++i) s_nbits[i] = sw.nbits[i];
 #pragma unroll
     for (int i = 0; i < kMaxTileBits; ++i) s_tbits[i] = sw.tbits[i];
+    s_meas = 0;
   }
   for (int i = tid; i < a.n_slots; i += nth) acc[i] = 0.0;
   {
@@ -301,10 +387,6 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
     int* dst = reinterpret_cast<int*>(phs);
     const int nw = nph * (int)(sizeof(PhaseDev) / sizeof(int));
     for (int i = tid; i < nw; i += nth) dst[i] = src[i];
-    const int* osrc = reinterpret_cast<const int*>(a.ops + sw.op_begin);
-    int* odst = reinterpret_cast<int*>(sops + sw.op_begin);
-    const int now = (sw.op_end - sw.op_begin) * (int)(sizeof(OpDev) / sizeof(int));
-    for (int i = tid; i < now; i += nth) odst[i] = osrc[i];
   }
   __syncthreads();
 
@@ -319,6 +401,7 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
 
   for (uint32_t tau = t0; tau < t1; ++tau) {
     const int b = (int)(tau >> sw.n_nontile);
+    const int inst = b % a.n_inst;
     if (b != cur_b) {
       if (cur_b >= 0) {
         __syncthreads();
@@ -329,22 +412,32 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
         }
         __syncthreads();
       }
+      resolve_ops<R>(sw, a, sres, b, inst, &s_meas);
+      __syncthreads();
       cur_b = b;
     }
-    const int inst = b % a.n_inst;
     // state-local indices fit in 32 bits (n <= 32)
     const uint32_t sbase = deposit_bits(tau & tl_mask, s_nbits, sw.n_nontile);
-    const uint64_t gbase = ((uint64_t)b << a.n) | sbase;
     R eacc = 0, nacc = 0, racc = 0;
     int rslot = -1;
     uint32_t base = 0;      // thread's tile-local base index in this phase
     uint32_t sbw = 0;       // its swizzled exchange index
     uint32_t gob = 0;       // its state-index bits
-    uint32_t so[RB], ss[RB];  // per-slot state-index bit and exchange index
+    // The per-slot state-index bits (so) and exchange indices (ss) of a
+    // phase are read from shared memory where they are used, so that they
+    // hold no registers during the operations.
+    // operation words, loaded one operation ahead (the records of the
+    // sweep's phases are consecutive; a zero record follows the last)
+    // (c128: the third word, tc, is read when the operation runs)
+    uint4 n0 = sres[0], n1 = sres[1];
+    const uint4* onext = sres + NW;
 
     for (int pi = 0; pi < nph; ++pi) {
       const PhaseDev& ph = phs[pi];
       if (pi > 0) {  // exchange through shared memory: old mapping out
+        uint32_t ss[RB];
+#pragma unroll
+        for (int j = 0; j < RB; ++j) ss[j] = phs[pi - 1].ss[j];
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < NE; ++e) {
@@ -357,9 +450,11 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
       base = ph.bl[lane] | ph.bw[warp];
       gob = ph.gl[lane] | ph.gw[warp];
       sbw = swz(base, DT);
-#pragma unroll
-      for (int j = 0; j < RB; ++j) { so[j] = ph.so[j]; ss[j] = ph.ss[j]; }
       if (pi == 0) {  // global load (the lanes are the 5 low tile bits)
+        const uint64_t gbase = ((uint64_t)b << a.n) | sbase;
+        uint32_t so[RB];
+#pragma unroll
+        for (int j = 0; j < RB; ++j) so[j] = ph.so[j];
         const T2* src = reinterpret_cast<const T2*>((sw.flags & SW_CKPT_READ) ? a.ckpt : a.psi);
 #pragma unroll
         for (int e = 0; e < NE; ++e) {
@@ -375,6 +470,9 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
           }
         }
       } else {        // new mapping in
+        uint32_t ss[RB];
+#pragma unroll
+        for (int j = 0; j < RB; ++j) ss[j] = ph.ss[j];
 #pragma unroll
         for (int e = 0; e < NE; ++e) {
           const uint32_t loc = sbw ^ comb<RB>(ss, e);
@@ -383,14 +481,17 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
         }
       }
 
-      for (int oi = ph.op_begin; oi < ph.op_end; ++oi) {
-        const uint4* opw = reinterpret_cast<const uint4*>(sops + oi);
-        const uint4 w0 = opw[0];
-        const uint4 w1 = opw[1];
-        const int kind = (int)(w0.x & 255u), flags = (int)((w0.x >> 8) & 255u);
-        const int oa = (int)((w0.x >> 16) & 255u), ob = (int)(w0.x >> 24);
-        const int idx = (int)w1.x, slot = (int)w1.y;
-        if (kind == OP_GRAD_HOP || kind == OP_GRAD_DIAG || kind == OP_GRADINV_HOP || kind == OP_GRADINV_DIAG) {
+      const int nops_ph = ph.op_end - ph.op_begin;
+      for (int oi = 0; oi < nops_ph; ++oi) {
+        const uint4 w0 = n0, w1 = n1;
+        uint4 w2;
+        if constexpr (NW == 3) w2 = onext[2 - NW];
+        n0 = onext[0];
+        n1 = onext[1];
+        onext += NW;
+        const int code = (int)(w0.x & 255u), aux = (int)((w0.x >> 8) & 255u);
+        if (aux & RA_GRAD) {
+          const int slot = (int)(w0.x >> 16);
           if (slot != rslot) {
             if (rslot >= 0) cta_add(acc, rslot, (double)racc);
             racc = 0;
@@ -401,59 +502,95 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
         // the thread's other tile bits and the tile's non-tile bits
         const int tpar = (__popc(base & w0.z) + __popc(sbase & w0.w)) & 1;
         const uint32_t sm = w0.y ^ (tpar ? 0xffffffffu : 0u);
-        switch (kind) {
-          case OP_GIV: {
-            const T2 cs = reinterpret_cast<const T2*>(a.coef)[(size_t)b * a.n_gates + idx];
-            const R sn = (flags & OPF_INV) ? -cs.y : cs.y;
-            const R cc = cs.x;
-            const bool dol = (NV == 2) && (flags & OPF_LAM);
-#define HUB_GIV(A, B)                       \
-  {                                         \
-    pair_giv<A, B>(v, cc, sn, sm);          \
-    if (dol) pair_giv<A, B>(l, cc, sn, sm); \
-  }
-            HUB_PAIR_SWITCH(oa, ob, HUB_GIV)
-#undef HUB_GIV
-            break;
-          }
-          case OP_GRADINV_HOP: {
-            if (NV == 2) {
-              const T2 cs = reinterpret_cast<const T2*>(a.coef)[(size_t)b * a.n_gates + idx];
-              const R tc = (R)a.hcoef[(size_t)inst * a.n_hterms + (int)w1.z];
-              const R cc = cs.x, sn = -cs.y;
-              R part = 0;
-#define HUB_GI(A, B) { part = pair_gradinv<A, B>(v, l, cc, sn, tc, sm); }
-              HUB_PAIR_SWITCH(oa, ob, HUB_GI)
-#undef HUB_GI
-              racc += (R)2 * part;
+        R c, s, tc;
+        if constexpr (DT == 0) {
+          c = __uint_as_float(w1.x);
+          s = __uint_as_float(w1.y);
+          tc = __uint_as_float(w1.z);
+        } else {
+          c = __hiloint2double((int)w1.y, (int)w1.x);
+          s = __hiloint2double((int)w1.w, (int)w1.z);
+          tc = __hiloint2double((int)w2.y, (int)w2.x);
+        }
+#define HUB_GIV1(A, B) pair_giv<A, B>(v, c, s, sm);
+#define HUB_GIV2(A, B)                                  \
+  pair_giv<A, B>(v, c, s, sm);                          \
+  if constexpr (NV == 2) pair_giv<A, B>(l, c, s, sm);
+#define HUB_GI(A, B) \
+  if constexpr (NV == 2) racc += (R)2 * pair_gradinv<A, B>(v, l, c, s, tc, sm);
+#define HUB_M0(A, B) eacc += (R)2 * pair_hop<A, B, 0>(v, l, tc, sm);
+#define HUB_M1(A, B) \
+  if constexpr (NV == 2) eacc += (R)2 * pair_hop<A, B, 1>(v, l, tc, sm);
+#define HUB_M2(A, B) \
+  if constexpr (NV == 2) racc += (R)2 * pair_hop<A, B, 2>(v, l, tc, sm);
+        switch (code) {
+          HUB_PAIRS(RC_GIV, HUB_GIV1)
+          HUB_PAIRS(RC_GIV_L, HUB_GIV2)
+          HUB_PAIRS(RC_GRADINV, HUB_GI)
+          HUB_PAIRS(RC_MEAS, HUB_M0)
+          HUB_PAIRS(RC_LAM, HUB_M1)
+          HUB_PAIRS(RC_GRAD, HUB_M2)
+          case RC_DIAG: {
+            const T2* ptab = ptabs + w1.x;
+            uint32_t so[RB];
+#pragma unroll
+            for (int j = 0; j < RB; ++j) so[j] = ph.so[j];
+            const bool inv = aux & RA_INV;
+            const bool dol = (NV == 2) && (aux & RA_LAM);
+            const uint32_t xb0 = sbase | gob;
+            const int ny = aux & RA_NY;
+            if (ny) {
+              // on-site factor only: phase of the double-occupancy pattern
+              const T2* ty = ptab + 1024;
+#pragma unroll
+              for (int e = 0; e < NE; ++e) {
+                const uint32_t x = xb0 | comb<RB>(so, e);
+                const uint32_t y = x & (x >> a.s) & upm;
+                T2 p = ty[y & 255u];
+                if (ny == 2) p = cmul(p, ty[256 + ((y >> 8) & 255u)]);
+                if (inv) p.y = -p.y;
+                v[e] = cmul(v[e], p);
+                if (dol) l[e] = cmul(l[e], p);
+              }
+              break;
+            }
+            const DiagOpDev& d = a.diag_ops[w1.z];
+#pragma unroll
+            for (int e = 0; e < NE; ++e) {
+              T2 p = diag_phase<T2>(d, ptab, xb0 | comb<RB>(so, e), a.s, upm);
+              if (inv) p.y = -p.y;
+              v[e] = cmul(v[e], p);
+              if (dol) l[e] = cmul(l[e], p);
             }
             break;
           }
-          case OP_GRADINV_DIAG: {
-            if (NV == 2) {
-              const DiagOpDev& d = a.diag_ops[idx];
-              const R* rtab = rtabs + (size_t)inst * a.real_stride + d.real_off;
-              const T2* ptab = reinterpret_cast<const T2*>(a.phase_tabs) + (size_t)b * a.phase_stride + d.phase_off;
-              const bool fast = d.has_x == 0 && d.n_vb == 0 && d.has_y <= 2;
-              const bool two = d.has_y == 2;
+          case RC_GRADINV_DIAG: {
+            if constexpr (NV == 2) {
+              const T2* ptab = ptabs + w1.x;
+            uint32_t so[RB];
+#pragma unroll
+            for (int j = 0; j < RB; ++j) so[j] = ph.so[j];
+              const R* rtab = rtabs + w1.y;
+              const int ny = aux & RA_NY;
               const uint32_t xb0 = sbase | gob;
+              const DiagOpDev* dp = ny ? nullptr : &a.diag_ops[w1.z];
               R pe = 0;
 #pragma unroll
               for (int e = 0; e < NE; ++e) {
                 const uint32_t x = xb0 | comb<RB>(so, e);
                 R dv;
                 T2 p;
-                if (fast) {
+                if (ny) {
                   const uint32_t y = x & (x >> a.s) & upm;
                   dv = rtab[1024 + (y & 255u)];
                   p = ptab[1024 + (y & 255u)];
-                  if (two) {
+                  if (ny == 2) {
                     dv += rtab[1280 + ((y >> 8) & 255u)];
                     p = cmul(p, ptab[1280 + ((y >> 8) & 255u)]);
                   }
                 } else {
-                  dv = diag_real<R>(d, rtab, x, a.s, upm);
-                  p = diag_phase<T2>(d, ptab, x, a.s, upm);
+                  dv = diag_real<R>(*dp, rtab, x, a.s, upm);
+                  p = diag_phase<T2>(*dp, ptab, x, a.s, upm);
                 }
                 pe += dv * (l[e].x * v[e].y - l[e].y * v[e].x);
                 p.y = -p.y;
@@ -464,113 +601,69 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
             }
             break;
           }
-          case OP_MEAS_HOP:
-          case OP_LAM_HOP:
-          case OP_GRAD_HOP: {
-            const R tc = (R)a.hcoef[(size_t)inst * a.n_hterms + idx];
-            R part = 0;
-            if (kind == OP_MEAS_HOP) {
-#define HUB_M0(A, B) { part = pair_hop<A, B, 0>(v, l, tc, sm); }
-              HUB_PAIR_SWITCH(oa, ob, HUB_M0)
-#undef HUB_M0
-              eacc += (R)2 * part;
-            } else if (kind == OP_LAM_HOP) {
-              if (NV == 2) {
-#define HUB_M1(A, B) { part = pair_hop<A, B, 1>(v, l, tc, sm); }
-                HUB_PAIR_SWITCH(oa, ob, HUB_M1)
-#undef HUB_M1
-              }
-              eacc += (R)2 * part;
-            } else {
-              if (NV == 2) {
-#define HUB_M2(A, B) { part = pair_hop<A, B, 2>(v, l, tc, sm); }
-                HUB_PAIR_SWITCH(oa, ob, HUB_M2)
-#undef HUB_M2
-              }
-              racc += (R)2 * part;
-            }
-            break;
-          }
-          case OP_DIAG: {
-            const DiagOpDev& d = a.diag_ops[idx];
-            const T2* ptab = reinterpret_cast<const T2*>(a.phase_tabs) + (size_t)b * a.phase_stride + d.phase_off;
-            const bool inv = flags & OPF_INV;
-            const bool dol = (NV == 2) && (flags & OPF_LAM);
-            const uint32_t xb0 = sbase | gob;
-            if (d.has_x == 0 && d.n_vb == 0 && d.has_y <= 2) {
-              // on-site factor only: phase of the double-occupancy pattern
-              const T2* ty = ptab + 1024;
-              const bool two = d.has_y == 2;
+          case RC_MEAS_DIAG:
+          case RC_LAM_DIAG:
+          case RC_GRAD_DIAG: {
+            const R* rtab = rtabs + w1.y;
+            uint32_t so[RB];
 #pragma unroll
-              for (int e = 0; e < NE; ++e) {
-                const uint32_t x = xb0 | comb<RB>(so, e);
-                const uint32_t y = x & (x >> a.s) & upm;
-                T2 p = ty[y & 255u];
-                if (two) p = cmul(p, ty[256 + ((y >> 8) & 255u)]);
-                if (inv) p.y = -p.y;
-                v[e] = cmul(v[e], p);
-                if (dol) l[e] = cmul(l[e], p);
-              }
-              break;
-            }
-#pragma unroll
-            for (int e = 0; e < NE; ++e) {
-              T2 p = diag_phase<T2>(d, ptab, xb0 | comb<RB>(so, e), a.s, upm);
-              if (inv) p.y = -p.y;
-              v[e] = cmul(v[e], p);
-              if (dol) l[e] = cmul(l[e], p);
-            }
-            break;
-          }
-          case OP_MEAS_DIAG:
-          case OP_LAM_DIAG:
-          case OP_GRAD_DIAG: {
-            const DiagOpDev& d = a.diag_ops[idx];
-            const R* rtab = rtabs + (size_t)inst * a.real_stride + d.real_off;
+            for (int j = 0; j < RB; ++j) so[j] = ph.so[j];
+            const int ny = aux & RA_NY;
+            const DiagOpDev* dp = ny ? nullptr : &a.diag_ops[w1.z];
             R pe = 0, pn = 0;
-            const bool fast = d.has_x == 0 && d.n_vb == 0 && d.has_y <= 2;
-            const bool two = d.has_y == 2;
             const uint32_t xb0 = sbase | gob;
 #pragma unroll
             for (int e = 0; e < NE; ++e) {
               const uint32_t x = xb0 | comb<RB>(so, e);
               R dv;
-              if (fast) {   // on-site terms only
+              if (ny) {   // on-site terms only
                 const uint32_t y = x & (x >> a.s) & upm;
                 dv = rtab[1024 + (y & 255u)];
-                if (two) dv += rtab[1280 + ((y >> 8) & 255u)];
+                if (ny == 2) dv += rtab[1280 + ((y >> 8) & 255u)];
               } else {
-                dv = diag_real<R>(d, rtab, x, a.s, upm);
+                dv = diag_real<R>(*dp, rtab, x, a.s, upm);
               }
               const T2 u = v[e];
-              if (kind == OP_GRAD_DIAG) {
+              if (code == RC_GRAD_DIAG) {
                 if (NV == 2) pe += dv * (l[e].x * u.y - l[e].y * u.x);
               } else {
                 const R m2 = u.x * u.x + u.y * u.y;
                 pe += dv * m2;
                 pn += m2;
-                if (NV == 2 && kind == OP_LAM_DIAG) {
+                if (NV == 2 && code == RC_LAM_DIAG) {
                   l[e].x += dv * u.x;
                   l[e].y += dv * u.y;
                 }
               }
             }
-            if (kind == OP_GRAD_DIAG) racc += (R)2 * pe;
+            if (code == RC_GRAD_DIAG) racc += (R)2 * pe;
             else { eacc += pe; nacc += pn; }
             break;
           }
           default: break;
         }
+#undef HUB_GIV1
+#undef HUB_GIV2
+#undef HUB_GI
+#undef HUB_M0
+#undef HUB_M1
+#undef HUB_M2
       }
     }
     if (rslot >= 0) cta_add(acc, rslot, (double)racc);
-    cta_add(acc, a.slot_E, (double)eacc);
-    cta_add(acc, a.slot_N, (double)nacc);
+    if (s_meas) {
+      cta_add(acc, a.slot_E, (double)eacc);
+      cta_add(acc, a.slot_N, (double)nacc);
+    }
 
     // ---- store from registers (the last phase has the low bits on the lanes) ----
     const bool wp = sw.flags & SW_WRITE_PSI, wc = sw.flags & SW_CKPT_WRITE;
     const bool wl = (NV == 2) && (sw.flags & SW_WRITE_LAM);
     if (wp || wc || wl) {
+      const uint64_t gbase = ((uint64_t)b << a.n) | sbase;
+      uint32_t so[RB];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) so[j] = phs[nph - 1].so[j];
 #pragma unroll
       for (int e = 0; e < NE; ++e) {
         const uint64_t g = gbase + (gob | comb<RB>(so, e));
