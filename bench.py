@@ -228,6 +228,8 @@ def run_gpu(args, rank, world, dist):
         tune = {"best_log2_tile": best, "ms": {str(k): round(v, 2) for k, v in times.items()}}
     elif args.tile:
         a.set_tile(dtype, args.tile)
+    if args.runs:
+        a.set_runs(dtype, args.runs)
     theta_h = torch.tensor(w.theta(), dtype=torch.float64).pin_memory()
     theta = theta_h.to(dev)
     psi = torch.empty((batch, 1 << w.n_qubits), dtype=tdt, device=dev)
@@ -327,6 +329,8 @@ def run_gpu(args, rank, world, dist):
         out["autotune"] = tune
     elif args.tile:
         out["config"]["log2_tile"] = args.tile
+    if args.runs:
+        out["config"]["log2_run"] = args.runs
     del psi, lam
     torch.cuda.empty_cache()
     if args.c128 and dtype == H.C64 and rank == 0:
@@ -376,6 +380,7 @@ def main():
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
     ap.add_argument("--tile", type=int, default=0, help="log2 tile override (0 = planner default)")
     ap.add_argument("--autotune", action="store_true", help="pick the tile size by timing first")
+    ap.add_argument("--runs", type=int, default=0, help="log2 contiguous amplitudes per HBM run (0 = default)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -242,6 +242,10 @@ class Ansatz:
     def set_tile(self, dtype: int, log2_tile: int):
         check(lib().ans_set_tile(self._h, dtype, log2_tile))
 
+    def set_runs(self, dtype: int, log2_run: int):
+        """log2 of the contiguous amplitudes per HBM run (0 = automatic)."""
+        check(lib().ans_set_runs(self._h, dtype, log2_run))
+
 
 def sync(stream=None):
     check(lib().hub_sync(_stream(stream)))

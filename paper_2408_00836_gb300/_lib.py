@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "HUB_OK", 1: "HUB_EINVAL", 2: "HUB_EUNSUPPORTED", 3: "HUB_ENO
 EXPORTS = [
     "hub_square_lattice", "hub_create", "hub_destroy", "ans_create", "ans_create_multi",
     "ans_destroy", "ans_num_params", "ans_num_qubits", "state_prepare", "energy",
-    "energy_grad", "hub_apply_h", "ans_plan_stats", "ans_set_tile", "hub_sync",
+    "energy_grad", "hub_apply_h", "ans_plan_stats", "ans_set_tile", "ans_set_runs", "hub_sync",
     "hub_last_error", "ans_plan_describe", "ans_profile", "ans_profile_read", "energy_noalloc",
 ]
 
@@ -75,6 +75,7 @@ def lib():
         "hub_apply_h": (st, [c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_void_p]),
         "ans_plan_stats": (st, [c_void_p, c_int32, c_int32, c_uint32, POINTER(c_int32), POINTER(c_double)]),
         "ans_set_tile": (st, [c_void_p, c_int32, c_int32]),
+        "ans_set_runs": (st, [c_void_p, c_int32, c_int32]),
         "ans_plan_describe": (st, [c_void_p, c_int32, c_int32, c_uint32, POINTER(c_int64), c_int32,
                                    POINTER(c_int32)]),
         "ans_profile": (st, [c_void_p, c_int32]),

@@ -536,6 +536,16 @@ extern "C" hub_status ans_set_tile(ans_t a, int32_t dtype, int32_t log2_tile) {
   return HUB_OK;
 }
 
+extern "C" hub_status ans_set_runs(ans_t a, int32_t dtype, int32_t log2_run) {
+  if (!a || (dtype != HUB_C64 && dtype != HUB_C128)) return fail(HUB_EINVAL, "ans_set_runs: bad arguments");
+  if (log2_run != 0 && (log2_run < 1 || log2_run > 5))
+    return fail(HUB_EINVAL, "ans_set_runs: log2_run must be 0 or in [1, 5]");
+  a->run_override[dtype] = log2_run;
+  for (auto& kv : a->plans) delete kv.second;
+  a->plans.clear();
+  return HUB_OK;
+}
+
 namespace {
 
 hub_status ensure_device(hub_ansatz* a) {

@@ -101,6 +101,7 @@ struct hub_ansatz {
   hubsv::DevBuf d_coef[2], d_phase[2], d_acc;
   std::map<int, hubsv::Plan*> plans;     // key = which*16 + dtype*4 + flags
   int tile_override[2] = {0, 0};
+  int run_override[2] = {0, 0};         // log2 contiguous amplitudes per run (0 = default)
   bool dev_ready = false;
   struct ProfRec { cudaEvent_t e0, e1; int nv, dtype; double bytes; };
   bool prof = false;
@@ -110,6 +111,13 @@ struct hub_ansatz {
 };
 
 namespace hubsv {
+// Default tile and run bits (log2 of the amplitudes per tile, and of the
+// contiguous amplitudes a warp reads or writes as one piece), chosen by
+// timing the 32-qubit energy + gradient on GB300: c64 tiles of 2^12 (two
+// CTAs of 256 threads per SM) with 128-byte runs; c128 tiles of 2^12 (one
+// CTA of 512 threads) with 128-byte runs.
+inline int default_tile_bits(int dtype) { return dtype == HUB_C64 ? 12 : 12; }
+inline int default_run_bits(int dtype) { return dtype == HUB_C64 ? 4 : 3; }
 uint64_t diag_support(const hub_ansatz* a, int di);
 hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*& out);
 }  // namespace hubsv

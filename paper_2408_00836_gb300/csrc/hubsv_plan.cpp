@@ -9,8 +9,8 @@
 // the sequence within those rules into
 //
 //   sweeps  -- passes over the vector; a sweep holds a tile of k index bits
-//              (always including the 5 lowest) and runs every operation whose
-//              modes lie in the tile;
+//              (always including the c lowest, the run bits) and runs every
+//              operation whose modes lie in the tile;
 //   phases  -- within a sweep, groups of operations whose modes are r of the
 //              tile bits, run in registers (one thread holds 2^r amplitudes).
 //
@@ -177,26 +177,31 @@ int rank_gf2(std::vector<uint32_t> cols) {
   return r;
 }
 
-// Lane bits of a middle phase: 5 of the free tile bits whose first 4 (c64)
-// or 3 (c128) columns of the swizzle map are independent, so a warp's
-// shared-memory accesses hit distinct banks.
-void choose_lanes(uint32_t free_bits, int dtype, uint8_t* lanes, uint8_t* warps, int& nwarp) {
-  std::vector<int> fb;
-  for (int b = 0; b < 32; ++b)
-    if (free_bits >> b & 1) fb.push_back(b);
+// Lane bits of a phase: 5 of the free tile bits, including the `required`
+// ones (the run bits, in the first and last phase, so that a warp's global
+// accesses are whole runs), ordered so that the first 4 (c64) or 3 (c128)
+// columns of the swizzle map are independent: a warp's shared-memory
+// accesses then hit distinct banks.
+void choose_lanes(uint32_t free_bits, uint32_t required, int dtype, uint8_t* lanes, uint8_t* warps,
+                  int& nwarp) {
+  std::vector<int> req, fb;
+  for (int b = 0; b < 32; ++b) {
+    if (required >> b & 1) req.push_back(b);
+    else if (free_bits >> b & 1) fb.push_back(b);
+  }
   const int need = dtype == 0 ? 4 : 3;
   const uint32_t m = dtype == 0 ? 15u : 7u;
-  std::vector<int> best(fb.begin(), fb.begin() + kLaneBits);
+  const int nsel = kLaneBits - (int)req.size();
+  std::vector<int> best(req);
+  best.insert(best.end(), fb.begin(), fb.begin() + nsel);
   const int nfb = (int)fb.size();
   bool found = false;
-  // combinations of 5 of the free bits, the first `need` checked for rank
-  std::vector<int> idx(kLaneBits);
-  for (int i = 0; i < kLaneBits; ++i) idx[i] = i;
+  // combinations of nsel of the other free bits; orderings checked for rank
+  std::vector<int> idx(nsel);
+  for (int i = 0; i < nsel; ++i) idx[i] = i;
   while (!found) {
-    std::vector<int> cand;
-    for (int i : idx) cand.push_back(fb[i]);
-    // try orderings that put an independent set first
-    std::vector<int> perm(cand);
+    std::vector<int> perm(req);
+    for (int i : idx) perm.push_back(fb[i]);
     std::sort(perm.begin(), perm.end());
     do {
       std::vector<uint32_t> cols;
@@ -204,17 +209,17 @@ void choose_lanes(uint32_t free_bits, int dtype, uint8_t* lanes, uint8_t* warps,
       if (rank_gf2(cols) == need) { best = perm; found = true; break; }
     } while (std::next_permutation(perm.begin(), perm.end()));
     // next combination
-    int i = kLaneBits - 1;
-    while (i >= 0 && idx[i] == nfb - kLaneBits + i) --i;
+    int i = nsel - 1;
+    while (i >= 0 && idx[i] == nfb - nsel + i) --i;
     if (i < 0) break;
     ++idx[i];
-    for (int j = i + 1; j < kLaneBits; ++j) idx[j] = idx[j - 1] + 1;
+    for (int j = i + 1; j < nsel; ++j) idx[j] = idx[j - 1] + 1;
   }
   uint32_t used = 0;
   for (int j = 0; j < kLaneBits; ++j) { lanes[j] = (uint8_t)best[j]; used |= 1u << best[j]; }
   nwarp = 0;
-  for (int b : fb)
-    if (!(used >> b & 1)) warps[nwarp++] = (uint8_t)b;
+  for (int b = 0; b < 32; ++b)
+    if ((free_bits >> b & 1) && !(used >> b & 1)) warps[nwarp++] = (uint8_t)b;
 }
 
 }  // namespace
@@ -222,11 +227,14 @@ void choose_lanes(uint32_t free_bits, int dtype, uint8_t* lanes, uint8_t* warps,
 hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*& out) {
   const int n = a->n;
   if (n < kLaneBits + 1) return fail(HUB_EUNSUPPORTED, "need at least 6 qubits (3 sites)");
-  int k = a->tile_override[dtype] ? a->tile_override[dtype] : (dtype == HUB_C64 ? 13 : 12);
+  int k = a->tile_override[dtype] ? a->tile_override[dtype] : default_tile_bits(dtype);
   // threads = 32 << (k - 5 - r) must stay <= 512 for every sweep
   k = std::min(k, kLaneBits + 4 + std::min(max_reg_bits(dtype, 1), max_reg_bits(dtype, 2)));
   k = std::min(k, n);
-  const uint64_t cmask = (1ull << kLaneBits) - 1ull;
+  // run bits: the lowest index bits, always in the tile, so that global
+  // accesses come in runs of 2^c contiguous amplitudes
+  const int c = std::min(k, a->run_override[dtype] ? a->run_override[dtype] : default_run_bits(dtype));
+  const uint64_t cmask = (1ull << c) - 1ull;
   const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
   uint64_t upm = 0, dnm = 0;
   for (int i = 0; i < a->L; ++i) {
@@ -323,7 +331,7 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
     }
     sw.n_nontile = nn;
     // ---- register phases ----
-    const uint32_t low = (1u << kLaneBits) - 1u;
+    const uint32_t low = (uint32_t)cmask;   // tile-local bits 0..c-1 are the run bits
     const uint32_t tmask = (k >= 32) ? ~0u : ((1u << k) - 1u);
     auto need_local = [&](const SeqOp& op) -> uint64_t {
       return op.diagonal ? 0ull : ((1ull << localpos[op.p]) | (1ull << localpos[op.q]));
@@ -381,13 +389,7 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
       }
       const uint32_t freeb = tmask & ~P.S;
       int nw = 0;
-      if (edge && !(P.S & low)) {
-        for (int j = 0; j < kLaneBits; ++j) pd.lane[j] = (uint8_t)j;
-        for (int bit = kLaneBits; bit < k; ++bit)
-          if (freeb >> bit & 1) pd.warp[nw++] = (uint8_t)bit;
-      } else {
-        choose_lanes(freeb, dtype, pd.lane, pd.warp, nw);
-      }
+      choose_lanes(freeb, (edge && !(P.S & low)) ? low : 0u, dtype, pd.lane, pd.warp, nw);
       pd.nwarp = (uint8_t)nw;
       for (int v = 0; v < 32; ++v)
         for (int j = 0; j < kLaneBits; ++j)

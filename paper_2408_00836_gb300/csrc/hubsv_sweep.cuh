@@ -4,16 +4,18 @@
 // One kernel, sweep_kernel, does all amplitude work.  A sweep streams the
 // whole 2^n (x batch) amplitude vector once, one tile of 2^k amplitudes at a
 // time.  A tile holds every amplitude whose index agrees with the tile's
-// base on the non-tile bits; the tile bits always include the 5 lowest bits,
-// so a warp loads and stores runs of 32 contiguous amplitudes (256 B in c64).
+// base on the non-tile bits; the tile bits always include the c lowest bits
+// (the run bits), so a warp loads and stores whole runs of 2^c contiguous
+// amplitudes (128 B by default).  Fewer run bits leave more tile bits to
+// the operations, and so fewer sweeps.
 //
 // Inside a tile the amplitudes live in registers: in a register phase each
 // thread holds the 2^r amplitudes that differ in r chosen tile bits (its
 // register slots), and every operation whose bits are register slots runs
 // without touching memory.  Between phases the tile is exchanged through
 // shared memory (XOR-swizzled against bank conflicts) to bring other bits
-// into the register slots.  The first and last phase put the 5 low bits on
-// the lanes, so global loads and stores go straight to and from registers.
+// into the register slots.  The first and last phase put the run bits on
+// lanes, so global loads and stores go straight to and from registers.
 //
 // Operations (chosen and ordered by the host planner):
 //  * OP_GIV: the factor exp(-i theta G) of one hopping term of Eq. 7,
@@ -450,7 +452,7 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
       base = ph.bl[lane] | ph.bw[warp];
       gob = ph.gl[lane] | ph.gw[warp];
       sbw = swz(base, DT);
-      if (pi == 0) {  // global load (the lanes are the 5 low tile bits)
+      if (pi == 0) {  // global load (the run bits are on lanes)
         const uint64_t gbase = ((uint64_t)b << a.n) | sbase;
         uint32_t so[RB];
 #pragma unroll
@@ -656,7 +658,7 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
       cta_add(acc, a.slot_N, (double)nacc);
     }
 
-    // ---- store from registers (the last phase has the low bits on the lanes) ----
+    // ---- store from registers (the last phase has the run bits on lanes) ----
     const bool wp = sw.flags & SW_WRITE_PSI, wc = sw.flags & SW_CKPT_WRITE;
     const bool wl = (NV == 2) && (sw.flags & SW_WRITE_LAM);
     if (wp || wc || wl) {

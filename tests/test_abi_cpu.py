@@ -158,7 +158,8 @@ def test_schedules_are_valid(number, which):
     groups = H.hva_groups(bonds, cls, w.n_sites, w.layers, w.classes)
     a = H.Ansatz(m, groups, w.layers)
     seq = _sequence(groups, bonds, w.n_sites, which)
-    for dtype, k, c in [(H.C64, 13, 5), (H.C128, 12, 4)]:
+    # default tiles and runs: 2^12 amplitudes, 128-byte runs (c = 4 / 3)
+    for dtype, k, c in [(H.C64, 12, 4), (H.C128, 12, 3)]:
         k = min(k, w.n_qubits)
         plan = a.plan_describe(which, dtype)
         _check_schedule(plan, seq, w.n_qubits, k, min(c, k), set(range(w.n_qubits)))
@@ -167,4 +168,10 @@ def test_schedules_are_valid(number, which):
         plan = a.plan_describe(which, H.C64)
         # the planner caps c64 tiles at 13 bits (512 threads x 16 amplitudes)
         k_eff = min(kk, 13, w.n_qubits)
-        _check_schedule(plan, seq, w.n_qubits, k_eff, min(5, k_eff), set(range(w.n_qubits)))
+        _check_schedule(plan, seq, w.n_qubits, k_eff, min(4, k_eff), set(range(w.n_qubits)))
+    a.set_tile(H.C64, 0)
+    for runs in (2, 3, 5):
+        a.set_runs(H.C64, runs)
+        plan = a.plan_describe(which, H.C64)
+        k_eff = min(12, w.n_qubits)
+        _check_schedule(plan, seq, w.n_qubits, k_eff, min(runs, k_eff), set(range(w.n_qubits)))
