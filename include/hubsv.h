@@ -240,7 +240,7 @@ HUB_API hub_status ans_set_tile(ans_t ans, int32_t dtype, int32_t log2_tile);
 
 /* Run length override (log2 of the contiguous amplitudes that a warp moves
  * between HBM and registers as one piece; the lowest log2_run index bits are
- * in every tile).  0 = automatic (128-byte runs: 4 in c64, 3 in c128); else
+ * in every tile).  0 = automatic (3: 64-byte runs in c64, 128-byte in c128); else
  * 1..5.  Shorter runs leave more tile bits free for the operations (fewer
  * sweeps) at the cost of less contiguous HBM traffic.                       */
 HUB_API hub_status ans_set_runs(ans_t ans, int32_t dtype, int32_t log2_run);

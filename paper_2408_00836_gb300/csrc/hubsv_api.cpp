@@ -598,6 +598,14 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
                          a->n_inst, st),
              "coefficient kernel");
   }
+  if (pl->sector) {
+    // sweeps visit only the tiles that meet the sector; the amplitudes
+    // outside it, which those tiles also hold, must read as zero
+    const size_t vb = (size_t)batch * ((size_t)1 << n) * (dtype == HUB_C64 ? 8 : 16);
+    HUB_CUDA(cudaMemsetAsync(psi, 0, vb, st), "clear psi");
+    if (lam) HUB_CUDA(cudaMemsetAsync(lam, 0, vb, st), "clear lam");
+    if (ckpt) HUB_CUDA(cudaMemsetAsync(ckpt, 0, vb, st), "clear checkpoint");
+  }
   KernelArgs ka;
   std::memset(&ka, 0, sizeof(ka));
   ka.psi = psi;
@@ -655,7 +663,8 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
     per_sm = std::min(per_sm, 65536 / (regs * threads));
     per_sm = std::max(per_sm, 1);
     uint64_t grid = (uint64_t)sms * per_sm;
-    grid = std::min<uint64_t>(grid, ka.n_tiles);
+    const uint64_t sweep_tiles = sw.sector ? (uint64_t)batch * sw.live : ka.n_tiles;
+    grid = std::min<uint64_t>(grid, std::max<uint64_t>(1, sweep_tiles));
     hub_ansatz::ProfRec rec{};
     if (a->prof) {
       HUB_CUDA(cudaEventCreate(&rec.e0), "cudaEventCreate");
@@ -671,7 +680,8 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
                           ((f & SW_CKPT_WRITE) ? 1 : 0) + ((f & SW_CKPT_READ) ? 1 : 0);
       rec.nv = nv;
       rec.dtype = dtype;
-      rec.bytes = (double)nvec_io * (double)(dtype == HUB_C64 ? 8 : 16) * (double)(1ull << n) * (double)batch;
+      rec.bytes = (double)nvec_io * (double)(dtype == HUB_C64 ? 8 : 16) * (double)batch *
+                  (sw.sector ? (double)sw.live * (double)(1ull << sw.k) : (double)(1ull << n));
       a->prof_recs.push_back(rec);
     }
   }

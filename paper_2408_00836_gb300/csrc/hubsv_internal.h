@@ -111,7 +111,36 @@ struct SweepDev {
   int8_t tbits[kMaxTileBits];     // tile bit positions, ascending
   int8_t nbits[kMaxQubits];       // non-tile bit positions, ascending
   int32_t n_nontile;
+  // Sector tiles: every operation conserves the numbers of up and down
+  // electrons, so when the initial state is generated in the (N_up, N_dn)
+  // sector, a tile whose non-tile bits hold too many or too few electrons
+  // of either spin for the sector is zero throughout the call.  With sector
+  // = 1 the sweep visits only the other tiles ("live" tiles): their
+  // non-tile up bits (positions upnt) carry lo_u..hi_u electrons, their
+  // down bits (dnnt) lo_d..hi_d; live tile j of a state has up pattern
+  // j / cnt_d and down pattern j % cnt_d, each ranked by electron count and
+  // then in colex order.
+  int32_t sector;
+  int32_t nu, nd;                 // non-tile up / down bits
+  int32_t lo_u, hi_u, lo_d, hi_d;
+  uint32_t cnt_d;                 // live down patterns
+  uint32_t live;                  // live tiles per state
+  int8_t upnt[kMaxQubits];        // non-tile up-mode bit positions, ascending
+  int8_t dnnt[kMaxQubits];        // non-tile down-mode bit positions, ascending
 };
+
+// Binomial coefficients C(n, k), n, k <= 32 (C(32, 16) < 2^32).
+struct BinomTable {
+  uint32_t c[kMaxQubits + 1][kMaxQubits + 1];
+};
+constexpr BinomTable make_binom_table() {
+  BinomTable t{};
+  for (int n = 0; n <= kMaxQubits; ++n) {
+    t.c[n][0] = 1;
+    for (int k = 1; k <= n; ++k) t.c[n][k] = t.c[n - 1][k - 1] + t.c[n - 1][k];
+  }
+  return t;
+}
 
 struct PrepDev {
   int32_t kind;            // 0 Slater, 1 Neel

@@ -141,6 +141,8 @@ extern "C" hub_status energy_noalloc(ans_t a, const double* theta, void* psi, do
   if (ce != cudaSuccess) return cuda_fail(ce, "energy_noalloc: table copy");
   // the accumulators keep the previous call's sums: clear them
   HUB_CUDA(launch_zero(reinterpret_cast<double*>(S + o_acc), batch * n_slots, s), "energy_noalloc: zero accumulators");
+  if (pl->sector)   // sweeps visit only sector tiles: the rest of psi must read as zero
+    HUB_CUDA(cudaMemsetAsync(psi, 0, (size_t)batch * ((size_t)1 << n) * r2, s), "energy_noalloc: clear psi");
   HUB_CUDA(launch_coef(dtype, theta, a->P, reinterpret_cast<const int32_t*>(S + o_gp),
                        reinterpret_cast<const double*>(S + o_gt), a->n_gates, S + o_cf,
                        reinterpret_cast<const int32_t*>(S + o_tp), reinterpret_cast<const double*>(S + o_tv),
@@ -196,7 +198,8 @@ extern "C" hub_status energy_noalloc(ans_t a, const double* theta, void* psi, do
     per_sm = std::min(per_sm, 2048 / threads);
     per_sm = std::min(per_sm, 65536 / (regs * threads));
     per_sm = std::max(per_sm, 1);
-    const uint64_t grid = std::min<uint64_t>((uint64_t)sms * per_sm, n_tiles);
+    const uint64_t sweep_tiles = sw.sector ? (uint64_t)batch * sw.live : n_tiles;
+    const uint64_t grid = std::min<uint64_t>((uint64_t)sms * per_sm, std::max<uint64_t>(1, sweep_tiles));
     HUB_CUDA(launch_sweep(dtype, sw, ka, (int)grid, smem, s), "energy_noalloc: sweep kernel launch");
   }
   HUB_CUDA(launch_finalize(ka.acc, n_slots, a->P, a->P, E, nullptr, batch, s), "energy_noalloc: finalize kernel");

@@ -283,6 +283,10 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
   Plan* pl = new Plan();
   pl->k = k;
   const bool prep = which == 3 || (flags & HUB_FLAG_PREP_FUSED) != 0;
+  // an initial state generated here lies in the (N_up, N_dn) sector, and
+  // every operation keeps it there: visit only the tiles that meet it
+  pl->sector = prep && which != 2;
+  const BinomTable binom = make_binom_table();
   const bool keep = which == 3 || (flags & HUB_FLAG_KEEP_STATE) != 0;
   bool lam_live = false;
   const double amp = dtype == HUB_C64 ? 8.0 : 16.0;
@@ -330,6 +334,30 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
       else { localpos[b] = -1; sw.nbits[nn++] = (int8_t)b; }
     }
     sw.n_nontile = nn;
+    uint64_t tiles_per_state = 1ull << (n - k);
+    if (pl->sector) {
+      const int n_up = a->models[0]->n_up, n_dn = a->models[0]->n_dn;
+      int tu = 0, td = 0, nu = 0, nd = 0;
+      for (int b = 0; b < n; ++b) {
+        const bool isup = upm >> b & 1;
+        if (ps.tile >> b & 1) (isup ? tu : td)++;
+        else if (isup) sw.upnt[nu++] = (int8_t)b;
+        else sw.dnnt[nd++] = (int8_t)b;
+      }
+      sw.sector = 1;
+      sw.nu = nu;
+      sw.nd = nd;
+      sw.lo_u = std::max(0, n_up - tu);
+      sw.hi_u = std::min(n_up, nu);
+      sw.lo_d = std::max(0, n_dn - td);
+      sw.hi_d = std::min(n_dn, nd);
+      uint64_t cu = 0, cd = 0;
+      for (int e = sw.lo_u; e <= sw.hi_u; ++e) cu += binom.c[nu][e];
+      for (int e = sw.lo_d; e <= sw.hi_d; ++e) cd += binom.c[nd][e];
+      sw.cnt_d = (uint32_t)cd;
+      sw.live = (uint32_t)(cu * cd);   // <= 2^(n-k)
+      tiles_per_state = sw.live;
+    }
     // ---- register phases ----
     const uint32_t low = (uint32_t)cmask;   // tile-local bits 0..c-1 are the run bits
     const uint32_t tmask = (k >= 32) ? ~0u : ((1u << k) - 1u);
@@ -456,7 +484,7 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
     }
     sw.phase_end = (int)pl->hphases.size();
     sw.op_end = (int)pl->hops.size();
-    bytes += amp * (double)(1ull << n) *
+    bytes += amp * (double)tiles_per_state * (double)(1ull << k) *
              (((f & SW_READ_PSI) ? 1 : 0) + ((f & SW_WRITE_PSI) ? 1 : 0) +
               ((f & SW_READ_LAM) ? 1 : 0) + ((f & SW_WRITE_LAM) ? 1 : 0) +
               ((f & SW_CKPT_WRITE) ? 1 : 0));

@@ -6,8 +6,11 @@
 // time.  A tile holds every amplitude whose index agrees with the tile's
 // base on the non-tile bits; the tile bits always include the c lowest bits
 // (the run bits), so a warp loads and stores whole runs of 2^c contiguous
-// amplitudes (128 B by default).  Fewer run bits leave more tile bits to
-// the operations, and so fewer sweeps.
+// amplitudes (8 by default: 64 B in c64).  Fewer run bits leave more tile
+// bits to the operations, and so fewer sweeps.  Every operation conserves
+// the numbers of up and down electrons, so when the library generates the
+// initial state (in the (N_up, N_dn) sector) a sweep visits only the tiles
+// that meet the sector; the others are zero throughout (see SweepDev).
 //
 // Inside a tile the amplitudes live in registers: in a register phase each
 // thread holds the 2^r amplitudes that differ in r chosen tile bits (its
@@ -58,6 +61,23 @@ __device__ __forceinline__ uint32_t deposit_bits(uint32_t v, const int8_t* pos, 
   uint32_t r = 0;
   for (int i = 0; i < cnt; ++i) r |= ((v >> i) & 1u) << pos[i];
   return r;
+}
+
+static __constant__ BinomTable c_binom = make_binom_table();
+
+// The r-th n-bit pattern among those with lo, lo+1, ... bits set, ordered by
+// the number of set bits and then colexicographically (combinatorial number
+// system: the highest set bit is the largest p with C(p, m) <= rank).  All
+// threads of a CTA unrank the same r, so the table reads are uniform.
+__device__ __forceinline__ uint32_t unrank_bits(uint32_t r, int n, int lo) {
+  int m = lo;
+  while (r >= c_binom.c[n][m]) { r -= c_binom.c[n][m]; ++m; }
+  uint32_t x = 0;
+  for (int p = n - 1; p >= 0 && m > 0; --p) {
+    const uint32_t cnt = c_binom.c[p][m];
+    if (r >= cnt) { x |= 1u << p; r -= cnt; --m; }
+  }
+  return x;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -367,6 +387,8 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
   const size_t op_off = ((size_t)(reinterpret_cast<unsigned char*>(phs + nph) - smem_raw) + 15) & ~(size_t)15;
   uint4* sres = reinterpret_cast<uint4*>(smem_raw + op_off);   // indexed by local op index
   __shared__ int8_t s_nbits[kMaxQubits];
+  __shared__ int8_t s_upnt[kMaxQubits];
+  __shared__ int8_t s_dnnt[kMaxQubits];
   __shared__ int8_t s_tbits[kMaxTileBits];
   __shared__ int s_meas;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -380,6 +402,10 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
 #pragma unroll
     for (int i = 0; i < kMaxQubits; ++i) s_nbits[i] = sw.nbits[i];
 #pragma unroll
+    for (int i = 0; i < kMaxQubits; ++i) s_upnt[i] = sw.upnt[i];
+#pragma unroll
+    for (int i = 0; i < kMaxQubits; ++i) s_dnnt[i] = sw.dnnt[i];
+#pragma unroll
     for (int i = 0; i < kMaxTileBits; ++i) s_tbits[i] = sw.tbits[i];
     s_meas = 0;
   }
@@ -392,7 +418,8 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
   }
   __syncthreads();
 
-  const uint32_t n_tiles = (uint32_t)a.n_tiles;
+  // tiles of this sweep: all 2^(n-k) per state, or the live ones (sector)
+  const uint32_t n_tiles = sw.sector ? (uint32_t)a.batch * sw.live : (uint32_t)a.n_tiles;
   const uint32_t chunk = (n_tiles + gridDim.x - 1) / gridDim.x;
   const uint32_t t0 = blockIdx.x * chunk;
   const uint32_t t1 = min(t0 + chunk, n_tiles);
@@ -402,7 +429,20 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
   T2 l[NE];
 
   for (uint32_t tau = t0; tau < t1; ++tau) {
-    const int b = (int)(tau >> sw.n_nontile);
+    // batch element and non-tile bits of the tile (state-local indices fit
+    // in 32 bits, n <= 32)
+    int b;
+    uint32_t sbase;
+    if (sw.sector) {
+      b = (int)(tau / sw.live);
+      const uint32_t j = tau - (uint32_t)b * sw.live;
+      const uint32_t ju = j / sw.cnt_d, jd = j - ju * sw.cnt_d;
+      sbase = deposit_bits(unrank_bits(ju, sw.nu, sw.lo_u), s_upnt, sw.nu) |
+              deposit_bits(unrank_bits(jd, sw.nd, sw.lo_d), s_dnnt, sw.nd);
+    } else {
+      b = (int)(tau >> sw.n_nontile);
+      sbase = deposit_bits(tau & tl_mask, s_nbits, sw.n_nontile);
+    }
     const int inst = b % a.n_inst;
     if (b != cur_b) {
       if (cur_b >= 0) {
@@ -418,8 +458,6 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
       __syncthreads();
       cur_b = b;
     }
-    // state-local indices fit in 32 bits (n <= 32)
-    const uint32_t sbase = deposit_bits(tau & tl_mask, s_nbits, sw.n_nontile);
     R eacc = 0, nacc = 0, racc = 0;
     int rslot = -1;
     uint32_t base = 0;      // thread's tile-local base index in this phase

@@ -158,8 +158,8 @@ def test_schedules_are_valid(number, which):
     groups = H.hva_groups(bonds, cls, w.n_sites, w.layers, w.classes)
     a = H.Ansatz(m, groups, w.layers)
     seq = _sequence(groups, bonds, w.n_sites, which)
-    # default tiles and runs: 2^12 amplitudes, 128-byte runs (c = 4 / 3)
-    for dtype, k, c in [(H.C64, 12, 4), (H.C128, 12, 3)]:
+    # default tiles and runs: 2^12 amplitudes, runs of 8 amplitudes (c = 3)
+    for dtype, k, c in [(H.C64, 12, 3), (H.C128, 12, 3)]:
         k = min(k, w.n_qubits)
         plan = a.plan_describe(which, dtype)
         _check_schedule(plan, seq, w.n_qubits, k, min(c, k), set(range(w.n_qubits)))
@@ -168,10 +168,43 @@ def test_schedules_are_valid(number, which):
         plan = a.plan_describe(which, H.C64)
         # the planner caps c64 tiles at 13 bits (512 threads x 16 amplitudes)
         k_eff = min(kk, 13, w.n_qubits)
-        _check_schedule(plan, seq, w.n_qubits, k_eff, min(4, k_eff), set(range(w.n_qubits)))
+        _check_schedule(plan, seq, w.n_qubits, k_eff, min(3, k_eff), set(range(w.n_qubits)))
     a.set_tile(H.C64, 0)
     for runs in (2, 3, 5):
         a.set_runs(H.C64, runs)
         plan = a.plan_describe(which, H.C64)
         k_eff = min(12, w.n_qubits)
         _check_schedule(plan, seq, w.n_qubits, k_eff, min(runs, k_eff), set(range(w.n_qubits)))
+
+
+@pytest.mark.parametrize("number", [2, 4, 5])
+def test_sector_plan_bytes(number):
+    """With a generated initial state the sweeps visit only tiles whose
+    non-tile bits can still hold N_up up and N_dn down electrons; the plan's
+    byte count is the count of such tiles times the tile bytes, per sweep."""
+    from math import comb
+    w = H.workloads.workload(number, batch_sets=1)
+    bonds, cls = H.square_lattice(w.nx, w.ny, w.order)
+    t, U, V = w.coefficients(bonds)
+    m = H.Model(w.n_sites, bonds, t, U, V if w.V else None, w.n_up, w.n_dn)
+    a = H.Ansatz(m, H.hva_groups(bonds, cls, w.n_sites, w.layers, w.classes), w.layers)
+    L, n = w.n_sites, w.n_qubits
+    upm, dnm = (1 << L) - 1, ((1 << L) - 1) << L
+
+    def live(tile, N, mask):
+        in_tile = bin(tile & mask).count("1")
+        free = L - in_tile
+        return sum(comb(free, e) for e in range(max(0, N - in_tile), min(N, free) + 1))
+
+    for dtype, amp in ((H.C64, 8), (H.C128, 16)):
+        plan = a.plan_describe(1, dtype)
+        k = bin(plan[0][0]).count("1")
+        expect = 0
+        for tile, flags, _ in plan:
+            f = flags & 0xFFFF
+            nvec = sum(1 for bit in (2, 4, 16, 32, 64) if f & bit)
+            expect += nvec * live(tile, w.n_up, upm) * live(tile, w.n_dn, dnm) * (1 << k) * amp
+        assert a.plan_stats(1, dtype, fused=True)[1] == expect
+        dense = a.plan_stats(1, dtype, fused=False)[1]
+        assert dense == sum(sum(1 for bit in (2, 4, 16, 32, 64) if (fl & 0xFFFF) & bit)
+                            for _, fl, _ in a.plan_describe(1, dtype, flags=0)) * (1 << n) * amp
