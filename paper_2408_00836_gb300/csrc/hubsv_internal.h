@@ -115,18 +115,19 @@ struct SweepDev {
   // electrons, so when the initial state is generated in the (N_up, N_dn)
   // sector, a tile whose non-tile bits hold too many or too few electrons
   // of either spin for the sector is zero throughout the call.  With sector
-  // = 1 the sweep visits only the other tiles ("live" tiles): their
-  // non-tile up bits (positions upnt) carry lo_u..hi_u electrons, their
-  // down bits (dnnt) lo_d..hi_d; live tile j of a state has up pattern
-  // j / cnt_d and down pattern j % cnt_d, each ranked by electron count and
-  // then in colex order.
+  // = 1 the sweep visits only the other tiles ("live" tiles).  The non-tile
+  // bits are split by spin into part a (the spin holding the lowest
+  // non-tile bit) and part b; live tile j of a state has part-a pattern
+  // j % cnt_a and part-b pattern j / cnt_a, each ranked by electron count
+  // (from lo_a / lo_b up) and then in colex order, so that consecutive live
+  // tiles differ first in low index bits and lie close together in HBM.
   int32_t sector;
-  int32_t nu, nd;                 // non-tile up / down bits
-  int32_t lo_u, hi_u, lo_d, hi_d;
-  uint32_t cnt_d;                 // live down patterns
+  int32_t na, nb;                 // non-tile bits of part a / b
+  int32_t lo_a, lo_b;             // fewest electrons a live pattern holds
+  uint32_t cnt_a;                 // live part-a patterns
   uint32_t live;                  // live tiles per state
-  int8_t upnt[kMaxQubits];        // non-tile up-mode bit positions, ascending
-  int8_t dnnt[kMaxQubits];        // non-tile down-mode bit positions, ascending
+  int8_t pa[kMaxQubits];          // part-a bit positions, ascending
+  int8_t pb[kMaxQubits];          // part-b bit positions, ascending
 };
 
 // Binomial coefficients C(n, k), n, k <= 32 (C(32, 16) < 2^32).

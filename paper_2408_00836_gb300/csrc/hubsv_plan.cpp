@@ -264,18 +264,46 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
       windows.push_back(t);
     }
   }
+  // An initial state generated here lies in the (N_up, N_dn) sector and
+  // every operation keeps it there: sweeps then visit only the tiles that
+  // meet the sector (see SweepDev), and a candidate tile is worth the
+  // operations it runs per live fraction of the vector it moves.
+  const bool sector = (which == 3 || (flags & HUB_FLAG_PREP_FUSED) != 0) && which != 2;
+  const BinomTable binom = make_binom_table();
+  auto pad_tile = [&](uint64_t t) {
+    for (int b = 0; b < n && popc64(t) < k; ++b) t |= 1ull << b;   // pad with low bits
+    return t;
+  };
+  auto live_frac = [&](uint64_t t) {
+    double f = 1.0;
+    for (int sp = 0; sp < 2; ++sp) {
+      const uint64_t m = sp == 0 ? upm : dnm;
+      const int N = sp == 0 ? a->models[0]->n_up : a->models[0]->n_dn;
+      const int in = popc64(t & m), fr = popc64(m) - in;
+      double c = 0.0;
+      for (int e = std::max(0, N - in); e <= std::min(N, fr); ++e) c += binom.c[fr][e];
+      f *= c / (double)(1ull << fr);
+    }
+    return f;
+  };
+  auto worth = [&](const Scan& s) {
+    if (!sector) return (double)s.exec.size();
+    return (double)s.exec.size() / (live_frac(pad_tile(s.tile)) + 0.05);
+  };
   struct PS { uint64_t tile; std::vector<int> ops; };
   std::vector<PS> sweeps;
   while (!remaining.empty()) {
     Scan best = scan(seq, remaining, cmask, all, k, need_modes);
-    auto consider = [&](Scan&& s) { if (s.exec.size() > best.exec.size()) best = std::move(s); };
+    double best_w = worth(best);
+    auto consider = [&](Scan&& s) {
+      const double w = worth(s);
+      if (w > best_w) { best = std::move(s); best_w = w; }
+    };
     consider(scan(seq, remaining, cmask, cmask | upm, k, need_modes));
     consider(scan(seq, remaining, cmask, cmask | dnm, k, need_modes));
     for (uint64_t t : windows) consider(scan(seq, remaining, t, t, k, need_modes));
     if (best.exec.empty()) return fail(HUB_EUNSUPPORTED, "planner made no progress");
-    uint64_t tile = best.tile;
-    for (int b = 0; b < n && popc64(tile) < k; ++b) tile |= 1ull << b;   // pad with low bits
-    sweeps.push_back({tile, best.exec});
+    sweeps.push_back({pad_tile(best.tile), best.exec});
     remaining.swap(best.rest);
   }
   if (sweeps.empty()) sweeps.push_back({(1ull << k) - 1ull, {}});   // initial state only
@@ -283,10 +311,7 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
   Plan* pl = new Plan();
   pl->k = k;
   const bool prep = which == 3 || (flags & HUB_FLAG_PREP_FUSED) != 0;
-  // an initial state generated here lies in the (N_up, N_dn) sector, and
-  // every operation keeps it there: visit only the tiles that meet it
-  pl->sector = prep && which != 2;
-  const BinomTable binom = make_binom_table();
+  pl->sector = sector;
   const bool keep = which == 3 || (flags & HUB_FLAG_KEEP_STATE) != 0;
   bool lam_live = false;
   const double amp = dtype == HUB_C64 ? 8.0 : 16.0;
@@ -338,23 +363,28 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
     if (pl->sector) {
       const int n_up = a->models[0]->n_up, n_dn = a->models[0]->n_dn;
       int tu = 0, td = 0, nu = 0, nd = 0;
+      int8_t upos[kMaxQubits], dpos[kMaxQubits];
       for (int b = 0; b < n; ++b) {
         const bool isup = upm >> b & 1;
         if (ps.tile >> b & 1) (isup ? tu : td)++;
-        else if (isup) sw.upnt[nu++] = (int8_t)b;
-        else sw.dnnt[nd++] = (int8_t)b;
+        else if (isup) upos[nu++] = (int8_t)b;
+        else dpos[nd++] = (int8_t)b;
       }
-      sw.sector = 1;
-      sw.nu = nu;
-      sw.nd = nd;
-      sw.lo_u = std::max(0, n_up - tu);
-      sw.hi_u = std::min(n_up, nu);
-      sw.lo_d = std::max(0, n_dn - td);
-      sw.hi_d = std::min(n_dn, nd);
+      const int lo_u = std::max(0, n_up - tu), hi_u = std::min(n_up, nu);
+      const int lo_d = std::max(0, n_dn - td), hi_d = std::min(n_dn, nd);
       uint64_t cu = 0, cd = 0;
-      for (int e = sw.lo_u; e <= sw.hi_u; ++e) cu += binom.c[nu][e];
-      for (int e = sw.lo_d; e <= sw.hi_d; ++e) cd += binom.c[nd][e];
-      sw.cnt_d = (uint32_t)cd;
+      for (int e = lo_u; e <= hi_u; ++e) cu += binom.c[nu][e];
+      for (int e = lo_d; e <= hi_d; ++e) cd += binom.c[nd][e];
+      // part a: the spin that holds the lowest non-tile bit
+      const bool up_a = nd == 0 || (nu > 0 && upos[0] < dpos[0]);
+      sw.sector = 1;
+      sw.na = up_a ? nu : nd;
+      sw.nb = up_a ? nd : nu;
+      sw.lo_a = up_a ? lo_u : lo_d;
+      sw.lo_b = up_a ? lo_d : lo_u;
+      sw.cnt_a = (uint32_t)(up_a ? cu : cd);
+      for (int i = 0; i < sw.na; ++i) sw.pa[i] = up_a ? upos[i] : dpos[i];
+      for (int i = 0; i < sw.nb; ++i) sw.pb[i] = up_a ? dpos[i] : upos[i];
       sw.live = (uint32_t)(cu * cd);   // <= 2^(n-k)
       tiles_per_state = sw.live;
     }
