@@ -38,6 +38,9 @@ WORKLOAD_TEXT = {
        "Slater start, energy + adjoint gradient",
     6: "grid3x4u: 3x4 open Hubbard, 24 qubits, N=6+6, t=1, U=8, 4 HVA layers x (U,h1,v1,h2,v2), "
        "Slater start, energy + adjoint gradient (profiling proxy of grid4x4)",
+    2: "grid2x4 batched: 2x4 open Hubbard (snake order), 16 qubits, N=4+4, t=1, U/t in {1,2,4,8}, "
+       "4 HVA layers x (U,h1,v1,h2,v2), perturbed-orbital Slater start, 1024 seeded theta sets x 4 U "
+       "values = 4096 states per launch, energy + adjoint gradient",
     3: "grid3x4: 3x4 open extended Hubbard, 24 qubits, N=6+6, t=1+0.1N(0,1), U=4(1+0.1N(0,1)), V=0.5, "
        "6 HVA layers x (U,V,h1,v1,h2,v2), Slater start, energy + adjoint gradient",
 }
@@ -197,7 +200,7 @@ def oracle_sample(number: int, down_configs: int = 512):
 # ---------------------------------------------------------------------------
 
 def build_problem(number, H):
-    w = H.workloads.workload(number, batch_sets=1 if number == 2 else None)
+    w = H.workloads.workload(number)
     bonds, cls = H.square_lattice(w.nx, w.ny, w.order)
     models = []
     for r in range(w.n_instances):
@@ -320,7 +323,7 @@ def run_gpu(args, rank, world, dist):
            "dtype": args.dtype, "data": "synthetic (seeded inputs of the named workload)",
            "config": {"workload": WORKLOAD_TEXT.get(args.workload, w.name), "qubits": w.n_qubits,
                       "params": a.P, "batch_per_gpu": batch, "parallelism": f"replicas x{world}",
-                      "l2": "inputs larger than L2 (one vector = %.1f GB)" % (a.amp_bytes(dtype) / 1e9)},
+                      "l2": "inputs larger than L2 (psi = %.1f GB for the batch)" % (batch * a.amp_bytes(dtype) / 1e9)},
            "hbm_tbs": round(hbm_tbs, 3),
            "plan": {"sweeps": n_sweeps, "bytes_per_eval": bytes_per_state},
            "energy": E_val, "roofline": roof, "e2e": e2e, "gpu_launches": launches,
@@ -373,7 +376,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", type=int, default=5, choices=[3, 4, 5, 6])
+    ap.add_argument("--workload", type=int, default=5, choices=[2, 3, 4, 5, 6])
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--no-c128", dest="c128", action="store_false")
     ap.add_argument("--c128-steps", type=int, default=1)

@@ -158,3 +158,45 @@ def run_vqe(ans: Ansatz, theta0, dtype: int = C64, max_iter: int = 200, ckpt: bo
     x, f, g, it, reason, hist = lbfgs(fun, theta0, max_iter=max_iter)
     sec = time.perf_counter() - t0
     return VQEResult(x, f, float(np.max(np.abs(g))), it, fn.evals, reason, hist, sec)
+
+
+def _main():
+    """Run the energy-based VQE of a seeded workload in complex64 and then in
+    complex128 from the same start, and print one JSON line with both
+    results (final energies, iterations, evaluations, wall time)."""
+    import argparse
+    import json
+
+    import torch
+
+    from . import PREP_SLATER, Model, hva_groups, square_lattice
+    from . import workloads as W
+
+    ap = argparse.ArgumentParser(description=_main.__doc__)
+    ap.add_argument("--workload", type=int, default=4)
+    ap.add_argument("--iters", type=int, default=200)
+    ap.add_argument("--dtypes", default="c64,c128")
+    args = ap.parse_args()
+    torch.cuda.init()
+    w = W.workload(args.workload, batch_sets=1)
+    bonds, cls = square_lattice(w.nx, w.ny, w.order)
+    t, U, V = w.coefficients(bonds)
+    m = Model(w.n_sites, bonds, t, U, V if w.V else None, w.n_up, w.n_dn)
+    ans = Ansatz(m, hva_groups(bonds, cls, w.n_sites, w.layers, w.classes), w.layers)
+    theta0 = w.theta()[0]
+    out = {"workload": w.name, "qubits": w.n_qubits, "params": ans.P, "max_iter": args.iters}
+    for name in args.dtypes.split(","):
+        dt = C64 if name == "c64" else C128
+        ans.state_prepare(PREP_SLATER, w.orbital_perturbation(), None, None, dt, 1)
+        r = run_vqe(ans, theta0, dtype=dt, max_iter=args.iters)
+        out[name] = {"energy": r.energy, "grad_max": r.grad_norm, "iterations": r.iterations,
+                     "evaluations": r.evaluations, "reason": r.reason, "seconds": round(r.seconds, 2),
+                     "evals_per_s": round(r.evaluations / r.seconds, 3), "E_first": r.history[0]}
+        torch.cuda.empty_cache()
+    if "c64" in out and "c128" in out:
+        out["final_energy_diff"] = abs(out["c64"]["energy"] - out["c128"]["energy"])
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    _main()
