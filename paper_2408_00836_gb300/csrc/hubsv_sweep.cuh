@@ -365,6 +365,21 @@ __device__ void resolve_ops(const SweepDev& sw, const KernelArgs& a, uint4* sres
   }
 }
 
+// Global load of one amplitude of a run, with the L2 told to fetch 64 bytes
+// for a miss (the default fetched the whole 128-byte line, doubling DRAM
+// reads where a run is 64 bytes long and the rest of the line belongs to a
+// tile processed at another time).
+__device__ __forceinline__ float2 ldg_run(const float2* p) {
+  float2 r;
+  asm volatile("ld.global.L2::64B.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "l"(p) : "memory");
+  return r;
+}
+__device__ __forceinline__ double2 ldg_run(const double2* p) {
+  double2 r;
+  asm volatile("ld.global.L2::64B.v2.f64 {%0, %1}, [%2];" : "=d"(r.x), "=d"(r.y) : "l"(p) : "memory");
+  return r;
+}
+
 // ---------------------------------------------------------------------------
 // the sweep kernel
 // ---------------------------------------------------------------------------
@@ -505,10 +520,10 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
           if (sw.flags & SW_PREP) {
             v[e] = mk<T2, R>(prep_amp<R>(a.prep, sdt, sbase | off, inst), (R)0);
           } else {
-            v[e] = src[gbase + off];
+            v[e] = ldg_run(src + gbase + off);
           }
           if (NV == 2) {
-            if (sw.flags & SW_READ_LAM) l[e] = reinterpret_cast<const T2*>(a.lam)[gbase + off];
+            if (sw.flags & SW_READ_LAM) l[e] = ldg_run(reinterpret_cast<const T2*>(a.lam) + gbase + off);
             else l[e] = mk<T2, R>((R)0, (R)0);
           }
         }
