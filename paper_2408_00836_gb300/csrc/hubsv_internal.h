@@ -124,6 +124,7 @@ struct SweepDev {
   int32_t sector;
   int32_t na, nb;                 // non-tile bits of part a / b
   int32_t lo_a, lo_b;             // fewest electrons a live pattern holds
+  int32_t hi_a, hi_b;             // most electrons a live pattern holds
   uint32_t cnt_a;                 // live part-a patterns
   uint32_t live;                  // live tiles per state
   int8_t pa[kMaxQubits];          // part-a bit positions, ascending

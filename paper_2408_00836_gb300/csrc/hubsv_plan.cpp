@@ -382,6 +382,8 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
       sw.nb = up_a ? nd : nu;
       sw.lo_a = up_a ? lo_u : lo_d;
       sw.lo_b = up_a ? lo_d : lo_u;
+      sw.hi_a = up_a ? hi_u : hi_d;
+      sw.hi_b = up_a ? hi_d : hi_u;
       sw.cnt_a = (uint32_t)(up_a ? cu : cd);
       for (int i = 0; i < sw.na; ++i) sw.pa[i] = up_a ? upos[i] : dpos[i];
       for (int i = 0; i < sw.nb; ++i) sw.pb[i] = up_a ? dpos[i] : upos[i];

@@ -80,6 +80,30 @@ __device__ __forceinline__ uint32_t unrank_bits(uint32_t r, int n, int lo) {
   return x;
 }
 
+// Advance x to the next pattern in that order (n bits, at most hi set):
+// the colex successor with the same number of set bits (Gosper's rule), else
+// the smallest pattern with one more bit set.  Returns false when x was the
+// last pattern.
+__device__ __forceinline__ bool next_pattern(uint32_t& x, int n, int hi) {
+  const int m = __popc(x);
+  if (m > 0) {
+    const uint32_t c = x & (0u - x);
+    const uint32_t r = x + c;
+    const uint32_t nx = r | (((r ^ x) >> 2) >> (__ffs(c) - 1));
+    if (nx < (1u << n)) { x = nx; return true; }
+  }
+  if (m + 1 > hi) return false;
+  x = (1u << (m + 1)) - 1u;
+  return true;
+}
+
+// Bits of x moved to positions pos[i] (one step per set bit).
+__device__ __forceinline__ uint32_t deposit_set(uint32_t x, const int8_t* pos) {
+  uint32_t r = 0;
+  for (; x; x &= x - 1u) r |= 1u << pos[__ffs(x) - 1];
+  return r;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -445,6 +469,19 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
   int cur_b = -1;
   T2 v[NE];
   T2 l[NE];
+  // Sector tiles: thread 0 unranks the CTA's first live tile and then steps
+  // the two patterns (part a fastest), one tile ahead, into a double buffer
+  // in shared memory (so that they hold no registers during the operations);
+  // the barrier at the top of each tile publishes them.
+  __shared__ uint32_t s_tile[2][3];   // pattern a, pattern b, batch element
+  if (sw.sector && t0 < t1 && tid == 0) {
+    const uint32_t b0 = t0 / sw.live;
+    const uint32_t j = t0 - b0 * sw.live;
+    const uint32_t jb = j / sw.cnt_a, ja = j - jb * sw.cnt_a;
+    s_tile[0][0] = unrank_bits(ja, sw.na, sw.lo_a);
+    s_tile[0][1] = unrank_bits(jb, sw.nb, sw.lo_b);
+    s_tile[0][2] = b0;
+  }
 
   for (uint32_t tau = t0; tau < t1; ++tau) {
     // batch element and non-tile bits of the tile (state-local indices fit
@@ -452,11 +489,25 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
     int b;
     uint32_t sbase;
     if (sw.sector) {
-      b = (int)(tau / sw.live);
-      const uint32_t j = tau - (uint32_t)b * sw.live;
-      const uint32_t jb = j / sw.cnt_a, ja = j - jb * sw.cnt_a;
-      sbase = deposit_bits(unrank_bits(ja, sw.na, sw.lo_a), s_pa, sw.na) |
-              deposit_bits(unrank_bits(jb, sw.nb, sw.lo_b), s_pb, sw.nb);
+      __syncthreads();
+      const uint32_t* cur = s_tile[(tau - t0) & 1u];
+      uint32_t pat_a = cur[0], pat_b = cur[1];
+      b = (int)cur[2];
+      sbase = deposit_set(pat_a, s_pa) | deposit_set(pat_b, s_pb);
+      if (tid == 0 && tau + 1 < t1) {
+        uint32_t bn = (uint32_t)b;
+        if (!next_pattern(pat_a, sw.na, sw.hi_a)) {
+          pat_a = (1u << sw.lo_a) - 1u;
+          if (!next_pattern(pat_b, sw.nb, sw.hi_b)) {
+            pat_b = (1u << sw.lo_b) - 1u;
+            ++bn;
+          }
+        }
+        uint32_t* nxt = s_tile[(tau + 1 - t0) & 1u];
+        nxt[0] = pat_a;
+        nxt[1] = pat_b;
+        nxt[2] = bn;
+      }
     } else {
       b = (int)(tau >> sw.n_nontile);
       sbase = deposit_bits(tau & tl_mask, s_nbits, sw.n_nontile);

@@ -9,7 +9,6 @@ const void* sweep_ptr_d1(int r) {
     case 1: return (const void*)sweep_kernel<double, 1, 1>;
     case 2: return (const void*)sweep_kernel<double, 1, 2>;
     case 3: return (const void*)sweep_kernel<double, 1, 3>;
-    case 4: return (const void*)sweep_kernel<double, 1, 4>;
     default: return nullptr;
   }
 }
