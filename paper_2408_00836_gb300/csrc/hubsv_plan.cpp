@@ -290,21 +290,50 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
     if (!sector) return (double)s.exec.size();
     return (double)s.exec.size() / (live_frac(pad_tile(s.tile)) + 0.05);
   };
+  auto candidates = [&](const std::vector<int>& rem) {
+    std::vector<Scan> cs;
+    cs.push_back(scan(seq, rem, cmask, all, k, need_modes));
+    cs.push_back(scan(seq, rem, cmask, cmask | upm, k, need_modes));
+    cs.push_back(scan(seq, rem, cmask, cmask | dnm, k, need_modes));
+    for (uint64_t t : windows) cs.push_back(scan(seq, rem, t, t, k, need_modes));
+    return cs;
+  };
+  auto lf_of = [&](const Scan& s) { return sector ? live_frac(pad_tile(s.tile)) : 1.0; };
+  // Sector mode looks one sweep ahead: of the best few candidates by worth,
+  // take the one whose pair (it, then the best next sweep) runs the most
+  // operations per live fraction moved.
+  constexpr int kLookahead = 4;
   struct PS { uint64_t tile; std::vector<int> ops; };
   std::vector<PS> sweeps;
   while (!remaining.empty()) {
-    Scan best = scan(seq, remaining, cmask, all, k, need_modes);
-    double best_w = worth(best);
-    auto consider = [&](Scan&& s) {
-      const double w = worth(s);
-      if (w > best_w) { best = std::move(s); best_w = w; }
-    };
-    consider(scan(seq, remaining, cmask, cmask | upm, k, need_modes));
-    consider(scan(seq, remaining, cmask, cmask | dnm, k, need_modes));
-    for (uint64_t t : windows) consider(scan(seq, remaining, t, t, k, need_modes));
-    if (best.exec.empty()) return fail(HUB_EUNSUPPORTED, "planner made no progress");
-    sweeps.push_back({pad_tile(best.tile), best.exec});
-    remaining.swap(best.rest);
+    std::vector<Scan> cs = candidates(remaining);
+    std::vector<int> order(cs.size());
+    for (size_t i = 0; i < cs.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return worth(cs[x]) > worth(cs[y]); });
+    if (cs[order[0]].exec.empty()) return fail(HUB_EUNSUPPORTED, "planner made no progress");
+    int pick = order[0];
+    if (sector) {
+      double best_v = -1.0;
+      for (int i = 0; i < kLookahead && i < (int)order.size(); ++i) {
+        const Scan& s1 = cs[order[i]];
+        if (s1.exec.empty()) break;
+        double n2 = 0.0, l2 = 0.0;
+        if (!s1.rest.empty()) {
+          std::vector<Scan> c2 = candidates(s1.rest);
+          const Scan* b2 = nullptr;
+          for (const Scan& t : c2)
+            if (!b2 || worth(t) > worth(*b2)) b2 = &t;
+          n2 = (double)b2->exec.size();
+          l2 = lf_of(*b2);
+        }
+        const double v = ((double)s1.exec.size() + n2) / (lf_of(s1) + l2 + 0.1);
+        if (v > best_v) { best_v = v; pick = order[i]; }
+      }
+    }
+    sweeps.push_back({pad_tile(cs[pick].tile), cs[pick].exec});
+    std::vector<int> rest = cs[pick].rest;
+    remaining.swap(rest);
   }
   if (sweeps.empty()) sweeps.push_back({(1ull << k) - 1ull, {}});   // initial state only
 
