@@ -299,41 +299,63 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
     return cs;
   };
   auto lf_of = [&](const Scan& s) { return sector ? live_frac(pad_tile(s.tile)) : 1.0; };
-  // Sector mode looks one sweep ahead: of the best few candidates by worth,
-  // take the one whose pair (it, then the best next sweep) runs the most
-  // operations per live fraction moved.
-  constexpr int kLookahead = 4;
+  // Sweep selection.  Sector mode looks one sweep ahead: of the best `width`
+  // candidates by worth, take the one whose pair (it, then the best next
+  // sweep) runs the most operations per live fraction moved.  The outcome
+  // of such greedy rules varies with the width in no regular way, so
+  // several widths are planned (planning is cheap next to one sweep) and the
+  // plan that moves the fewest vector bytes is kept (cost: live fraction x
+  // vectors a sweep reads and writes: 2, 3 with lam being built, 4 with the
+  // gradient).
   struct PS { uint64_t tile; std::vector<int> ops; };
-  std::vector<PS> sweeps;
-  while (!remaining.empty()) {
-    std::vector<Scan> cs = candidates(remaining);
-    std::vector<int> order(cs.size());
-    for (size_t i = 0; i < cs.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int x, int y) { return worth(cs[x]) > worth(cs[y]); });
-    if (cs[order[0]].exec.empty()) return fail(HUB_EUNSUPPORTED, "planner made no progress");
-    int pick = order[0];
-    if (sector) {
-      double best_v = -1.0;
-      for (int i = 0; i < kLookahead && i < (int)order.size(); ++i) {
-        const Scan& s1 = cs[order[i]];
-        if (s1.exec.empty()) break;
-        double n2 = 0.0, l2 = 0.0;
-        if (!s1.rest.empty()) {
-          std::vector<Scan> c2 = candidates(s1.rest);
-          const Scan* b2 = nullptr;
-          for (const Scan& t : c2)
-            if (!b2 || worth(t) > worth(*b2)) b2 = &t;
-          n2 = (double)b2->exec.size();
-          l2 = lf_of(*b2);
+  auto select_sweeps = [&](int width, std::vector<PS>& out, double& cost) -> bool {
+    std::vector<int> rem = remaining;
+    cost = 0.0;
+    while (!rem.empty()) {
+      std::vector<Scan> cs = candidates(rem);
+      std::vector<int> order(cs.size());
+      for (size_t i = 0; i < cs.size(); ++i) order[i] = (int)i;
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int x, int y) { return worth(cs[x]) > worth(cs[y]); });
+      if (cs[order[0]].exec.empty()) return false;
+      int pick = order[0];
+      if (sector && width > 1) {
+        double best_v = -1.0;
+        for (int i = 0; i < width && i < (int)order.size(); ++i) {
+          const Scan& s1 = cs[order[i]];
+          if (s1.exec.empty()) break;
+          double n2 = 0.0, l2 = 0.0;
+          if (!s1.rest.empty()) {
+            std::vector<Scan> c2 = candidates(s1.rest);
+            const Scan* b2 = nullptr;
+            for (const Scan& t : c2)
+              if (!b2 || worth(t) > worth(*b2)) b2 = &t;
+            n2 = (double)b2->exec.size();
+            l2 = lf_of(*b2);
+          }
+          const double v = ((double)s1.exec.size() + n2) / (lf_of(s1) + l2 + 0.1);
+          if (v > best_v) { best_v = v; pick = order[i]; }
         }
-        const double v = ((double)s1.exec.size() + n2) / (lf_of(s1) + l2 + 0.1);
-        if (v > best_v) { best_v = v; pick = order[i]; }
       }
+      int nvec = 2;
+      for (int idx : cs[pick].exec) nvec = std::max(nvec, seq[idx].cls == 3 ? 4 : (seq[idx].cls == 2 ? 3 : 2));
+      cost += lf_of(cs[pick]) * nvec;
+      out.push_back({pad_tile(cs[pick].tile), cs[pick].exec});
+      std::vector<int> rest = cs[pick].rest;
+      rem.swap(rest);
     }
-    sweeps.push_back({pad_tile(cs[pick].tile), cs[pick].exec});
-    std::vector<int> rest = cs[pick].rest;
-    remaining.swap(rest);
+    return true;
+  };
+  std::vector<PS> sweeps;
+  {
+    double best_cost = 0.0;
+    for (int width : {1, 2, 3, 4, 6}) {
+      if (!sector && width > 1) break;
+      std::vector<PS> sw;
+      double cost = 0.0;
+      if (!select_sweeps(width, sw, cost)) return fail(HUB_EUNSUPPORTED, "planner made no progress");
+      if (sweeps.empty() || cost < best_cost) { sweeps.swap(sw); best_cost = cost; }
+    }
   }
   if (sweeps.empty()) sweeps.push_back({(1ull << k) - 1ull, {}});   // initial state only
 
