@@ -253,8 +253,8 @@ cudaError_t launch_zero(double* p, int64_t n, cudaStream_t st);
 cudaError_t launch_finalize(const double* acc, int n_slots, int P, int slot_E,
                             double* E, double* grad, int64_t batch, cudaStream_t st);
 int sweep_max_smem_optin();
-cudaError_t sweep_set_smem(int dtype, int nv, int r, size_t smem);
-int sweep_regs(int dtype, int nv, int r);
+cudaError_t sweep_set_smem(int dtype, int nv, int r, int threads, size_t smem);
+int sweep_regs(int dtype, int nv, int r, int threads);
 int device_sm_count();
 // Register bits the kernels are compiled for: r in [1, max_r(dtype, nv)].
 inline int max_reg_bits(int dtype, int nv) {

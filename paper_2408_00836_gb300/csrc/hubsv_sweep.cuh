@@ -408,8 +408,12 @@ __device__ __forceinline__ double2 ldg_run(const double2* p) {
 // the sweep kernel
 // ---------------------------------------------------------------------------
 
-template <typename R, int NV, int RB>
-__global__ void __launch_bounds__(512, 1)
+// MINB = 1: up to 512 threads, one CTA per SM guaranteed (128 registers a
+// thread); MINB = 4: at most 256 threads and four CTAs per SM (64
+// registers), used for psi-only c64 sweeps of 256-thread tiles, where the
+// extra CTAs hide the tile loads.
+template <typename R, int NV, int RB, int MINB = 1>
+__global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB)
 sweep_kernel(const SweepDev sw, const KernelArgs a) {
   using T2 = typename CT<R>::T2;
   constexpr int DT = CT<R>::DT;

@@ -14,4 +14,12 @@ const void* sweep_ptr_f1(int r) {
   }
 }
 
+// Four CTAs of at most 256 threads per SM.
+const void* sweep_ptr_f1_narrow(int r) {
+  switch (r) {
+    case 4: return (const void*)sweep_kernel<float, 1, 4, 4>;
+    default: return nullptr;
+  }
+}
+
 }  // namespace hubsv

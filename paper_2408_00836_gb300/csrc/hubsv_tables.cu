@@ -99,12 +99,16 @@ const void* sweep_ptr_f1(int r);
 const void* sweep_ptr_f2(int r);
 const void* sweep_ptr_d1(int r);
 const void* sweep_ptr_d2(int r);
+const void* sweep_ptr_f1_narrow(int r);
 
 namespace {
 int g_sm_count = 0;
 
-const void* kernel_for(int dtype, int nv, int r) {
+const void* kernel_for(int dtype, int nv, int r, int threads) {
   if (r < 1 || r > max_reg_bits(dtype, nv)) return nullptr;
+  if (dtype == 0 && nv == 1 && threads <= 256) {
+    if (const void* f = sweep_ptr_f1_narrow(r)) return f;
+  }
   if (dtype == 0) return nv == 2 ? sweep_ptr_f2(r) : sweep_ptr_f1(r);
   return nv == 2 ? sweep_ptr_d2(r) : sweep_ptr_d1(r);
 }
@@ -126,14 +130,14 @@ int sweep_max_smem_optin() {
   return v;
 }
 
-cudaError_t sweep_set_smem(int dtype, int nv, int r, size_t smem) {
-  const void* f = kernel_for(dtype, nv, r);
+cudaError_t sweep_set_smem(int dtype, int nv, int r, int threads, size_t smem) {
+  const void* f = kernel_for(dtype, nv, r, threads);
   if (!f) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-int sweep_regs(int dtype, int nv, int r) {
-  const void* f = kernel_for(dtype, nv, r);
+int sweep_regs(int dtype, int nv, int r, int threads) {
+  const void* f = kernel_for(dtype, nv, r, threads);
   cudaFuncAttributes at;
   if (!f || cudaFuncGetAttributes(&at, f) != cudaSuccess) return 0;
   return at.numRegs;
@@ -142,9 +146,9 @@ int sweep_regs(int dtype, int nv, int r) {
 cudaError_t launch_sweep(int dtype, const SweepDev& sw, const KernelArgs& a, int grid, size_t smem,
                          cudaStream_t st) {
   const int nv = (sw.flags & SW_HAS_LAM) ? 2 : 1;
-  const void* f = kernel_for(dtype, nv, sw.r);
-  if (!f) return cudaErrorInvalidValue;
   const int threads = 32 << sw.w;
+  const void* f = kernel_for(dtype, nv, sw.r, threads);
+  if (!f) return cudaErrorInvalidValue;
   SweepDev swc = sw;
   KernelArgs ac = a;
   void* args[] = {(void*)&swc, (void*)&ac};
