@@ -211,6 +211,23 @@ def build_problem(number, H):
     return w, a
 
 
+def job_ms(ms_local, dist, device):
+    """Whole-job time of a timed region: the slowest rank's (replicas run in
+    parallel, so the job ends when the last one does)."""
+    if dist is None:
+        return ms_local
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, batch, steps, ms):
+    """Evaluations per second of the whole job: every rank evaluates
+    batch states per step."""
+    return world * batch * steps / (ms / 1e3)
+
+
 def run_gpu(args, rank, world, dist):
     import numpy as np
     import torch
@@ -267,12 +284,9 @@ def run_gpu(args, rank, world, dist):
     recs = H.profile_read(a)
     H.profile(a, False)
     ck = clocks.stop() if clocks else None
-    if dist:
-        tt = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = job_ms(ms_total, dist, dev)
     ms_step = ms_total / args.steps
-    value = world * batch * args.steps / (ms_total / 1e3)
+    value = job_value(world, batch, args.steps, ms_total)
     E_val = float(E[0].item())
 
     # roofline of the dominant kernel
@@ -311,8 +325,8 @@ def run_gpu(args, rank, world, dist):
         stream.synchronize()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    e2e = {"value": round(world * batch * args.steps / (e2e_ms / 1e3), 4), "unit": "evals/s",
+    e2e_ms = job_ms(e0.elapsed_time(e1), dist, dev)
+    e2e = {"value": round(job_value(world, batch, args.steps, e2e_ms), 4), "unit": "evals/s",
            "h2d_bytes_per_step": int(theta_h.numel() * 8),
            "d2h_bytes_per_step": int((E_h.numel() + g_h.numel()) * 8)}
     launches = args.steps * (n_sweeps + 3)
