@@ -233,14 +233,14 @@ HUB_API hub_status ans_profile(ans_t ans, int32_t enable);
 HUB_API hub_status ans_profile_read(ans_t ans, double* out, int32_t cap,
                                     int32_t* n);
 
-/* Tile size override (log2 amplitudes per tile, 6..14; 0 = automatic: 12,
- * capped at 13 for c64 and 12 for c128 by the register budget).  Used by the
- * autotuner.                                                                */
+/* Tile size override (log2 amplitudes per tile, 6..14; 0 = automatic: 12 for
+ * c64, 10 for c128; capped at 13 for c64 and 12 for c128 by the register
+ * budget).  Used by the autotuner.                                          */
 HUB_API hub_status ans_set_tile(ans_t ans, int32_t dtype, int32_t log2_tile);
 
 /* Run length override (log2 of the contiguous amplitudes that a warp moves
  * between HBM and registers as one piece; the lowest log2_run index bits are
- * in every tile).  0 = automatic (3: 64-byte runs in c64, 128-byte in c128); else
+ * in every tile).  0 = automatic (c64: 3, 64-byte runs; c128: 1, 32-byte); else
  * 1..5.  Shorter runs leave more tile bits free for the operations (fewer
  * sweeps) at the cost of less contiguous HBM traffic.                       */
 HUB_API hub_status ans_set_runs(ans_t ans, int32_t dtype, int32_t log2_run);

@@ -115,10 +115,11 @@ namespace hubsv {
 // Default tile and run bits (log2 of the amplitudes per tile, and of the
 // contiguous amplitudes a warp reads or writes as one piece), chosen by
 // timing the 32-qubit energy + gradient on GB300: c64 tiles of 2^12 (two
-// CTAs of 256 threads per SM) with 64-byte runs; c128 tiles of 2^12 (one
-// CTA of 512 threads) with 128-byte runs.
-inline int default_tile_bits(int dtype) { return dtype == HUB_C64 ? 12 : 12; }
-inline int default_run_bits(int dtype) { return dtype == HUB_C64 ? 3 : 3; }
+// CTAs of 256 threads per SM) with 64-byte runs; c128 tiles of 2^10 (CTAs
+// of 128 threads) with 32-byte runs.  c128 is bound by FP64 arithmetic, so
+// it gains most from the plan that visits the fewest live amplitudes.
+inline int default_tile_bits(int dtype) { return dtype == HUB_C64 ? 12 : 10; }
+inline int default_run_bits(int dtype) { return dtype == HUB_C64 ? 3 : 1; }
 uint64_t diag_support(const hub_ansatz* a, int di);
 hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*& out);
 }  // namespace hubsv

@@ -158,8 +158,9 @@ def test_schedules_are_valid(number, which):
     groups = H.hva_groups(bonds, cls, w.n_sites, w.layers, w.classes)
     a = H.Ansatz(m, groups, w.layers)
     seq = _sequence(groups, bonds, w.n_sites, which)
-    # default tiles and runs: 2^12 amplitudes, runs of 8 amplitudes (c = 3)
-    for dtype, k, c in [(H.C64, 12, 3), (H.C128, 12, 3)]:
+    # default tiles and runs: c64 2^12 amplitudes, runs of 8 (c = 3);
+    # c128 2^10 amplitudes, runs of 2 (c = 1)
+    for dtype, k, c in [(H.C64, 12, 3), (H.C128, 10, 1)]:
         k = min(k, w.n_qubits)
         plan = a.plan_describe(which, dtype)
         _check_schedule(plan, seq, w.n_qubits, k, min(c, k), set(range(w.n_qubits)))
