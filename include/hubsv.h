@@ -70,7 +70,8 @@ typedef enum {
   HUB_EUNSUPPORTED = 2,  /* valid but outside what this build supports     */
   HUB_ENOMEM = 3,        /* a library-owned allocation failed              */
   HUB_ECUDA = 4,         /* a CUDA call or kernel launch failed            */
-  HUB_ETIMEOUT = 5       /* a bounded device wait ran out                  */
+  HUB_ETIMEOUT = 5       /* reserved: a bounded device wait ran out (no    */
+                         /* kernel of this build waits on another)         */
 } hub_status;
 
 typedef enum { HUB_C64 = 0, HUB_C128 = 1 } hub_dtype;

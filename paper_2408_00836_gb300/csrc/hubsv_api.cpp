@@ -2,7 +2,7 @@
 // and ansatz handles with their coefficient tables, the FP64 one-body
 // diagonalisation and determinant tables of the Slater-determinant initial
 // state, plan execution and the profiling hooks.  The planner lives in
-// hubsv_plan.cpp, the kernels in hubsv_kernels.cu.
+// hubsv_plan.cpp, the kernels in hubsv_sweep.cuh and hubsv_tables.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>

@@ -1,5 +1,6 @@
-// Internal data structures shared by the host planner (hubsv_host.cpp) and
-// the sm_103a kernels (hubsv_kernels.cu).  Not part of the public ABI.
+// Internal data structures shared by the host side (planner hubsv_plan.cpp,
+// API hubsv_api.cpp, hubsv_noalloc.cu) and the sm_103a kernels
+// (hubsv_sweep.cuh, hubsv_tables.cu).  Not part of the public ABI.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -240,7 +241,7 @@ __host__ __device__ inline uint32_t swz(uint32_t l, int dtype) {
 
 }  // namespace hubsv
 
-// Launchers implemented in hubsv_kernels.cu (C++ linkage, internal).
+// Launchers implemented in hubsv_tables.cu (C++ linkage, internal).
 namespace hubsv {
 cudaError_t launch_sweep(int dtype, const SweepDev& sw, const KernelArgs& a,
                          int grid, size_t smem, cudaStream_t st);
