@@ -259,7 +259,7 @@ def run_gpu(args, rank, world, dist):
     stream = torch.cuda.current_stream()
 
     def step():
-        a.energy_grad(theta, psi, lam, E, g, dtype=dtype, batch=batch)
+        a.energy_grad(theta, psi, lam, E, g, dtype=dtype, batch=batch, sweeps=args.sweeps)
 
     for _ in range(args.warmup):
         step()
@@ -291,7 +291,8 @@ def run_gpu(args, rank, world, dist):
 
     # roofline of the dominant kernel
     names = {(1, 0): "sweep_kernel<float,1>", (2, 0): "sweep_kernel<float,2>",
-             (1, 1): "sweep_kernel<double,1>", (2, 1): "sweep_kernel<double,2>"}
+             (1, 1): "sweep_kernel<double,1>", (2, 1): "sweep_kernel<double,2>",
+             (0, 0): "small_kernel<float>", (0, 1): "small_kernel<double>"}
     agg = {}
     for nv, dt, by, ms in recs:
         k = names[(nv, dt)]
@@ -301,15 +302,25 @@ def run_gpu(args, rank, world, dist):
         s[2] += ms
     tot_ms = sum(v[2] for v in agg.values()) or 1.0
     dom = max(agg.items(), key=lambda kv: kv[1][2])
-    peak, peak_kind = _peaks()
+    on_chip = dom[0].startswith("small_kernel")
     ach = dom[1][1] / (dom[1][2] / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": dom[0], "achieved": round(ach, 1), "peak": peak,
+    if on_chip:
+        # sector amplitudes live in shared memory: the bound is its bandwidth,
+        # 32 banks x 4 B per clock per SM, at the sampled maximum SM clock
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (ck or {}).get("sm_max_mhz") or 2070.0
+        peak, peak_kind = round(128.0 * sms * mhz * 1e6 / 1e9, 1), f"derived: 128 B/clk x {sms} SMs x {mhz:.0f} MHz"
+        bound = "smem"
+    else:
+        peak, peak_kind = _peaks()
+        bound = "hbm"
+    roof = {"bound": bound, "kernel": dom[0], "achieved": round(ach, 1), "peak": peak,
             "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": peak_kind,
-            "traffic": _traffic(dom[0], w.name, args.dtype),
+            "traffic": None if on_chip else _traffic(dom[0], w.name, args.dtype),
             "launches": dom[1][0], "share": round(dom[1][2] / tot_ms, 4),
             "kernels": {k: {"launches": v[0], "ms": round(v[2], 3), "share": round(v[2] / tot_ms, 4),
                             "GB/s": round(v[1] / (v[2] / 1e3) / 1e9, 1)} for k, v in agg.items()}}
-    hbm_tbs = bytes_per_state * batch * args.steps / (ms_total / 1e3) / 1e12
+    hbm_tbs = 0.0 if on_chip else bytes_per_state * batch * args.steps / (ms_total / 1e3) / 1e12
 
     # end to end through the C ABI with host buffers
     E_h = torch.empty(batch, dtype=torch.float64).pin_memory()
@@ -319,7 +330,7 @@ def run_gpu(args, rank, world, dist):
     e0.record(stream)
     for _ in range(args.steps):
         theta.copy_(theta_h, non_blocking=True)
-        a.energy_grad(theta, psi, lam, E, g, dtype=dtype, batch=batch)
+        a.energy_grad(theta, psi, lam, E, g, dtype=dtype, batch=batch, sweeps=args.sweeps)
         E_h.copy_(E, non_blocking=True)
         g_h.copy_(g, non_blocking=True)
         stream.synchronize()
@@ -329,7 +340,9 @@ def run_gpu(args, rank, world, dist):
     e2e = {"value": round(job_value(world, batch, args.steps, e2e_ms), 4), "unit": "evals/s",
            "h2d_bytes_per_step": int(theta_h.numel() * 8),
            "d2h_bytes_per_step": int((E_h.numel() + g_h.numel()) * 8)}
-    launches = args.steps * (n_sweeps + 3)
+    # per step: the recorded main kernels, plus the coefficient and finalize
+    # kernels, plus the accumulator clear of the sweep engine
+    launches = len(recs) + args.steps * (2 if on_chip else 3)
 
     out = {"metric": METRIC, "value": round(value, 4), "unit": "evals/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
@@ -339,7 +352,9 @@ def run_gpu(args, rank, world, dist):
                       "params": a.P, "batch_per_gpu": batch, "parallelism": f"replicas x{world}",
                       "l2": "inputs larger than L2 (psi = %.1f GB for the batch)" % (batch * a.amp_bytes(dtype) / 1e9)},
            "hbm_tbs": round(hbm_tbs, 3),
-           "plan": {"sweeps": n_sweeps, "bytes_per_eval": bytes_per_state},
+           "plan": ({"engine": "on-chip (one CTA per state, sector amplitudes in shared memory)",
+                     "hbm_bytes_per_eval": 0} if on_chip else
+                    {"engine": "sweeps", "sweeps": n_sweeps, "bytes_per_eval": bytes_per_state}),
            "energy": E_val, "roofline": roof, "e2e": e2e, "gpu_launches": launches,
            "clocks": ck}
     if tune:
@@ -367,13 +382,13 @@ def run_c128(args, w, a, H, torch, dev, theta, ms_c64):
     lam = torch.empty_like(psi)
     E = torch.empty(w.batch, dtype=torch.float64, device=dev)
     g = torch.empty((w.batch, a.P), dtype=torch.float64, device=dev)
-    a.energy_grad(theta, psi, lam, E, g, dtype=H.C128, batch=w.batch)   # warm-up
+    a.energy_grad(theta, psi, lam, E, g, dtype=H.C128, batch=w.batch, sweeps=args.sweeps)   # warm-up
     torch.cuda.synchronize()
     steps = max(1, args.c128_steps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(steps):
-        a.energy_grad(theta, psi, lam, E, g, dtype=H.C128, batch=w.batch)
+        a.energy_grad(theta, psi, lam, E, g, dtype=H.C128, batch=w.batch, sweeps=args.sweeps)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
@@ -398,6 +413,8 @@ def main():
     ap.add_argument("--tile", type=int, default=0, help="log2 tile override (0 = planner default)")
     ap.add_argument("--autotune", action="store_true", help="pick the tile size by timing first")
     ap.add_argument("--runs", type=int, default=0, help="log2 contiguous amplitudes per HBM run (0 = default)")
+    ap.add_argument("--sweeps", action="store_true",
+                    help="run the HBM sweep engine even where the sector fits on chip")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -87,6 +87,8 @@ typedef enum { HUB_PREP_SLATER = 0, HUB_PREP_NEEL = 1 } hub_prep;
                                     one set by the last state_prepare call
                                     and is generated inside the first sweep   */
 #define HUB_FLAG_KEEP_STATE 2u   /* energy: leave the final state psi_K in psi */
+#define HUB_FLAG_SWEEPS     4u   /* run as HBM sweeps even where the on-chip
+                                    path applies (see energy_grad)             */
 
 /* Lattice: sites 0..n_sites-1, undirected bonds (pairs of sites).  mode_up /
  * mode_dn map a site to its two qubits; both NULL = blocked order (up i -> i,

@@ -29,6 +29,7 @@ HOP, ONSITE, NN_V, POT, RZ = 0, 1, 2, 3, 4
 PREP_SLATER, PREP_NEEL = 0, 1
 FLAG_PREP_FUSED = 1
 FLAG_KEEP_STATE = 2
+FLAG_SWEEPS = 4
 CLASS_IDS = {"h1": 0, "h2": 1, "v1": 2, "v2": 3, "even": 0, "odd": 1}
 
 
@@ -196,20 +197,22 @@ class Ansatz:
         del pa, na
 
     def energy(self, theta, psi, E, dtype=C64, batch: int = 1, fused: bool = True,
-               keep_state: bool = False, stream=None):
-        flags = (FLAG_PREP_FUSED if fused else 0) | (FLAG_KEEP_STATE if keep_state else 0)
+               keep_state: bool = False, sweeps: bool = False, stream=None):
+        flags = ((FLAG_PREP_FUSED if fused else 0) | (FLAG_KEEP_STATE if keep_state else 0)
+                 | (FLAG_SWEEPS if sweeps else 0))
         check(lib().energy(self._h, _ptr(theta, 8 * batch * self.P, "theta"),
                            _ptr(psi, batch * self.amp_bytes(dtype), "psi"), _ptr(E, 8 * batch, "E"),
                            dtype, batch, flags, _stream(stream)))
         return E
 
     def energy_grad(self, theta, psi, lam, E, grad, ckpt=None, dtype=C64, batch: int = 1,
-                    fused: bool = True, stream=None):
+                    fused: bool = True, sweeps: bool = False, stream=None):
         nb = batch * self.amp_bytes(dtype)
         check(lib().energy_grad(self._h, _ptr(theta, 8 * batch * self.P, "theta"), _ptr(psi, nb, "psi"),
                                 _ptr(lam, nb, "lam"), _ptr(ckpt, nb, "ckpt"), _ptr(E, 8 * batch, "E"),
                                 _ptr(grad, 8 * batch * self.P, "grad"), dtype, batch,
-                                FLAG_PREP_FUSED if fused else 0, _stream(stream)))
+                                (FLAG_PREP_FUSED if fused else 0) | (FLAG_SWEEPS if sweeps else 0),
+                                _stream(stream)))
         return E, grad
 
     def apply_h(self, psi, lam, dtype=C64, batch: int = 1, stream=None):

@@ -1,6 +1,6 @@
 """Build the in-tree CUDA library libhubsv.so for sm_103a with nvcc.
 
-Two translation units are compiled in parallel and linked into one shared
+The translation units are compiled in parallel and linked into one shared
 library next to this file.  Usage: ``python -m paper_2408_00836_gb300.build``.
 """
 
@@ -16,7 +16,8 @@ LIB = os.path.join(HERE, "libhubsv.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["hubsv_api.cpp", "hubsv_plan.cpp", "hubsv_tables.cu", "hubsv_sweep_f1.cu",
-           "hubsv_sweep_f2.cu", "hubsv_sweep_d1.cu", "hubsv_sweep_d2.cu", "hubsv_noalloc.cu"]
+           "hubsv_sweep_f2.cu", "hubsv_sweep_d1.cu", "hubsv_sweep_d2.cu", "hubsv_noalloc.cu",
+           "hubsv_small.cu"]
 
 
 def _nvcc():

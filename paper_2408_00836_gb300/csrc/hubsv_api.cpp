@@ -54,6 +54,7 @@ void hub_ansatz::prof_clear() {
 hub_ansatz::~hub_ansatz() {
   prof_clear();
   for (auto& kv : plans) delete kv.second;
+  for (auto& kv : small_plans) delete kv.second;
 }
 
 // ---------------------------------------------------------------------------
@@ -689,6 +690,112 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
   return HUB_OK;
 }
 
+// The on-chip path (hubsv_small.cu) for a call, or nullptr when the call
+// must run as sweeps: the state is caller-given or must be kept, the caller
+// asked for sweeps, or the sector does not fit in one CTA's shared memory.
+SmallPlan* small_plan_for(hub_ansatz* a, int which, int dtype, uint32_t flags, size_t& smem) {
+  if (!(flags & HUB_FLAG_PREP_FUSED) || (flags & (HUB_FLAG_KEEP_STATE | HUB_FLAG_SWEEPS))) return nullptr;
+  SmallPlan* sp = nullptr;
+  auto it = a->small_plans.find(which);
+  if (it != a->small_plans.end()) {
+    sp = it->second;
+  } else {
+    if (make_small_plan(a, which, sp) != HUB_OK) sp = nullptr;
+    a->small_plans[which] = sp;   // a failed build is remembered as nullptr
+  }
+  if (!sp) return nullptr;
+  // the kernel's multiply-high division is exact for n * d < 2^32
+  const uint64_t C = (uint64_t)sp->cup * (uint64_t)sp->cdn;
+  if (C * (uint64_t)std::max(sp->cup, sp->cdn) >= (1ull << 32)) return nullptr;
+  smem = small_smem_bytes(dtype, sp->cup, sp->cdn, (int)sp->pairs.size(), a->P + 2);
+  if ((int)smem > sweep_max_smem_optin()) return nullptr;
+  return sp;
+}
+
+hub_status run_small(hub_ansatz* a, SmallPlan* sp, size_t smem, int dtype, const double* theta, int64_t batch,
+                     double* E, double* grad, cudaStream_t st) {
+  const int n_slots = a->P + 2;
+  hub_status s;
+  if ((s = ensure_device(a)) != HUB_OK) return s;
+  if (!sp->uploaded) {
+    if ((s = sp->d_ops.upload(sp->ops, "on-chip ops")) != HUB_OK ||
+        (s = sp->d_xup.upload(sp->xup, "up patterns")) != HUB_OK ||
+        (s = sp->d_xdn.upload(sp->xdn, "down patterns")) != HUB_OK ||
+        (s = sp->d_pairs.upload(sp->pairs, "pattern pairs")) != HUB_OK)
+      return s;
+    sp->uploaded = true;
+  }
+  const size_t r2 = dtype == HUB_C64 ? 8 : 16;
+  if ((s = a->d_coef[dtype].ensure(r2 * std::max<int64_t>(1, batch * a->n_gates), "coefficients")) != HUB_OK) return s;
+  if ((s = a->d_phase[dtype].ensure(r2 * std::max<int64_t>(1, batch * a->n_tab), "phase tables")) != HUB_OK) return s;
+  if ((s = a->d_acc.ensure(8 * (size_t)batch * n_slots, "accumulators")) != HUB_OK) return s;
+  if (theta) {
+    HUB_CUDA(launch_coef(dtype, theta, a->P, (const int32_t*)a->d_gate_param.p, (const double*)a->d_gate_t.p,
+                         a->n_gates, a->d_coef[dtype].p, (const int32_t*)a->d_tab_param.p,
+                         (const double*)a->d_tab_val.p, a->n_tab, a->n_inst, a->d_phase[dtype].p, batch,
+                         a->n_inst, st),
+             "coefficient kernel");
+  }
+  SmallArgs ka;
+  std::memset(&ka, 0, sizeof(ka));
+  ka.ops = (const SmallOpDev*)sp->d_ops.p;
+  ka.n_ops = (int)sp->ops.size();
+  ka.xup = (const uint32_t*)sp->d_xup.p;
+  ka.xdn = (const uint32_t*)sp->d_xdn.p;
+  ka.cup = sp->cup;
+  ka.cdn = sp->cdn;
+  ka.ld = sp->cup | 1;
+  ka.m_cup = small_magic(sp->cup);
+  ka.m_cdn = small_magic(sp->cdn);
+  ka.pairs = (const uint32_t*)sp->d_pairs.p;
+  ka.n_pairs = (int)sp->pairs.size();
+  ka.diag_ops = (const DiagOpDev*)a->d_diag.p;
+  ka.coef = a->d_coef[dtype].p;
+  ka.n_gates = a->n_gates;
+  ka.hcoef = (const double*)a->d_hcoef.p;
+  ka.n_hterms = (int)a->hterms.size();
+  ka.real_tabs = (const double*)a->d_real.p;
+  ka.real_tabs32 = (const float*)a->d_real32.p;
+  ka.real_stride = a->real_stride;
+  ka.phase_tabs = a->d_phase[dtype].p;
+  ka.phase_stride = a->n_tab;
+  ka.n_inst = a->n_inst;
+  ka.s = a->s;
+  ka.upmask = a->upmask;
+  ka.batch = batch;
+  ka.acc = (double*)a->d_acc.p;
+  ka.n_slots = n_slots;
+  ka.slot_E = a->P;
+  ka.slot_N = a->P + 1;
+  ka.prep.kind = a->prep_kind;
+  ka.prep.L = a->L;
+  ka.prep.s = a->s;
+  ka.prep.layout = a->layout;
+  ka.prep.neel_x0 = a->neel_x0;
+  ka.prep.sd = (const double*)a->d_sd.p;
+  ka.prep.sd32 = (const float*)a->d_sd32.p;
+  const int sms = device_sm_count();
+  if (sms <= 0) return fail(HUB_ECUDA, "no CUDA device");
+  const int per_sm = std::max(1, small_max_ctas_per_sm(dtype, smem));
+  const int64_t grid = std::min<int64_t>(batch, (int64_t)sms * per_sm);
+  hub_ansatz::ProfRec rec{};
+  if (a->prof) {
+    HUB_CUDA(cudaEventCreate(&rec.e0), "cudaEventCreate");
+    HUB_CUDA(cudaEventCreate(&rec.e1), "cudaEventCreate");
+    HUB_CUDA(cudaEventRecord(rec.e0, st), "cudaEventRecord");
+  }
+  HUB_CUDA(launch_small(dtype, ka, (int)grid, smem, st), "on-chip kernel launch");
+  if (a->prof) {
+    HUB_CUDA(cudaEventRecord(rec.e1, st), "cudaEventRecord");
+    rec.nv = 0;   // on-chip: shared-memory amplitude traffic, no vector in HBM
+    rec.dtype = dtype;
+    rec.bytes = (double)sp->accesses * (double)(dtype == HUB_C64 ? 8 : 16) * (double)batch;
+    a->prof_recs.push_back(rec);
+  }
+  HUB_CUDA(launch_finalize((const double*)a->d_acc.p, n_slots, a->P, a->P, E, grad, batch, st), "finalize kernel");
+  return HUB_OK;
+}
+
 hub_status check_call(hub_ansatz* a, int32_t dtype, int64_t batch) {
   if (!a) return fail(HUB_EINVAL, "NULL ansatz");
   if (dtype != HUB_C64 && dtype != HUB_C128) return fail(HUB_EINVAL, "dtype must be HUB_C64 or HUB_C128");
@@ -772,8 +879,11 @@ extern "C" hub_status energy(ans_t a, const double* theta, void* psi, double* E,
   if (!psi || !E || (a->P > 0 && !theta)) return fail(HUB_EINVAL, "energy: NULL buffer");
   if ((flags & HUB_FLAG_PREP_FUSED) && a->prep_kind < 0)
     return fail(HUB_EINVAL, "energy: HUB_FLAG_PREP_FUSED needs a prior state_prepare");
+  size_t smem = 0;
+  if (SmallPlan* sp = small_plan_for(a, 0, dtype, flags, smem))
+    return run_small(a, sp, smem, dtype, theta, batch, E, nullptr, (cudaStream_t)stream);
   Plan* pl;
-  if ((s = get_plan(a, 0, dtype, flags, pl)) != HUB_OK) return s;
+  if ((s = get_plan(a, 0, dtype, flags & 3u, pl)) != HUB_OK) return s;
   return run_plan(a, pl, dtype, theta, psi, nullptr, nullptr, batch, E, nullptr, (cudaStream_t)stream);
 }
 
@@ -787,6 +897,9 @@ extern "C" hub_status energy_grad(ans_t a, const double* theta, void* psi, void*
   if ((flags & HUB_FLAG_PREP_FUSED) && a->prep_kind < 0)
     return fail(HUB_EINVAL, "energy_grad: HUB_FLAG_PREP_FUSED needs a prior state_prepare");
   if (ckpt && (ckpt == psi || ckpt == lam)) return fail(HUB_EINVAL, "energy_grad: ckpt must be a third buffer");
+  size_t smem = 0;
+  if (SmallPlan* sp = small_plan_for(a, 1, dtype, flags, smem))
+    return run_small(a, sp, smem, dtype, theta, batch, E, grad, (cudaStream_t)stream);
   const uint32_t pf = (flags & 3u) | (ckpt ? kPlanCkpt : 0u);
   Plan* pl;
   if ((s = get_plan(a, 1, dtype, pf, pl)) != HUB_OK) return s;

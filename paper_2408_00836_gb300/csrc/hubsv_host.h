@@ -8,6 +8,7 @@
 
 #include "hubsv.h"
 #include "hubsv_internal.h"
+#include "hubsv_small.h"
 
 namespace hubsv {
 
@@ -65,6 +66,16 @@ struct Plan {
   double bytes_per_state = 0;             // amplitude bytes moved per state
 };
 
+// On-chip plan of a call kind (see SmallOpDev).
+struct SmallPlan {
+  int cup = 0, cdn = 0;
+  std::vector<uint32_t> xup, xdn, pairs;
+  std::vector<SmallOpDev> ops;
+  double accesses = 0;   // shared-memory amplitude loads + stores of one evaluation
+  DevBuf d_ops, d_xup, d_xdn, d_pairs;
+  bool uploaded = false;
+};
+
 }  // namespace hubsv
 
 struct hub_model {
@@ -101,6 +112,7 @@ struct hub_ansatz {
   uint64_t neel_x0 = 0;
   hubsv::DevBuf d_coef[2], d_phase[2], d_acc;
   std::map<int, hubsv::Plan*> plans;     // key = which*16 + dtype*4 + flags
+  std::map<int, hubsv::SmallPlan*> small_plans;   // key = which
   int tile_override[2] = {0, 0};
   int run_override[2] = {0, 0};         // log2 contiguous amplitudes per run (0 = default)
   bool dev_ready = false;
@@ -122,4 +134,8 @@ inline int default_tile_bits(int dtype) { return dtype == HUB_C64 ? 12 : 10; }
 inline int default_run_bits(int dtype) { return dtype == HUB_C64 ? 3 : 1; }
 uint64_t diag_support(const hub_ansatz* a, int di);
 hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*& out);
+// The operation sequence of a call kind (0 energy, 1 energy + gradient, 2
+// lam = H psi, 3 initial state only), before any tiling.
+std::vector<SeqOp> op_sequence(const hub_ansatz* a, int which, uint32_t flags);
+hub_status make_small_plan(hub_ansatz* a, int which, SmallPlan*& out);
 }  // namespace hubsv

@@ -224,6 +224,10 @@ void choose_lanes(uint32_t free_bits, uint32_t required, int dtype, uint8_t* lan
 
 }  // namespace
 
+std::vector<SeqOp> op_sequence(const hub_ansatz* a, int which, uint32_t flags) {
+  return build_sequence(a, which, flags);
+}
+
 hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*& out) {
   const int n = a->n;
   if (n < kLaneBits + 1) return fail(HUB_EUNSUPPORTED, "need at least 6 qubits (3 sites)");

@@ -21,7 +21,7 @@ DT = {H.C64: torch.complex64, H.C128: torch.complex128}
 
 
 def _run(prob, theta, dtype, batch=1, grad=True, prep_kind=H.PREP_SLATER, neel_up=None,
-         keep_state=False):
+         keep_state=False, sweeps=False):
     dev = "cuda"
     a = prob.ans
     a.state_prepare(prep_kind, prob.perturb, neel_up, None, dtype, batch)
@@ -31,10 +31,10 @@ def _run(prob, theta, dtype, batch=1, grad=True, prep_kind=H.PREP_SLATER, neel_u
     if grad:
         lam = torch.empty_like(psi)
         g = torch.empty((batch, a.P), dtype=torch.float64, device=dev)
-        a.energy_grad(th, psi, lam, E, g, dtype=dtype, batch=batch)
+        a.energy_grad(th, psi, lam, E, g, dtype=dtype, batch=batch, sweeps=sweeps)
         H.sync()
         return E.cpu().numpy(), g.cpu().numpy(), None
-    a.energy(th, psi, E, dtype=dtype, batch=batch, keep_state=keep_state)
+    a.energy(th, psi, E, dtype=dtype, batch=batch, keep_state=keep_state, sweeps=sweeps)
     H.sync()
     return E.cpu().numpy(), None, (psi.cpu().numpy() if keep_state else None)
 
@@ -84,9 +84,10 @@ def _disordered_2x3(modes="blocked", V=0.4):
     return t, U, Vm
 
 
+@pytest.mark.parametrize("sweeps", [False, True])
 @pytest.mark.parametrize("modes", ["blocked", "interleaved"])
 @pytest.mark.parametrize("dtype", [H.C128, H.C64])
-def test_disordered_extended_2x3_all_group_kinds(modes, dtype):
+def test_disordered_extended_2x3_all_group_kinds(modes, dtype, sweeps):
     t, U, Vm = _disordered_2x3()
     prob = Problem(2, 3, modes=modes, t=t, U=U, V=Vm, layers=2,
                    classes=("U", "V", "pot", "h1", "v1", "h2", "v2"))
@@ -95,14 +96,17 @@ def test_disordered_extended_2x3_all_group_kinds(modes, dtype):
     assert rel_err(st[0], prob.full(prob.oracle_state(theta))) < TOL[dtype]
     Eo, go = prob.oracle_energy_grad(theta)
     assert abs(E[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
-    E2, g, _ = _run(prob, theta, dtype)
+    E2, g, _ = _run(prob, theta, dtype, sweeps=sweeps)
     assert abs(E2[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
     assert np.max(np.abs(g[0] - go)) < TOL[dtype] * max(1.0, np.max(np.abs(go)))
     assert g[0][6] == 0.0 and g[0][13] == 0.0      # v2 is empty on two rows
+    E3, _, _ = _run(prob, theta, dtype, grad=False, sweeps=sweeps)
+    assert abs(E3[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
 
 
+@pytest.mark.parametrize("sweeps", [False, True])
 @pytest.mark.parametrize("dtype", [H.C128, H.C64])
-def test_neel_start(dtype):
+def test_neel_start(dtype, sweeps):
     t, U, Vm = _disordered_2x3()
     prob = Problem(2, 3, t=t, U=U, V=Vm, layers=2, classes=("U", "V", "h1", "v1", "h2"))
     neel = [1 if (x + y) % 2 == 0 else 0 for (x, y) in prob.lat.coords]
@@ -111,16 +115,17 @@ def test_neel_start(dtype):
     psi0 = O.neel_state(om, prob.lat, prob.basis)
     E0 = O.energy(om, prob.basis, prob.ogroups, np.zeros(prob.P), psi0, prob.Hmat())
     assert abs(E0 - O.neel_energy(om)) < 1e-12
-    Eg, gg, _ = _run(prob, np.zeros(prob.P), dtype, prep_kind=H.PREP_NEEL, neel_up=neel)
+    Eg, gg, _ = _run(prob, np.zeros(prob.P), dtype, prep_kind=H.PREP_NEEL, neel_up=neel, sweeps=sweeps)
     assert abs(Eg[0] - O.neel_energy(om)) < TOL[dtype] * max(1.0, abs(E0))
-    Eg, gg, _ = _run(prob, theta, dtype, prep_kind=H.PREP_NEEL, neel_up=neel)
+    Eg, gg, _ = _run(prob, theta, dtype, prep_kind=H.PREP_NEEL, neel_up=neel, sweeps=sweeps)
     Eo, go = O.energy_and_gradient(om, prob.basis, prob.ogroups, theta, psi0, prob.Hmat())
     assert abs(Eg[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
     assert np.max(np.abs(gg[0] - go)) < TOL[dtype] * max(1.0, np.max(np.abs(go)))
 
 
+@pytest.mark.parametrize("sweeps", [False, True])
 @pytest.mark.parametrize("dtype", [H.C64, H.C128])
-def test_grid2x4_batched_instances(dtype):
+def test_grid2x4_batched_instances(dtype, sweeps):
     """Workload 2 shape (16 qubits, snake order, perturbed orbitals, four U
     instances) with two seeded parameter sets: batch of 8 states."""
     w = W.workload(2, batch_sets=2)
@@ -130,13 +135,13 @@ def test_grid2x4_batched_instances(dtype):
     prob = Problem(2, 4, order="snake", layers=4, classes=w.classes, perturb=w.orbital_perturbation(),
                    instances=inst)
     theta = w.theta()
-    E, g, _ = _run(prob, theta, dtype, batch=w.batch)
+    E, g, _ = _run(prob, theta, dtype, batch=w.batch, sweeps=sweeps)
     for b in range(w.batch):
         Eo, go = prob.oracle_energy_grad(theta[b], r=b % 4)
         assert abs(E[b] - Eo) < TOL[dtype] * max(1.0, abs(Eo)), b
         assert np.max(np.abs(g[b] - go)) < TOL[dtype] * max(1.0, np.max(np.abs(go))), b
     # energy-only path, same batch
-    E2, _, _ = _run(prob, theta, dtype, batch=w.batch, grad=False)
+    E2, _, _ = _run(prob, theta, dtype, batch=w.batch, grad=False, sweeps=sweeps)
     assert np.max(np.abs(E2 - E)) < TOL[dtype] * max(1.0, np.max(np.abs(E)))
 
 
