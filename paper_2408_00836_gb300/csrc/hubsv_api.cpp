@@ -328,6 +328,11 @@ int add_diag_op(hub_ansatz* a, const std::vector<std::vector<double>>& xcoef,
     }
     a->tab_val.swap(nv);
     for (int e = 0; e < len; ++e) a->tab_param.push_back(param);
+    for (int i = 0; i < d.has_x; ++i)
+      for (int j = 0; j < 256; ++j) a->tab_live.push_back(a->n_tab + i * 256 + j);
+    for (int i = 0; i < d.has_y; ++i)
+      for (int j = 0; j < 256; ++j) a->tab_live.push_back(a->n_tab + 1024 + i * 256 + j);
+    for (int e = 0; e < vlen; ++e) a->tab_live.push_back(a->n_tab + 2048 + e);
     a->n_tab += len;
   } else {
     d.phase_off = -1;
@@ -556,6 +561,8 @@ hub_status ensure_device(hub_ansatz* a) {
       (st = a->d_gate_t.upload(a->gate_t, "gate coefficients")) != HUB_OK ||
       (st = a->d_tab_param.upload(a->tab_param, "phase params")) != HUB_OK ||
       (st = a->d_tab_val.upload(a->tab_val, "phase values")) != HUB_OK ||
+      (st = a->d_tab_live.upload(a->tab_live.empty() ? std::vector<int32_t>(1) : a->tab_live,
+                                 "phase entries")) != HUB_OK ||
       (st = a->d_hcoef.upload(a->hcoef, "hop coefficients")) != HUB_OK ||
       (st = a->d_real.upload(a->real_tabs, "diagonal tables")) != HUB_OK ||
       (st = a->d_real32.upload(std::vector<float>(a->real_tabs.begin(), a->real_tabs.end()),
@@ -595,7 +602,8 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
   if (theta) {
     HUB_CUDA(launch_coef(dtype, theta, a->P, (const int32_t*)a->d_gate_param.p, (const double*)a->d_gate_t.p,
                          a->n_gates, a->d_coef[dtype].p, (const int32_t*)a->d_tab_param.p,
-                         (const double*)a->d_tab_val.p, a->n_tab, a->n_inst, a->d_phase[dtype].p, batch,
+                         (const double*)a->d_tab_val.p, a->n_tab, (const int32_t*)a->d_tab_live.p,
+                         (int)a->tab_live.size(), a->d_phase[dtype].p, batch,
                          a->n_inst, st),
              "coefficient kernel");
   }
@@ -707,7 +715,8 @@ SmallPlan* small_plan_for(hub_ansatz* a, int which, int dtype, uint32_t flags, s
   // the kernel's multiply-high division is exact for n * d < 2^32
   const uint64_t C = (uint64_t)sp->cup * (uint64_t)sp->cdn;
   if (C * (uint64_t)std::max(sp->cup, sp->cdn) >= (1ull << 32)) return nullptr;
-  smem = small_smem_bytes(dtype, sp->cup, sp->cdn, (int)sp->pairs.size(), a->P + 2);
+  smem = small_smem_bytes(dtype, sp->cup, sp->cdn, (int)sp->pairs.size(), a->P + 2, a->n_gates,
+                          (int)a->hterms.size());
   if ((int)smem > sweep_max_smem_optin()) return nullptr;
   return sp;
 }
@@ -732,7 +741,8 @@ hub_status run_small(hub_ansatz* a, SmallPlan* sp, size_t smem, int dtype, const
   if (theta) {
     HUB_CUDA(launch_coef(dtype, theta, a->P, (const int32_t*)a->d_gate_param.p, (const double*)a->d_gate_t.p,
                          a->n_gates, a->d_coef[dtype].p, (const int32_t*)a->d_tab_param.p,
-                         (const double*)a->d_tab_val.p, a->n_tab, a->n_inst, a->d_phase[dtype].p, batch,
+                         (const double*)a->d_tab_val.p, a->n_tab, (const int32_t*)a->d_tab_live.p,
+                         (int)a->tab_live.size(), a->d_phase[dtype].p, batch,
                          a->n_inst, st),
              "coefficient kernel");
   }

@@ -101,10 +101,11 @@ struct hub_ansatz {
   std::vector<double> gate_t;            // [n_inst][n_gates]
   std::vector<int32_t> tab_param;        // [n_tab]
   std::vector<double> tab_val;           // [n_inst][n_tab]
+  std::vector<int32_t> tab_live;         // entries of the phase tables that kernels read
   std::vector<double> hcoef;             // [n_inst][n_hterms]
   std::vector<double> real_tabs;         // [n_inst][real_stride]
   int n_gates = 0, n_tab = 0, real_stride = 0;
-  hubsv::DevBuf d_gate_param, d_gate_t, d_tab_param, d_tab_val, d_hcoef, d_real, d_diag;
+  hubsv::DevBuf d_gate_param, d_gate_t, d_tab_param, d_tab_val, d_tab_live, d_hcoef, d_real, d_diag;
   hubsv::DevBuf d_real32;                // FP32 copy of real_tabs
   hubsv::DevBuf d_sd, d_sd32;            // Slater determinant tables (FP64, FP32)
   std::vector<double> sd_host;           // host copy of the determinant tables

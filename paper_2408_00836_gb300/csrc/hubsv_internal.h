@@ -248,7 +248,7 @@ cudaError_t launch_sweep(int dtype, const SweepDev& sw, const KernelArgs& a,
 cudaError_t launch_coef(int dtype, const double* theta, int P, const int32_t* gate_param,
                         const double* gate_t, int n_gates, void* coef,
                         const int32_t* tab_param, const double* tab_val,
-                        int n_tab, int n_inst_tab, void* phase_tabs,
+                        int n_tab, const int32_t* tab_live, int n_live, void* phase_tabs,
                         int64_t batch, int n_inst, cudaStream_t st);
 cudaError_t launch_zero(double* p, int64_t n, cudaStream_t st);
 cudaError_t launch_finalize(const double* acc, int n_slots, int P, int slot_E,

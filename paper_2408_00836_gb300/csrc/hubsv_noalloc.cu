@@ -102,6 +102,7 @@ extern "C" hub_status energy_noalloc(ans_t a, const double* theta, void* psi, do
   const size_t o_gt = lay.take(8 * a->gate_t.size());
   const size_t o_tp = lay.take(4 * a->tab_param.size());
   const size_t o_tv = lay.take(8 * a->tab_val.size());
+  const size_t o_tl = lay.take(4 * a->tab_live.size());
   const size_t o_hc = lay.take(8 * a->hcoef.size());
   const size_t o_rt = lay.take(8 * a->real_tabs.size());
   const size_t o_r32 = lay.take(4 * real32.size());
@@ -130,6 +131,7 @@ extern "C" hub_status energy_noalloc(ans_t a, const double* theta, void* psi, do
   if (ce == cudaSuccess) ce = put(o_gt, a->gate_t.data(), 8 * a->gate_t.size());
   if (ce == cudaSuccess) ce = put(o_tp, a->tab_param.data(), 4 * a->tab_param.size());
   if (ce == cudaSuccess) ce = put(o_tv, a->tab_val.data(), 8 * a->tab_val.size());
+  if (ce == cudaSuccess) ce = put(o_tl, a->tab_live.data(), 4 * a->tab_live.size());
   if (ce == cudaSuccess) ce = put(o_hc, a->hcoef.data(), 8 * a->hcoef.size());
   if (ce == cudaSuccess) ce = put(o_rt, a->real_tabs.data(), 8 * a->real_tabs.size());
   if (ce == cudaSuccess) ce = put(o_r32, real32.data(), 4 * real32.size());
@@ -146,7 +148,8 @@ extern "C" hub_status energy_noalloc(ans_t a, const double* theta, void* psi, do
   HUB_CUDA(launch_coef(dtype, theta, a->P, reinterpret_cast<const int32_t*>(S + o_gp),
                        reinterpret_cast<const double*>(S + o_gt), a->n_gates, S + o_cf,
                        reinterpret_cast<const int32_t*>(S + o_tp), reinterpret_cast<const double*>(S + o_tv),
-                       a->n_tab, a->n_inst, S + o_pt, batch, a->n_inst, s),
+                       a->n_tab, reinterpret_cast<const int32_t*>(S + o_tl), (int)a->tab_live.size(),
+                       S + o_pt, batch, a->n_inst, s),
            "energy_noalloc: coefficient kernel");
   KernelArgs ka;
   std::memset(&ka, 0, sizeof(ka));

@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <type_traits>
 
 #include "hubsv_host.h"
 #include "hubsv_sweep.cuh"
@@ -126,11 +127,18 @@ hub_status make_small_plan(hub_ansatz* a, int which, SmallPlan*& out) {
 
 uint32_t small_magic(int d) { return d <= 1 ? 0u : (uint32_t)((((uint64_t)1 << 32) + (uint64_t)d - 1) / (uint64_t)d); }
 
-size_t small_smem_bytes(int dtype, int cup, int cdn, int n_pairs, int n_slots) {
+namespace {
+constexpr int kSmallThreads = 512;
+constexpr int kSmallWarps = kSmallThreads / 32;
+}  // namespace
+
+size_t small_smem_bytes(int dtype, int cup, int cdn, int n_pairs, int n_slots, int n_gates, int n_hterms) {
   const size_t amp = dtype == 0 ? 8 : 16;
   const size_t c = (size_t)(cup | 1) * (size_t)cdn;       // rows of odd pitch
   size_t s = 2 * c * amp;                                   // psi, lam
-  s += 8 * (size_t)n_slots;                                 // accumulators
+  s += amp * (size_t)n_gates;                               // (cos, sin) of the element
+  s += 8 * (size_t)kSmallWarps * (size_t)n_slots;          // accumulators, one row per warp
+  s += amp / 2 * (size_t)n_hterms;                          // -t of the element's instance
   s += 4 * ((size_t)cup + (size_t)cdn + (size_t)n_pairs);   // patterns, pair lists
   return (s + 15) & ~(size_t)15;
 }
@@ -141,13 +149,85 @@ size_t small_smem_bytes(int dtype, int cup, int cdn, int n_pairs, int n_slots) {
 
 namespace {
 
-constexpr int kSmallThreads = 512;
-
-// Sum of v over the CTA into acc[slot] (FP64, shared memory).
-__device__ __forceinline__ void block_add(double* acc, int slot, double v) {
-  v = warp_sum(v);
-  if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(&acc[slot], v);
+// FP64 arithmetic is a small fraction of FP32 throughput on this part, so
+// the complex64 kernel reduces in FP32 and keeps its running totals as
+// unevaluated float pairs (hi + lo) updated with Knuth's TwoSum, which is
+// exact: the totals carry about 48 bits although no FP64 instruction runs
+// per operation.  The complex128 kernel reduces in FP64.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
 }
+
+// (h, l) += v, renormalised so that |l| <= ulp(h) / 2.
+__device__ __forceinline__ void ff_add(float& h, float& l, float v) {
+  float s, e;
+  two_sum(h, v, s, e);
+  e += l;
+  h = s + e;
+  l = e - (h - s);
+}
+
+// Sum of float pairs over the warp, into lane 0's (h, l).
+__device__ __forceinline__ void warp_sum_ff(float& h, float& l) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+    float s, e;
+    two_sum(h, h2, s, e);
+    e += l + l2;
+    h = s + e;
+    l = e - (h - s);
+  }
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Running totals of one thread (R = float: float pairs; double: FP64).
+template <typename R> struct Tot;
+template <> struct Tot<float> {
+  float h = 0.f, l = 0.f;
+  __device__ __forceinline__ void add(float v) { ff_add(h, l, v); }
+};
+template <> struct Tot<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+};
+
+// Per-warp accumulator rows: row w, slot i at acc[w * n_slots + i], float
+// pairs (c64) or doubles (c128); lane 0 of warp w alone writes row w, so no
+// atomics are needed, and the rows are summed in FP64 once per element.
+// Adds the warp's sum of v to its row's slot (every lane calls).
+__device__ __forceinline__ void row_add(float2* acc, int n_slots, int slot, float v) {
+  v = warp_sum_f(v);
+  if ((threadIdx.x & 31) == 0) {
+    float2& t = acc[(threadIdx.x >> 5) * n_slots + slot];
+    ff_add(t.x, t.y, v);
+  }
+}
+__device__ __forceinline__ void row_add(double* acc, int n_slots, int slot, double v) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) acc[(threadIdx.x >> 5) * n_slots + slot] += v;
+}
+// Adds the warp's sum of the lanes' running totals to its row (every lane calls).
+__device__ __forceinline__ void row_add_tot(float2* acc, int n_slots, int slot, Tot<float> t) {
+  warp_sum_ff(t.h, t.l);
+  if ((threadIdx.x & 31) == 0) {
+    float2& r = acc[(threadIdx.x >> 5) * n_slots + slot];
+    ff_add(r.x, r.y, t.h);
+    ff_add(r.x, r.y, t.l);
+  }
+}
+__device__ __forceinline__ void row_add_tot(double* acc, int n_slots, int slot, Tot<double> t) {
+  row_add(acc, n_slots, slot, t.v);
+}
+__device__ __forceinline__ double row_value(const float2& v) { return (double)v.x + (double)v.y; }
+__device__ __forceinline__ double row_value(double v) { return v; }
 
 // n / d for the n < 2^32 / d met here, with m = ceil(2^32 / d) from
 // small_magic (0 for d = 1): one high multiply instead of a division.
@@ -160,15 +240,18 @@ __device__ __forceinline__ uint32_t div_magic(uint32_t n, uint32_t m) { return m
 // matrix; the odd row pitch ld keeps the column accesses free of bank
 // conflicts.
 template <typename R>
-__global__ void __launch_bounds__(kSmallThreads, 1) small_kernel(const SmallArgs a) {
+__global__ void __launch_bounds__(kSmallThreads, sizeof(R) == 4 ? 2 : 1) small_kernel(const SmallArgs a) {
   using T2 = typename CT<R>::T2;
   constexpr int DT = CT<R>::DT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int C = a.cup * a.cdn, ld = a.ld;
   T2* psi = reinterpret_cast<T2*>(smem_raw);
   T2* lam = psi + (size_t)ld * a.cdn;
-  double* acc = reinterpret_cast<double*>(lam + (size_t)ld * a.cdn);
-  uint32_t* xup = reinterpret_cast<uint32_t*>(acc + a.n_slots);
+  T2* cs = lam + (size_t)ld * a.cdn;
+  using AccT = typename std::conditional<DT == 0, float2, double>::type;
+  AccT* acc = reinterpret_cast<AccT*>(cs + a.n_gates);   // [kSmallWarps][n_slots]
+  R* hc = reinterpret_cast<R*>(acc + kSmallWarps * a.n_slots);
+  uint32_t* xup = reinterpret_cast<uint32_t*>(hc + a.n_hterms);
   uint32_t* xdn = xup + a.cup;
   uint32_t* pairs = xdn + a.cdn;
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -185,7 +268,9 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_kernel(const SmallArgs
   for (int64_t b = blockIdx.x; b < a.batch; b += gridDim.x) {
     const int inst = (int)(b % a.n_inst);
     __syncthreads();   // tables copied; the previous element's read-out done
-    for (int i = tid; i < a.n_slots; i += nth) acc[i] = 0.0;
+    for (int i = tid; i < kSmallWarps * a.n_slots; i += nth) acc[i] = AccT{};
+    for (int i = tid; i < a.n_gates; i += nth) cs[i] = coef[b * a.n_gates + i];
+    for (int i = tid; i < a.n_hterms; i += nth) hc[i] = (R)a.hcoef[(size_t)inst * a.n_hterms + i];
     for (int f = tid; f < C; f += nth) {
       const int rd = (int)div_magic((uint32_t)f, a.m_cup), ru = f - rd * a.cup;
       const int e = rd * ld + ru;
@@ -193,18 +278,20 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_kernel(const SmallArgs
       lam[e] = mk<T2, R>((R)0, (R)0);
     }
     __syncthreads();
-    double eacc = 0.0, nacc = 0.0;   // this thread's share, over all operations
+    Tot<R> eacc, nacc;   // this thread's share, over all operations
+    SmallOpDev nxt = a.ops[0];
     for (int oi = 0; oi < a.n_ops; ++oi) {
-      const SmallOpDev op = a.ops[oi];
+      const SmallOpDev op = nxt;
+      if (oi + 1 < a.n_ops) nxt = a.ops[oi + 1];   // in flight during this operation
       R part = 0, npart = 0;   // this thread's share of one operation
       if (op.kind == OP_GIV || op.kind == OP_MEAS_HOP || op.kind == OP_LAM_HOP || op.kind == OP_GRAD_HOP) {
         R c = 0, s = 0, tc = 0;
         if (op.kind == OP_GIV) {
-          const T2 cs = coef[b * a.n_gates + op.gate];
-          c = cs.x;
-          s = (op.flags & OPF_INV) ? -cs.y : cs.y;
+          const T2 g = cs[op.gate];
+          c = g.x;
+          s = (op.flags & OPF_INV) ? -g.y : g.y;
         } else {
-          tc = (R)a.hcoef[(size_t)inst * a.n_hterms + op.hterm];
+          tc = hc[op.hterm];
         }
         const bool dol = (op.flags & OPF_LAM) != 0;
         const bool upair = op.spin == 0;
@@ -256,8 +343,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_kernel(const SmallArgs
             }
           }
         }
-        if (op.kind == OP_GRAD_HOP) block_add(acc, op.slot, 2.0 * (double)part);
-        else if (op.kind != OP_GIV) eacc += 2.0 * (double)part;
+        if (op.kind == OP_GRAD_HOP) row_add(acc, a.n_slots, op.slot, (R)2 * part);
+        else if (op.kind != OP_GIV) eacc.add((R)2 * part);
       } else {   // diagonal operations
         const DiagOpDev& d = a.diag_ops[op.a];
         const T2* ptab = ptabs + (size_t)b * a.phase_stride + d.phase_off;
@@ -292,18 +379,22 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_kernel(const SmallArgs
           }
         }
         if (op.kind == OP_GRAD_DIAG) {
-          block_add(acc, op.slot, 2.0 * (double)part);
+          row_add(acc, a.n_slots, op.slot, (R)2 * part);
         } else if (op.kind != OP_DIAG) {
-          eacc += (double)part;
-          nacc += (double)npart;
+          eacc.add(part);
+          nacc.add(npart);
         }
       }
       __syncthreads();
     }
-    block_add(acc, a.slot_E, eacc);
-    block_add(acc, a.slot_N, nacc);
+    row_add_tot(acc, a.n_slots, a.slot_E, eacc);
+    row_add_tot(acc, a.n_slots, a.slot_N, nacc);
     __syncthreads();
-    for (int i = tid; i < a.n_slots; i += nth) a.acc[(size_t)b * a.n_slots + i] = acc[i];
+    for (int i = tid; i < a.n_slots; i += nth) {
+      double x = 0.0;
+      for (int w = 0; w < kSmallWarps; ++w) x += row_value(acc[w * a.n_slots + i]);
+      a.acc[(size_t)b * a.n_slots + i] = x;
+    }
   }
 }
 

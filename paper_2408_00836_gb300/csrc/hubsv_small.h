@@ -50,9 +50,10 @@ struct SmallArgs {
   PrepDev prep;
 };
 
-// Shared memory of one CTA: psi and lam (ld x C_dn each), the accumulators
-// and the pattern and pair tables.
-size_t small_smem_bytes(int dtype, int cup, int cdn, int n_pairs, int n_slots);
+// Shared memory of one CTA: psi and lam (ld x C_dn each), the element's
+// Givens coefficients, the accumulators, the -t of its instance, and the
+// pattern and pair tables.
+size_t small_smem_bytes(int dtype, int cup, int cdn, int n_pairs, int n_slots, int n_gates, int n_hterms);
 // ceil(2^32 / d) for d > 1, 0 for d = 1: the multiplier of the kernel's
 // division n / d, exact for n * d < 2^32.
 uint32_t small_magic(int d);

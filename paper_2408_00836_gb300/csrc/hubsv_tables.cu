@@ -1,5 +1,7 @@
 // Small kernels of the Hubbard VQE statevector engine (coefficient and
 // phase tables, accumulator reset and read-out) and the launchers.
+#include <algorithm>
+
 #include "hubsv_internal.h"
 
 namespace hubsv {
@@ -38,6 +40,9 @@ __device__ __forceinline__ float2 unit_round<float>(double c, double s) {
   return make_float2(bc, bs);
 }
 
+// Batch elements along y, entries along x.  Only the phase-table entries
+// in tab_live (those some kernel reads: the byte tables a diagonal operator
+// uses) are made.
 template <typename R>
 __global__ void coef_kernel(const double* __restrict__ theta, int P,
                             const int32_t* __restrict__ gate_param,
@@ -45,27 +50,26 @@ __global__ void coef_kernel(const double* __restrict__ theta, int P,
                             typename CT<R>::T2* __restrict__ coef,
                             const int32_t* __restrict__ tab_param,
                             const double* __restrict__ tab_val, int n_tab,
+                            const int32_t* __restrict__ tab_live, int n_live,
                             typename CT<R>::T2* __restrict__ phase, int64_t batch, int n_inst) {
-  const int64_t per = (int64_t)n_gates + n_tab;
-  const int64_t total = per * batch;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = i / per;
-    const int64_t j = i - b * per;
+  const int per = n_gates + n_live;
+  for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
     const int inst = (int)(b % n_inst);
-    if (j < n_gates) {
-      const double al = theta[b * P + gate_param[j]] * gate_t[(int64_t)inst * n_gates + j];
-      double s, c;
-      sincos(al, &s, &c);
-      coef[b * n_gates + j] = unit_round<R>(c, s);
-    } else {
-      const int64_t e = j - n_gates;
-      const int pp = tab_param[e];
-      const double th = pp >= 0 ? theta[b * P + pp] : 0.0;
-      const double al = -th * tab_val[(int64_t)inst * n_tab + e];
-      double s, c;
-      sincos(al, &s, &c);
-      phase[b * n_tab + e] = unit_round<R>(c, s);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < per; j += gridDim.x * blockDim.x) {
+      if (j < n_gates) {
+        const double al = theta[b * P + gate_param[j]] * gate_t[(int64_t)inst * n_gates + j];
+        double s, c;
+        sincos(al, &s, &c);
+        coef[b * n_gates + j] = unit_round<R>(c, s);
+      } else {
+        const int e = tab_live[j - n_gates];
+        const int pp = tab_param[e];
+        const double th = pp >= 0 ? theta[b * P + pp] : 0.0;
+        const double al = -th * tab_val[(int64_t)inst * n_tab + e];
+        double s, c;
+        sincos(al, &s, &c);
+        phase[b * n_tab + e] = unit_round<R>(c, s);
+      }
     }
   }
 }
@@ -158,20 +162,21 @@ cudaError_t launch_sweep(int dtype, const SweepDev& sw, const KernelArgs& a, int
 cudaError_t launch_coef(int dtype, const double* theta, int P, const int32_t* gate_param,
                         const double* gate_t, int n_gates, void* coef,
                         const int32_t* tab_param, const double* tab_val, int n_tab,
-                        int /*n_inst_tab*/, void* phase_tabs, int64_t batch, int n_inst,
-                        cudaStream_t st) {
-  const int64_t total = ((int64_t)n_gates + n_tab) * batch;
-  if (total == 0) return cudaSuccess;
-  int grid = (int)((total + 255) / 256);
-  if (grid > 4096) grid = 4096;
+                        const int32_t* tab_live, int n_live, void* phase_tabs, int64_t batch,
+                        int n_inst, cudaStream_t st) {
+  const int per = n_gates + n_live;
+  if (per == 0 || batch <= 0) return cudaSuccess;
+  const int gx = std::min((per + 255) / 256, 64);
+  const int gy = (int)std::min<int64_t>(batch, std::max(1, 8192 / gx));
+  const dim3 grid(gx, gy);
   if (dtype == 0)
     coef_kernel<float><<<grid, 256, 0, st>>>(theta, P, gate_param, gate_t, n_gates,
-                                             (float2*)coef, tab_param, tab_val, n_tab,
-                                             (float2*)phase_tabs, batch, n_inst);
+                                             (float2*)coef, tab_param, tab_val, n_tab, tab_live,
+                                             n_live, (float2*)phase_tabs, batch, n_inst);
   else
     coef_kernel<double><<<grid, 256, 0, st>>>(theta, P, gate_param, gate_t, n_gates,
-                                              (double2*)coef, tab_param, tab_val, n_tab,
-                                              (double2*)phase_tabs, batch, n_inst);
+                                              (double2*)coef, tab_param, tab_val, n_tab, tab_live,
+                                              n_live, (double2*)phase_tabs, batch, n_inst);
   return cudaGetLastError();
 }
 
