@@ -662,7 +662,7 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
     const SweepDev& sw = pl->sweeps[i];
     const int nv = pl->nvec[i];
     const int nph = sw.phase_end - sw.phase_begin;
-    const size_t smem = sweep_smem_bytes(dtype, nv, sw.k, n_slots, nph, sw.op_end - sw.op_begin);
+    const size_t smem = sweep_smem_bytes(dtype, nv, sw.k, n_slots, nph, sw.op_end - sw.op_begin, 32 << sw.w);
     if ((int)smem > optin) return fail(HUB_EUNSUPPORTED, "tile does not fit in shared memory");
     HUB_CUDA(sweep_set_smem(dtype, nv, sw.r, 32 << sw.w, smem), "cudaFuncSetAttribute");
     const int threads = 32 << sw.w;

@@ -223,10 +223,11 @@ __host__ __device__ inline int pair_index(int a, int b) { return b * (b - 1) / 2
 // when the sweep has a single phase), the CTA accumulators, copies of the
 // sweep's phases, and its resolved operations plus one spare record (the
 // kernel loads one operation ahead).
-inline size_t sweep_smem_bytes(int dtype, int nv, int k, int n_slots, int n_phases, int n_ops) {
+inline size_t sweep_smem_bytes(int dtype, int nv, int k, int n_slots, int n_phases, int n_ops, int threads) {
   const size_t amp = dtype == 0 ? 8 : 16;
   const int nbuf = n_phases > 1 ? nv : 0;
-  size_t s = (size_t)nbuf * (amp << k) + 8 * (size_t)n_slots + sizeof(PhaseDev) * (size_t)n_phases;
+  const size_t rows = dtype == 0 ? (size_t)threads / 32 : 1;   // accumulator rows (8-byte entries)
+  size_t s = (size_t)nbuf * (amp << k) + 8 * rows * (size_t)n_slots + sizeof(PhaseDev) * (size_t)n_phases;
   s = (s + 15) & ~(size_t)15;                  // operations are read as 16-byte words
   return s + 16 * (size_t)res_words(dtype) * (size_t)(n_ops + 1);
 }

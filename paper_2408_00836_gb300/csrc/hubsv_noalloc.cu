@@ -192,7 +192,7 @@ extern "C" hub_status energy_noalloc(ans_t a, const double* theta, void* psi, do
     const SweepDev& sw = pl->sweeps[i];
     const int nv = pl->nvec[i];
     const int nph = sw.phase_end - sw.phase_begin;
-    const size_t smem = sweep_smem_bytes(dtype, nv, sw.k, n_slots, nph, sw.op_end - sw.op_begin);
+    const size_t smem = sweep_smem_bytes(dtype, nv, sw.k, n_slots, nph, sw.op_end - sw.op_begin, 32 << sw.w);
     if ((int)smem > optin) return fail(HUB_EUNSUPPORTED, "energy_noalloc: tile does not fit in shared memory");
     HUB_CUDA(sweep_set_smem(dtype, nv, sw.r, 32 << sw.w, smem), "energy_noalloc: cudaFuncSetAttribute");
     const int threads = 32 << sw.w;

@@ -149,25 +149,9 @@ size_t small_smem_bytes(int dtype, int cup, int cdn, int n_pairs, int n_slots, i
 
 namespace {
 
-// FP64 arithmetic is a small fraction of FP32 throughput on this part, so
-// the complex64 kernel reduces in FP32 and keeps its running totals as
-// unevaluated float pairs (hi + lo) updated with Knuth's TwoSum, which is
-// exact: the totals carry about 48 bits although no FP64 instruction runs
-// per operation.  The complex128 kernel reduces in FP64.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-// (h, l) += v, renormalised so that |l| <= ulp(h) / 2.
-__device__ __forceinline__ void ff_add(float& h, float& l, float v) {
-  float s, e;
-  two_sum(h, v, s, e);
-  e += l;
-  h = s + e;
-  l = e - (h - s);
-}
+// The complex64 kernel reduces in FP32 and keeps its running totals as
+// float pairs (two_sum, ff_add, warp_sum_f from the sweep kernel's header);
+// the complex128 kernel reduces in FP64.
 
 // Sum of float pairs over the warp, into lane 0's (h, l).
 __device__ __forceinline__ void warp_sum_ff(float& h, float& l) {
@@ -180,12 +164,6 @@ __device__ __forceinline__ void warp_sum_ff(float& h, float& l) {
     h = s + e;
     l = e - (h - s);
   }
-}
-
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
 }
 
 // Running totals of one thread (R = float: float pairs; double: FP64).
@@ -226,8 +204,6 @@ __device__ __forceinline__ void row_add_tot(float2* acc, int n_slots, int slot, 
 __device__ __forceinline__ void row_add_tot(double* acc, int n_slots, int slot, Tot<double> t) {
   row_add(acc, n_slots, slot, t.v);
 }
-__device__ __forceinline__ double row_value(const float2& v) { return (double)v.x + (double)v.y; }
-__device__ __forceinline__ double row_value(double v) { return v; }
 
 // n / d for the n < 2^32 / d met here, with m = ceil(2^32 / d) from
 // small_magic (0 for d = 1): one high multiply instead of a division.

@@ -38,6 +38,8 @@
 // are reduced per warp in FP64 and summed per CTA in shared memory; each CTA
 // adds its totals to the global FP64 accumulators once per batch element.
 #pragma once
+#include <type_traits>
+
 #include "hubsv_internal.h"
 
 namespace hubsv {
@@ -110,9 +112,48 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Add a per-thread partial to acc[slot] (shared).  Called uniformly by the
-// whole CTA.
-__device__ __forceinline__ void cta_add(double* acc, int slot, double v) {
+// FP64 arithmetic is a small fraction of FP32 throughput on this part, so
+// the complex64 kernels reduce in FP32 and keep their running sums as
+// unevaluated float pairs (hi + lo) updated with Knuth's TwoSum, which is
+// exact: the sums carry about 48 bits although no FP64 instruction runs per
+// tile.  The complex128 kernels reduce in FP64.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (h, l) += v, renormalised so that |l| <= ulp(h) / 2.
+__device__ __forceinline__ void ff_add(float& h, float& l, float v) {
+  float s, e;
+  two_sum(h, v, s, e);
+  e += l;
+  h = s + e;
+  l = e - (h - s);
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double row_value(const float2& v) { return (double)v.x + (double)v.y; }
+__device__ __forceinline__ double row_value(double v) { return v; }
+
+// Shared accumulators of a CTA.  complex64: one row of float pairs per warp
+// (row w, slot i at acc[w * n_slots + i]), written by lane 0 of warp w only,
+// so no atomics; complex128: one row of doubles, FP64 atomics.  Both are
+// summed over rows in FP64 when they are flushed to global memory.
+// cta_add adds a per-thread partial to slot; called uniformly by the CTA.
+__device__ __forceinline__ void cta_add(float2* acc, int n_slots, int slot, float v) {
+  v = warp_sum_f(v);
+  if ((threadIdx.x & 31) == 0) {
+    float2& t = acc[(threadIdx.x >> 5) * n_slots + slot];
+    ff_add(t.x, t.y, v);
+  }
+}
+__device__ __forceinline__ void cta_add(double* acc, int /*n_slots*/, int slot, double v) {
   v = warp_sum(v);
   if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(&acc[slot], v);
 }
@@ -425,8 +466,10 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
   const int nbuf = nph > 1 ? NV : 0;
   T2* xb = reinterpret_cast<T2*>(smem_raw);
   T2* xl = xb + tsize;
-  double* acc = reinterpret_cast<double*>(smem_raw + (size_t)nbuf * tsize * sizeof(T2));
-  PhaseDev* phs = reinterpret_cast<PhaseDev*>(acc + a.n_slots);
+  using AccT = typename std::conditional<DT == 0, float2, double>::type;
+  const int n_rows = DT == 0 ? (int)(blockDim.x >> 5) : 1;
+  AccT* acc = reinterpret_cast<AccT*>(smem_raw + (size_t)nbuf * tsize * sizeof(T2));
+  PhaseDev* phs = reinterpret_cast<PhaseDev*>(acc + n_rows * a.n_slots);
   const size_t op_off = ((size_t)(reinterpret_cast<unsigned char*>(phs + nph) - smem_raw) + 15) & ~(size_t)15;
   uint4* sres = reinterpret_cast<uint4*>(smem_raw + op_off);   // indexed by local op index
   __shared__ int8_t s_nbits[kMaxQubits];
@@ -452,7 +495,7 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
     for (int i = 0; i < kMaxTileBits; ++i) s_tbits[i] = sw.tbits[i];
     s_meas = 0;
   }
-  for (int i = tid; i < a.n_slots; i += nth) acc[i] = 0.0;
+  for (int i = tid; i < n_rows * a.n_slots; i += nth) acc[i] = AccT{};
   {
     const int* src = reinterpret_cast<const int*>(a.phases + sw.phase_begin);
     int* dst = reinterpret_cast<int*>(phs);
@@ -521,9 +564,12 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
       if (cur_b >= 0) {
         __syncthreads();
         for (int i = tid; i < a.n_slots; i += nth) {
-          const double x = acc[i];
+          double x = 0.0;
+          for (int w = 0; w < n_rows; ++w) {
+            x += row_value(acc[w * a.n_slots + i]);
+            acc[w * a.n_slots + i] = AccT{};
+          }
           if (x != 0.0) atomicAdd(&a.acc[(size_t)cur_b * a.n_slots + i], x);
-          acc[i] = 0.0;
         }
         __syncthreads();
       }
@@ -606,7 +652,7 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
         if (aux & RA_GRAD) {
           const int slot = (int)(w0.x >> 16);
           if (slot != rslot) {
-            if (rslot >= 0) cta_add(acc, rslot, (double)racc);
+            if (rslot >= 0) cta_add(acc, a.n_slots, rslot, racc);
             racc = 0;
             rslot = slot;
           }
@@ -763,10 +809,10 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
 #undef HUB_M2
       }
     }
-    if (rslot >= 0) cta_add(acc, rslot, (double)racc);
+    if (rslot >= 0) cta_add(acc, a.n_slots, rslot, racc);
     if (s_meas) {
-      cta_add(acc, a.slot_E, (double)eacc);
-      cta_add(acc, a.slot_N, (double)nacc);
+      cta_add(acc, a.n_slots, a.slot_E, eacc);
+      cta_add(acc, a.n_slots, a.slot_N, nacc);
     }
 
     // ---- store from registers (the last phase has the run bits on lanes) ----
@@ -789,7 +835,8 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
   __syncthreads();
   if (cur_b >= 0) {
     for (int i = tid; i < a.n_slots; i += nth) {
-      const double x = acc[i];
+      double x = 0.0;
+      for (int w = 0; w < n_rows; ++w) x += row_value(acc[w * a.n_slots + i]);
       if (x != 0.0) atomicAdd(&a.acc[(size_t)cur_b * a.n_slots + i], x);
     }
   }
