@@ -88,7 +88,7 @@ typedef enum { HUB_PREP_SLATER = 0, HUB_PREP_NEEL = 1 } hub_prep;
                                     and is generated inside the first sweep   */
 #define HUB_FLAG_KEEP_STATE 2u   /* energy: leave the final state psi_K in psi */
 #define HUB_FLAG_SWEEPS     4u   /* run as HBM sweeps even where the on-chip
-                                    path applies (see energy_grad)             */
+                                    engine applies (see energy_grad)           */
 
 /* Lattice: sites 0..n_sites-1, undirected bonds (pairs of sites).  mode_up /
  * mode_dn map a site to its two qubits; both NULL = blocked order (up i -> i,
@@ -175,7 +175,15 @@ HUB_API hub_status energy(ans_t ans, const double* theta, void* psi, double* E,
  * size as psi.  ckpt: NULL, or device workspace of the same size as psi for
  * one mid-circuit checkpoint of psi (bounds the rounding drift of the
  * backward un-computation).  grad: device double [batch][P], overwritten.
- * psi and lam are clobbered.                                                */
+ * psi and lam are clobbered.
+ *
+ * Engines (energy and energy_grad alike): with HUB_FLAG_PREP_FUSED, without
+ * HUB_FLAG_KEEP_STATE or HUB_FLAG_SWEEPS, and when the (N_up, N_dn) sector's
+ * C(L, N_up) * C(L, N_dn) amplitudes of psi and lam fit in one CTA's shared
+ * memory, each batch element runs on chip in one CTA and psi, lam and ckpt
+ * are not touched (their contents are then unspecified, as always); results
+ * agree with the sweep engine to the rounding of the dtype.  Otherwise the
+ * call runs as HBM sweeps over psi (and lam, ckpt).                         */
 HUB_API hub_status energy_grad(ans_t ans, const double* theta, void* psi, void* lam,
                        void* ckpt, double* E, double* grad, int32_t dtype,
                        int64_t batch, uint32_t flags, hub_stream_t stream);
