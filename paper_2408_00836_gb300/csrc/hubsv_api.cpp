@@ -278,6 +278,20 @@ int add_diag_op(hub_ansatz* a, const std::vector<std::vector<double>>& xcoef,
     d.vb_up[b] = a->models[0]->up[vbonds[b].first];
     d.vb_up2[b] = a->models[0]->up[vbonds[b].second];
   }
+  d.n_vs = 0;
+  for (int b = 0; b < d.n_vb && d.n_vs >= 0; ++b) {
+    const int u1 = std::min(d.vb_up[b], d.vb_up2[b]), u2 = std::max(d.vb_up[b], d.vb_up2[b]);
+    int g = 0;
+    while (g < d.n_vs && d.vs_shift[g] != u2 - u1) ++g;
+    if (g == d.n_vs) {
+      if (g == 32) { d.n_vs = -1; break; }
+      d.vs_shift[g] = u2 - u1;
+      d.vs_mask[g] = 0u;
+      ++d.n_vs;
+    }
+    if (u1 == u2 || (d.vs_mask[g] >> u1 & 1u)) d.n_vs = -1;   // not a plain bond list
+    else d.vs_mask[g] |= 1u << u1;
+  }
   d.param = param;
   d.real_off = a->real_stride;
   const int real_len = 2048 + d.n_vb;
@@ -664,9 +678,9 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
     const int nph = sw.phase_end - sw.phase_begin;
     const size_t smem = sweep_smem_bytes(dtype, nv, sw.k, n_slots, nph, sw.op_end - sw.op_begin, 32 << sw.w);
     if ((int)smem > optin) return fail(HUB_EUNSUPPORTED, "tile does not fit in shared memory");
-    HUB_CUDA(sweep_set_smem(dtype, nv, sw.r, 32 << sw.w, smem), "cudaFuncSetAttribute");
+    HUB_CUDA(sweep_set_smem(dtype, nv, sw.r, 32 << sw.w, (sw.flags & SW_VPOP) != 0, smem), "cudaFuncSetAttribute");
     const int threads = 32 << sw.w;
-    const int regs = std::max(1, sweep_regs(dtype, nv, sw.r, 32 << sw.w));
+    const int regs = std::max(1, sweep_regs(dtype, nv, sw.r, 32 << sw.w, (sw.flags & SW_VPOP) != 0));
     int per_sm = (int)((size_t)(228 * 1024) / (smem + 1024));
     per_sm = std::min(per_sm, 2048 / threads);
     per_sm = std::min(per_sm, 65536 / (regs * threads));

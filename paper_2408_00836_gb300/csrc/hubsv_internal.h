@@ -86,6 +86,14 @@ struct DiagOpDev {
   int32_t param;                 // theta column for phases; -1 for H's diagonal
   int32_t vb_up[64];             // up-mode of bond end i
   int32_t vb_up2[64];            // up-mode of bond end j
+  // v_uniform: the bonds grouped by the distance of their up-modes, for
+  // K = sum_g sum_{P,Q in (O1,O2)} popc(mask_g & P & (Q >> shift_g)), with
+  // O1 / O2 the sites holding at least one / two electrons (at their
+  // up-mode positions): n_i n_j = (O1_i + O2_i)(O1_j + O2_j).  n_vs = -1:
+  // use the bond list (a bond given twice).
+  int32_t n_vs;
+  int32_t vs_shift[32];
+  uint32_t vs_mask[32];          // bit u: a bond from up-mode u to u + shift
 };
 // Real table layout at real_off: [4][256] X, [4][256] Y, [n_vb] v_b.
 // Phase table layout at phase_off: [4][256] X, [4][256] Y, then either
@@ -100,6 +108,8 @@ enum SweepFlag : uint32_t {
   SW_WRITE_LAM = 32u,
   SW_CKPT_WRITE = 64u, // also store psi to the checkpoint buffer
   SW_CKPT_READ = 128u, // read psi from the checkpoint buffer
+  SW_VPOP = 256u,      // a diagonal operation has uniform V terms: the kernel
+                       // variant that counts them with popcounts is used
 };
 
 struct SweepDev {
@@ -255,8 +265,8 @@ cudaError_t launch_zero(double* p, int64_t n, cudaStream_t st);
 cudaError_t launch_finalize(const double* acc, int n_slots, int P, int slot_E,
                             double* E, double* grad, int64_t batch, cudaStream_t st);
 int sweep_max_smem_optin();
-cudaError_t sweep_set_smem(int dtype, int nv, int r, int threads, size_t smem);
-int sweep_regs(int dtype, int nv, int r, int threads);
+cudaError_t sweep_set_smem(int dtype, int nv, int r, int threads, bool vp, size_t smem);
+int sweep_regs(int dtype, int nv, int r, int threads, bool vp);
 int device_sm_count();
 // Register bits the kernels are compiled for: r in [1, max_r(dtype, nv)].
 inline int max_reg_bits(int dtype, int nv) {

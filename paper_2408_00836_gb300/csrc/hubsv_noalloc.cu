@@ -194,9 +194,9 @@ extern "C" hub_status energy_noalloc(ans_t a, const double* theta, void* psi, do
     const int nph = sw.phase_end - sw.phase_begin;
     const size_t smem = sweep_smem_bytes(dtype, nv, sw.k, n_slots, nph, sw.op_end - sw.op_begin, 32 << sw.w);
     if ((int)smem > optin) return fail(HUB_EUNSUPPORTED, "energy_noalloc: tile does not fit in shared memory");
-    HUB_CUDA(sweep_set_smem(dtype, nv, sw.r, 32 << sw.w, smem), "energy_noalloc: cudaFuncSetAttribute");
+    HUB_CUDA(sweep_set_smem(dtype, nv, sw.r, 32 << sw.w, (sw.flags & SW_VPOP) != 0, smem), "energy_noalloc: cudaFuncSetAttribute");
     const int threads = 32 << sw.w;
-    const int regs = std::max(1, sweep_regs(dtype, nv, sw.r, 32 << sw.w));
+    const int regs = std::max(1, sweep_regs(dtype, nv, sw.r, 32 << sw.w, (sw.flags & SW_VPOP) != 0));
     int per_sm = (int)((size_t)(228 * 1024) / (smem + 1024));
     per_sm = std::min(per_sm, 2048 / threads);
     per_sm = std::min(per_sm, 65536 / (regs * threads));

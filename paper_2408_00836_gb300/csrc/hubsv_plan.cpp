@@ -571,6 +571,14 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
     }
     sw.phase_end = (int)pl->hphases.size();
     sw.op_end = (int)pl->hops.size();
+    for (int oi = sw.op_begin; oi < sw.op_end; ++oi) {
+      const OpDev& d = pl->hops[oi];
+      const bool diag = d.kind == OP_DIAG || d.kind == OP_MEAS_DIAG || d.kind == OP_LAM_DIAG ||
+                        d.kind == OP_GRAD_DIAG || d.kind == OP_GRADINV_DIAG;
+      if (!diag) continue;
+      const DiagOpDev& g = a->diag_ops[d.idx];
+      if (g.n_vb > 0 && g.v_uniform && g.n_vs >= 0) sw.flags |= SW_VPOP;
+    }
     bytes += amp * (double)tiles_per_state * (double)(1ull << k) *
              (((f & SW_READ_PSI) ? 1 : 0) + ((f & SW_WRITE_PSI) ? 1 : 0) +
               ((f & SW_READ_LAM) ? 1 : 0) + ((f & SW_WRITE_LAM) ? 1 : 0) +

@@ -169,9 +169,34 @@ __device__ __forceinline__ uint32_t comb(const uint32_t (&m)[RB], int e) {
   return v;
 }
 
+// K = sum over the bonds of n_i n_j at x, for uniform V (see DiagOpDev).
+__device__ __forceinline__ int v_count(const DiagOpDev& d, uint32_t x, int s, uint32_t upmask) {
+  int K = 0;
+  if (d.n_vs >= 0) {
+    const uint32_t A = x & upmask, B = (x >> s) & upmask;
+    const uint32_t O1 = A | B, O2 = A & B;
+    for (int g = 0; g < d.n_vs; ++g) {
+      const int sh = d.vs_shift[g];
+      const uint32_t m = d.vs_mask[g];
+      const uint32_t p1 = O1 & m, p2 = O2 & m, q1 = O1 >> sh, q2 = O2 >> sh;
+      K += __popc(p1 & q1) + __popc(p1 & q2) + __popc(p2 & q1) + __popc(p2 & q2);
+    }
+  } else {
+    for (int b = 0; b < d.n_vb; ++b) {
+      const int u1 = d.vb_up[b], u2 = d.vb_up2[b];
+      const int ni = (int)((x >> u1) & 1u) + (int)((x >> (u1 + s)) & 1u);
+      const int nj = (int)((x >> u2) & 1u) + (int)((x >> (u2 + s)) & 1u);
+      K += ni * nj;
+    }
+  }
+  return K;
+}
+
 // Real value of a diagonal operator at x (see DiagOpDev), in the working
 // precision R (tables stored in R).
-template <typename R>
+// VP: uniform V terms through v_count's popcounts (kernel variants for
+// sweeps flagged SW_VPOP); otherwise bond by bond.
+template <typename R, bool VP = false>
 __device__ __forceinline__ R diag_real(const DiagOpDev& d, const R* tab, uint32_t x, int s,
                                       uint32_t upmask) {
   R v = 0;
@@ -179,17 +204,21 @@ __device__ __forceinline__ R diag_real(const DiagOpDev& d, const R* tab, uint32_
   const uint32_t y = x & (x >> s) & upmask;
   for (int i = 0; i < d.has_y; ++i) v += tab[1024 + i * 256 + ((y >> (8 * i)) & 255u)];
   const R* vb = tab + 2048;
-  for (int b = 0; b < d.n_vb; ++b) {
-    const int u1 = d.vb_up[b], u2 = d.vb_up2[b];
-    const int ni = (int)((x >> u1) & 1u) + (int)((x >> (u1 + s)) & 1u);
-    const int nj = (int)((x >> u2) & 1u) + (int)((x >> (u2 + s)) & 1u);
-    v += vb[b] * (R)(ni * nj);
+  if (VP && d.n_vb > 0 && d.v_uniform) {
+    v += vb[0] * (R)v_count(d, x, s, upmask);
+  } else {
+    for (int b = 0; b < d.n_vb; ++b) {
+      const int u1 = d.vb_up[b], u2 = d.vb_up2[b];
+      const int ni = (int)((x >> u1) & 1u) + (int)((x >> (u1 + s)) & 1u);
+      const int nj = (int)((x >> u2) & 1u) + (int)((x >> (u2 + s)) & 1u);
+      v += vb[b] * (R)(ni * nj);
+    }
   }
   return v;
 }
 
 // Phase exp(-i theta d(x)) from the per-batch-element phase tables.
-template <typename T2>
+template <typename T2, bool VP = false>
 __device__ __forceinline__ T2 diag_phase(const DiagOpDev& d, const T2* tab, uint32_t x, int s,
                                          uint32_t upmask) {
   T2 ph; ph.x = 1; ph.y = 0;
@@ -198,7 +227,9 @@ __device__ __forceinline__ T2 diag_phase(const DiagOpDev& d, const T2* tab, uint
   for (int i = 0; i < d.has_y; ++i) ph = cmul(ph, tab[1024 + i * 256 + ((y >> (8 * i)) & 255u)]);
   if (d.n_vb > 0) {
     const T2* vt = tab + 2048;
-    if (d.v_uniform) {
+    if (VP && d.v_uniform) {
+      ph = cmul(ph, vt[v_count(d, x, s, upmask)]);
+    } else if (d.v_uniform) {
       int K = 0;
       for (int b = 0; b < d.n_vb; ++b) {
         const int u1 = d.vb_up[b], u2 = d.vb_up2[b];
@@ -453,7 +484,7 @@ __device__ __forceinline__ double2 ldg_run(const double2* p) {
 // thread); MINB = 4: at most 256 threads and four CTAs per SM (64
 // registers), used for psi-only c64 sweeps of 256-thread tiles, where the
 // extra CTAs hide the tile loads.
-template <typename R, int NV, int RB, int MINB = 1>
+template <typename R, int NV, int RB, int MINB = 1, bool VP = false>
 __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB)
 sweep_kernel(const SweepDev sw, const KernelArgs a) {
   using T2 = typename CT<R>::T2;
@@ -716,7 +747,7 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
             const DiagOpDev& d = a.diag_ops[w1.z];
 #pragma unroll
             for (int e = 0; e < NE; ++e) {
-              T2 p = diag_phase<T2>(d, ptab, xb0 | comb<RB>(so, e), a.s, upm);
+              T2 p = diag_phase<T2, VP>(d, ptab, xb0 | comb<RB>(so, e), a.s, upm);
               if (inv) p.y = -p.y;
               v[e] = cmul(v[e], p);
               if (dol) l[e] = cmul(l[e], p);
@@ -748,8 +779,8 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
                     p = cmul(p, ptab[1280 + ((y >> 8) & 255u)]);
                   }
                 } else {
-                  dv = diag_real<R>(*dp, rtab, x, a.s, upm);
-                  p = diag_phase<T2>(*dp, ptab, x, a.s, upm);
+                  dv = diag_real<R, VP>(*dp, rtab, x, a.s, upm);
+                  p = diag_phase<T2, VP>(*dp, ptab, x, a.s, upm);
                 }
                 pe += dv * (l[e].x * v[e].y - l[e].y * v[e].x);
                 p.y = -p.y;
@@ -780,7 +811,7 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
                 dv = rtab[1024 + (y & 255u)];
                 if (ny == 2) dv += rtab[1280 + ((y >> 8) & 255u)];
               } else {
-                dv = diag_real<R>(*dp, rtab, x, a.s, upm);
+                dv = diag_real<R, VP>(*dp, rtab, x, a.s, upm);
               }
               const T2 u = v[e];
               if (code == RC_GRAD_DIAG) {

@@ -104,12 +104,19 @@ const void* sweep_ptr_f2(int r);
 const void* sweep_ptr_d1(int r);
 const void* sweep_ptr_d2(int r);
 const void* sweep_ptr_f1_narrow(int r);
+const void* sweep_ptr_fv(int nv, int r, int threads);
+const void* sweep_ptr_dv(int nv, int r, int threads);
 
 namespace {
 int g_sm_count = 0;
 
-const void* kernel_for(int dtype, int nv, int r, int threads) {
+// vp: the sweep has uniform V terms (SW_VPOP); the popcount variant is
+// taken where one is compiled, else the plain kernel (bond by bond).
+const void* kernel_for(int dtype, int nv, int r, int threads, bool vp) {
   if (r < 1 || r > max_reg_bits(dtype, nv)) return nullptr;
+  if (vp) {
+    if (const void* f = dtype == 0 ? sweep_ptr_fv(nv, r, threads) : sweep_ptr_dv(nv, r, threads)) return f;
+  }
   if (dtype == 0 && nv == 1 && threads <= 256) {
     if (const void* f = sweep_ptr_f1_narrow(r)) return f;
   }
@@ -134,14 +141,14 @@ int sweep_max_smem_optin() {
   return v;
 }
 
-cudaError_t sweep_set_smem(int dtype, int nv, int r, int threads, size_t smem) {
-  const void* f = kernel_for(dtype, nv, r, threads);
+cudaError_t sweep_set_smem(int dtype, int nv, int r, int threads, bool vp, size_t smem) {
+  const void* f = kernel_for(dtype, nv, r, threads, vp);
   if (!f) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-int sweep_regs(int dtype, int nv, int r, int threads) {
-  const void* f = kernel_for(dtype, nv, r, threads);
+int sweep_regs(int dtype, int nv, int r, int threads, bool vp) {
+  const void* f = kernel_for(dtype, nv, r, threads, vp);
   cudaFuncAttributes at;
   if (!f || cudaFuncGetAttributes(&at, f) != cudaSuccess) return 0;
   return at.numRegs;
@@ -151,7 +158,7 @@ cudaError_t launch_sweep(int dtype, const SweepDev& sw, const KernelArgs& a, int
                          cudaStream_t st) {
   const int nv = (sw.flags & SW_HAS_LAM) ? 2 : 1;
   const int threads = 32 << sw.w;
-  const void* f = kernel_for(dtype, nv, sw.r, threads);
+  const void* f = kernel_for(dtype, nv, sw.r, threads, (sw.flags & SW_VPOP) != 0);
   if (!f) return cudaErrorInvalidValue;
   SweepDev swc = sw;
   KernelArgs ac = a;

@@ -105,6 +105,25 @@ def test_disordered_extended_2x3_all_group_kinds(modes, dtype, sweeps):
 
 
 @pytest.mark.parametrize("sweeps", [False, True])
+@pytest.mark.parametrize("modes", ["blocked", "interleaved"])
+@pytest.mark.parametrize("dtype", [H.C128, H.C64])
+def test_bond_dependent_V_2x3(modes, dtype, sweeps):
+    """V_ij different on every bond (the bond-by-bond path; the uniform-V
+    cases above take the popcount count of n_i n_j)."""
+    t, U, Vm = _disordered_2x3()
+    rng = np.random.default_rng(78)
+    bonds, _ = H.square_lattice(2, 3)
+    for (i, j) in bonds:
+        Vm[i, j] = Vm[j, i] = 0.5 + 0.3 * rng.standard_normal()
+    prob = Problem(2, 3, modes=modes, t=t, U=U, V=Vm, layers=2, classes=("U", "V", "h1", "v1", "h2"))
+    theta = np.random.default_rng(8).uniform(-math.pi, math.pi, prob.P)
+    Eo, go = prob.oracle_energy_grad(theta)
+    E, g, _ = _run(prob, theta, dtype, sweeps=sweeps)
+    assert abs(E[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
+    assert np.max(np.abs(g[0] - go)) < TOL[dtype] * max(1.0, np.max(np.abs(go)))
+
+
+@pytest.mark.parametrize("sweeps", [False, True])
 @pytest.mark.parametrize("dtype", [H.C128, H.C64])
 def test_neel_start(dtype, sweeps):
     t, U, Vm = _disordered_2x3()
