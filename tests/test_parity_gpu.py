@@ -123,6 +123,26 @@ def test_bond_dependent_V_2x3(modes, dtype, sweeps):
     assert np.max(np.abs(g[0] - go)) < TOL[dtype] * max(1.0, np.max(np.abs(go)))
 
 
+@pytest.mark.parametrize("fill", [(0, 3), (6, 2), (1, 5), (3, 0), (6, 6)])
+@pytest.mark.parametrize("dtype", [H.C128, H.C64])
+def test_edge_sectors_both_engines(fill, dtype):
+    """Sectors with one pattern for a spin (N = 0 or N = L: no pairs for its
+    hops, a division by one in the on-chip engine), one electron, and the
+    full lattice: both engines against the oracle and each other."""
+    t, U, Vm = _disordered_2x3()
+    n_up, n_dn = fill
+    prob = Problem(2, 3, t=t, U=U, V=Vm, n_up=n_up, n_dn=n_dn, layers=2,
+                   classes=("U", "V", "h1", "v1", "h2"))
+    theta = np.random.default_rng(9).uniform(-math.pi, math.pi, prob.P)
+    Eo, go = prob.oracle_energy_grad(theta)
+    for sweeps in (False, True):
+        E, g, _ = _run(prob, theta, dtype, sweeps=sweeps)
+        assert abs(E[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
+        assert np.max(np.abs(g[0] - go)) < TOL[dtype] * max(1.0, np.max(np.abs(go)))
+    if n_up in (0, 6) and n_dn in (0, 6):   # one basis state: no hopping can act
+        assert np.max(np.abs(go)) < 1e-12
+
+
 @pytest.mark.parametrize("sweeps", [False, True])
 @pytest.mark.parametrize("dtype", [H.C128, H.C64])
 def test_neel_start(dtype, sweeps):
