@@ -69,5 +69,14 @@ class Problem:
         return O.ansatz_state(self.omodels[r], self.basis, self.ogroups, theta, self.psi0(r))
 
 
+def grad_scale(prob, theta, go, r=0):
+    """Scale of a gradient comparison: max(1, |g|_inf, ||H psi||).  The
+    gradient is 2 Im<lam|G|psi> with lam = H psi (Sec. 2.1), so its rounding
+    error in a given precision scales with ||lam||, not with |g|, which can
+    be small through cancellation."""
+    lam_norm = float(np.linalg.norm(prob.Hmat(r) @ prob.oracle_state(theta, r)))
+    return max(1.0, float(np.max(np.abs(go))), lam_norm)
+
+
 def rel_err(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
