@@ -69,13 +69,25 @@ class Problem:
         return O.ansatz_state(self.omodels[r], self.basis, self.ogroups, theta, self.psi0(r))
 
 
-def grad_scale(prob, theta, go, r=0):
-    """Scale of a gradient comparison: max(1, |g|_inf, ||H psi||).  The
-    gradient is 2 Im<lam|G|psi> with lam = H psi (Sec. 2.1), so its rounding
-    error in a given precision scales with ||lam||, not with |g|, which can
-    be small through cancellation."""
-    lam_norm = float(np.linalg.norm(prob.Hmat(r) @ prob.oracle_state(theta, r)))
-    return max(1.0, float(np.max(np.abs(go))), lam_norm)
+def grad_scale(prob, theta, r=0):
+    """Per-parameter scale of a gradient comparison: max(1, S_p) with S_p =
+    sum over the groups of parameter p of 2 ||lam_k|| ||G_k psi_k||, the
+    Cauchy-Schwarz bound of the terms 2 Im<lam_k|G_k|psi_k> that make up g_p
+    (Sec. 2.1).  Rounding in a given precision is relative to the size of
+    these terms, not to |g_p|, which cancellation can make small (on a single
+    basis state g = 0 exactly while each term is of size ||H psi|| ||G psi||)."""
+    om, basis, groups = prob.omodels[r], prob.basis, prob.ogroups
+    psi = prob.oracle_state(theta, r)
+    lam = prob.Hmat(r) @ psi
+    S = np.zeros(len(theta))
+    cache = {}
+    for g in reversed(groups):
+        Gpsi = O.apply_generator(om, basis, g, psi, cache)
+        S[g.param] += 2.0 * float(np.linalg.norm(lam) * np.linalg.norm(Gpsi))
+        th = float(theta[g.param])
+        psi = O.apply_group(om, basis, g, th, psi, cache, inverse=True)
+        lam = O.apply_group(om, basis, g, th, lam, cache, inverse=True)
+    return np.maximum(1.0, S)
 
 
 def rel_err(a, b):
