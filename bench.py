@@ -292,7 +292,9 @@ def run_gpu(args, rank, world, dist):
     # roofline of the dominant kernel
     names = {(1, 0): "sweep_kernel<float,1>", (2, 0): "sweep_kernel<float,2>",
              (1, 1): "sweep_kernel<double,1>", (2, 1): "sweep_kernel<double,2>",
-             (0, 0): "small_kernel<float>", (0, 1): "small_kernel<double>"}
+             (0, 0): "small_kernel<float>", (0, 1): "small_kernel<double>",
+             (3, 0): "rows_kernel<float>", (3, 1): "rows_kernel<double>",
+             (4, 0): "transpose_kernel<float2>", (4, 1): "transpose_kernel<double2>"}
     agg = {}
     for nv, dt, by, ms in recs:
         k = names[(nv, dt)]
@@ -320,7 +322,14 @@ def run_gpu(args, rank, world, dist):
             "launches": dom[1][0], "share": round(dom[1][2] / tot_ms, 4),
             "kernels": {k: {"launches": v[0], "ms": round(v[2], 3), "share": round(v[2] / tot_ms, 4),
                             "GB/s": round(v[1] / (v[2] / 1e3) / 1e9, 1)} for k, v in agg.items()}}
-    hbm_tbs = 0.0 if on_chip else bytes_per_state * batch * args.steps / (ms_total / 1e3) / 1e12
+    rows_engine = any(k.startswith("rows_kernel") for k in agg)
+    rows_bytes = sum(v[1] for v in agg.values()) / args.steps / batch if rows_engine else 0.0
+    if on_chip:
+        hbm_tbs = 0.0
+    elif rows_engine:
+        hbm_tbs = rows_bytes * batch * args.steps / (ms_total / 1e3) / 1e12
+    else:
+        hbm_tbs = bytes_per_state * batch * args.steps / (ms_total / 1e3) / 1e12
 
     # end to end through the C ABI with host buffers
     E_h = torch.empty(batch, dtype=torch.float64).pin_memory()
@@ -340,8 +349,8 @@ def run_gpu(args, rank, world, dist):
     e2e = {"value": round(job_value(world, batch, args.steps, e2e_ms), 4), "unit": "evals/s",
            "h2d_bytes_per_step": int(theta_h.numel() * 8),
            "d2h_bytes_per_step": int((E_h.numel() + g_h.numel()) * 8)}
-    # per step: the recorded main kernels, plus the coefficient and finalize
-    # kernels, plus the accumulator clear of the sweep engine
+    # per step: the recorded kernels, plus the coefficient and finalize
+    # kernels, plus the accumulator clear of the sweep and row engines
     launches = len(recs) + args.steps * (2 if on_chip else 3)
 
     out = {"metric": METRIC, "value": round(value, 4), "unit": "evals/s", "n_gpus": world,
@@ -354,6 +363,8 @@ def run_gpu(args, rank, world, dist):
            "hbm_tbs": round(hbm_tbs, 3),
            "plan": ({"engine": "on-chip (one CTA per state, sector amplitudes in shared memory)",
                      "hbm_bytes_per_eval": 0} if on_chip else
+                    {"engine": "rows (sector amplitudes in HBM, row sweeps and transposes)",
+                     "hbm_bytes_per_eval": rows_bytes} if rows_engine else
                     {"engine": "sweeps", "sweeps": n_sweeps, "bytes_per_eval": bytes_per_state}),
            "energy": E_val, "roofline": roof, "e2e": e2e, "gpu_launches": launches,
            "clocks": ck}

@@ -87,8 +87,10 @@ typedef enum { HUB_PREP_SLATER = 0, HUB_PREP_NEEL = 1 } hub_prep;
                                     one set by the last state_prepare call
                                     and is generated inside the first sweep   */
 #define HUB_FLAG_KEEP_STATE 2u   /* energy: leave the final state psi_K in psi */
-#define HUB_FLAG_SWEEPS     4u   /* run as HBM sweeps even where the on-chip
-                                    engine applies (see energy_grad)           */
+#define HUB_FLAG_SWEEPS     4u   /* run as HBM sweeps of the dense vector even
+                                    where another engine applies (energy_grad) */
+#define HUB_FLAG_ROWS       8u   /* skip the on-chip engine: run on the row
+                                    engine where it applies (energy_grad)      */
 
 /* Lattice: sites 0..n_sites-1, undirected bonds (pairs of sites).  mode_up /
  * mode_dn map a site to its two qubits; both NULL = blocked order (up i -> i,
@@ -217,7 +219,9 @@ HUB_API hub_status hub_apply_h(ans_t ans, const void* psi, void* lam, int32_t dt
 
 /* Plan statistics for the last-planned configuration of a call kind (0 =
  * energy, 1 = energy_grad): number of sweeps and HBM bytes moved per batch
- * element (reads + writes of amplitude vectors).                            */
+ * element (reads + writes of amplitude vectors).  With HUB_FLAG_ROWS in
+ * flags: the row engine's schedule instead (n_sweeps = its row-sweep and
+ * transpose launches), whether or not a call would run on it.              */
 HUB_API hub_status ans_plan_stats(ans_t ans, int32_t which, int32_t dtype,
                           uint32_t flags, int32_t* n_sweeps,
                           double* bytes_per_state);

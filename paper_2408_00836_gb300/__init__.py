@@ -30,6 +30,7 @@ PREP_SLATER, PREP_NEEL = 0, 1
 FLAG_PREP_FUSED = 1
 FLAG_KEEP_STATE = 2
 FLAG_SWEEPS = 4
+FLAG_ROWS = 8
 CLASS_IDS = {"h1": 0, "h2": 1, "v1": 2, "v2": 3, "even": 0, "odd": 1}
 
 
@@ -197,21 +198,22 @@ class Ansatz:
         del pa, na
 
     def energy(self, theta, psi, E, dtype=C64, batch: int = 1, fused: bool = True,
-               keep_state: bool = False, sweeps: bool = False, stream=None):
+               keep_state: bool = False, sweeps: bool = False, rows: bool = False, stream=None):
         flags = ((FLAG_PREP_FUSED if fused else 0) | (FLAG_KEEP_STATE if keep_state else 0)
-                 | (FLAG_SWEEPS if sweeps else 0))
+                 | (FLAG_SWEEPS if sweeps else 0) | (FLAG_ROWS if rows else 0))
         check(lib().energy(self._h, _ptr(theta, 8 * batch * self.P, "theta"),
                            _ptr(psi, batch * self.amp_bytes(dtype), "psi"), _ptr(E, 8 * batch, "E"),
                            dtype, batch, flags, _stream(stream)))
         return E
 
     def energy_grad(self, theta, psi, lam, E, grad, ckpt=None, dtype=C64, batch: int = 1,
-                    fused: bool = True, sweeps: bool = False, stream=None):
+                    fused: bool = True, sweeps: bool = False, rows: bool = False, stream=None):
         nb = batch * self.amp_bytes(dtype)
         check(lib().energy_grad(self._h, _ptr(theta, 8 * batch * self.P, "theta"), _ptr(psi, nb, "psi"),
                                 _ptr(lam, nb, "lam"), _ptr(ckpt, nb, "ckpt"), _ptr(E, 8 * batch, "E"),
                                 _ptr(grad, 8 * batch * self.P, "grad"), dtype, batch,
-                                (FLAG_PREP_FUSED if fused else 0) | (FLAG_SWEEPS if sweeps else 0),
+                                (FLAG_PREP_FUSED if fused else 0) | (FLAG_SWEEPS if sweeps else 0)
+                                | (FLAG_ROWS if rows else 0),
                                 _stream(stream)))
         return E, grad
 
@@ -221,11 +223,13 @@ class Ansatz:
                                 _stream(stream)))
         return lam
 
-    def plan_stats(self, which: int, dtype=C64, fused: bool = True):
+    def plan_stats(self, which: int, dtype=C64, fused: bool = True, rows: bool = False):
+        """(sweeps, HBM bytes per state) of the dense sweep plan, or with
+        rows=True (launches, HBM bytes per state) of the row engine."""
         ns = ctypes.c_int32(0)
         by = ctypes.c_double(0.0)
-        check(lib().ans_plan_stats(self._h, which, dtype, FLAG_PREP_FUSED if fused else 0,
-                                   ctypes.byref(ns), ctypes.byref(by)))
+        flags = (FLAG_PREP_FUSED if fused else 0) | (FLAG_ROWS if rows else 0)
+        check(lib().ans_plan_stats(self._h, which, dtype, flags, ctypes.byref(ns), ctypes.byref(by)))
         return ns.value, by.value
 
     def plan_describe(self, which: int, dtype=C64, flags: int = FLAG_PREP_FUSED):

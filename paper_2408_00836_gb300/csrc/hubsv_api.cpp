@@ -55,6 +55,7 @@ hub_ansatz::~hub_ansatz() {
   prof_clear();
   for (auto& kv : plans) delete kv.second;
   for (auto& kv : small_plans) delete kv.second;
+  for (auto& kv : row_plans) delete kv.second;
 }
 
 // ---------------------------------------------------------------------------
@@ -715,16 +716,21 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
 // The on-chip path (hubsv_small.cu) for a call, or nullptr when the call
 // must run as sweeps: the state is caller-given or must be kept, the caller
 // asked for sweeps, or the sector does not fit in one CTA's shared memory.
-SmallPlan* small_plan_for(hub_ansatz* a, int which, int dtype, uint32_t flags, size_t& smem) {
-  if (!(flags & HUB_FLAG_PREP_FUSED) || (flags & (HUB_FLAG_KEEP_STATE | HUB_FLAG_SWEEPS))) return nullptr;
-  SmallPlan* sp = nullptr;
+// The sector plan of a call kind (patterns, pair lists, operation sequence),
+// shared by the on-chip and row engines; nullptr where none can be made.
+SmallPlan* get_small_plan(hub_ansatz* a, int which) {
   auto it = a->small_plans.find(which);
-  if (it != a->small_plans.end()) {
-    sp = it->second;
-  } else {
-    if (make_small_plan(a, which, sp) != HUB_OK) sp = nullptr;
-    a->small_plans[which] = sp;   // a failed build is remembered as nullptr
-  }
+  if (it != a->small_plans.end()) return it->second;
+  SmallPlan* sp = nullptr;
+  if (make_small_plan(a, which, sp) != HUB_OK) sp = nullptr;
+  a->small_plans[which] = sp;   // a failed build is remembered as nullptr
+  return sp;
+}
+
+SmallPlan* small_plan_for(hub_ansatz* a, int which, int dtype, uint32_t flags, size_t& smem) {
+  if (!(flags & HUB_FLAG_PREP_FUSED) || (flags & (HUB_FLAG_KEEP_STATE | HUB_FLAG_SWEEPS | HUB_FLAG_ROWS)))
+    return nullptr;
+  SmallPlan* sp = get_small_plan(a, which);
   if (!sp) return nullptr;
   // the kernel's multiply-high division is exact for n * d < 2^32
   const uint64_t C = (uint64_t)sp->cup * (uint64_t)sp->cdn;
@@ -820,6 +826,160 @@ hub_status run_small(hub_ansatz* a, SmallPlan* sp, size_t smem, int dtype, const
   return HUB_OK;
 }
 
+// The row engine (hubsv_rows.cu) for a call, or nullptr: the state is
+// caller-given or must be kept, the caller asked for sweeps, a row (with
+// lam, where the call builds it) does not fit in shared memory, or the
+// compressed matrix and its transpose do not fit in the caller's psi buffer.
+RowPlan* row_plan_for(hub_ansatz* a, int which, int dtype, uint32_t flags, SmallPlan*& sp_out) {
+  if (!(flags & HUB_FLAG_PREP_FUSED) || (flags & (HUB_FLAG_KEEP_STATE | HUB_FLAG_SWEEPS))) return nullptr;
+  SmallPlan* sp = get_small_plan(a, which);
+  if (!sp) return nullptr;
+  const uint64_t C = (uint64_t)sp->cup * (uint64_t)sp->cdn;
+  if (2 * C > (1ull << a->n)) return nullptr;
+  RowPlan* rp = nullptr;
+  auto it = a->row_plans.find(which);
+  if (it != a->row_plans.end()) {
+    rp = it->second;
+  } else {
+    if (make_row_plan(a, which, sp, rp) != HUB_OK) rp = nullptr;
+    a->row_plans[which] = rp;
+  }
+  if (!rp) return nullptr;
+  const int optin = sweep_max_smem_optin();
+  for (const RowSegHost& g : rp->segs) {
+    const int nv = (g.flags & RS_HAS_LAM) ? 2 : 1;
+    const int len = g.orient == 0 ? sp->cup : sp->cdn;
+    if ((int)rows_smem_bytes(dtype, nv, len, a->P + 2, a->n_gates, (int)a->hterms.size()) > optin) return nullptr;
+  }
+  sp_out = sp;
+  return rp;
+}
+
+hub_status run_rows(hub_ansatz* a, SmallPlan* sp, RowPlan* rp, int dtype, const double* theta, void* psi,
+                    void* lam, int64_t batch, double* E, double* grad, cudaStream_t st) {
+  const int n_slots = a->P + 2;
+  hub_status s;
+  if ((s = ensure_device(a)) != HUB_OK) return s;
+  if (!sp->uploaded) {
+    if ((s = sp->d_ops.upload(sp->ops, "on-chip ops")) != HUB_OK ||
+        (s = sp->d_xup.upload(sp->xup, "up patterns")) != HUB_OK ||
+        (s = sp->d_xdn.upload(sp->xdn, "down patterns")) != HUB_OK ||
+        (s = sp->d_pairs.upload(sp->pairs, "pattern pairs")) != HUB_OK)
+      return s;
+    sp->uploaded = true;
+  }
+  if (!rp->uploaded) {
+    if ((s = rp->d_ops.upload(rp->ops, "row ops")) != HUB_OK) return s;
+    rp->uploaded = true;
+  }
+  const size_t r2 = dtype == HUB_C64 ? 8 : 16;
+  if ((s = a->d_coef[dtype].ensure(r2 * std::max<int64_t>(1, batch * a->n_gates), "coefficients")) != HUB_OK) return s;
+  if ((s = a->d_phase[dtype].ensure(r2 * std::max<int64_t>(1, batch * a->n_tab), "phase tables")) != HUB_OK) return s;
+  if ((s = a->d_acc.ensure(8 * (size_t)batch * n_slots, "accumulators")) != HUB_OK) return s;
+  HUB_CUDA(launch_zero((double*)a->d_acc.p, batch * n_slots, st), "zero accumulators");
+  if (theta) {
+    HUB_CUDA(launch_coef(dtype, theta, a->P, (const int32_t*)a->d_gate_param.p, (const double*)a->d_gate_t.p,
+                         a->n_gates, a->d_coef[dtype].p, (const int32_t*)a->d_tab_param.p,
+                         (const double*)a->d_tab_val.p, a->n_tab, (const int32_t*)a->d_tab_live.p,
+                         (int)a->tab_live.size(), a->d_phase[dtype].p, batch,
+                         a->n_inst, st),
+             "coefficient kernel");
+  }
+  // the compressed matrix (region 0) and its transpose (region 1) of psi,
+  // likewise of lam, inside the caller's buffers
+  const size_t mat = (size_t)batch * (size_t)sp->cup * (size_t)sp->cdn;   // amplitudes
+  unsigned char* preg[2] = {(unsigned char*)psi, (unsigned char*)psi + mat * r2};
+  unsigned char* lreg[2] = {(unsigned char*)lam, lam ? (unsigned char*)lam + mat * r2 : nullptr};
+  int cur = 0, orient = rp->segs.empty() ? 0 : rp->segs[0].orient;
+  bool lam_live = false;
+  const int sms = device_sm_count();
+  if (sms <= 0) return fail(HUB_ECUDA, "no CUDA device");
+  auto record = [&](hub_ansatz::ProfRec& rec, bool start) -> cudaError_t {
+    if (!a->prof) return cudaSuccess;
+    if (start) {
+      cudaError_t e = cudaEventCreate(&rec.e0);
+      if (e == cudaSuccess) e = cudaEventCreate(&rec.e1);
+      if (e == cudaSuccess) e = cudaEventRecord(rec.e0, st);
+      return e;
+    }
+    cudaError_t e = cudaEventRecord(rec.e1, st);
+    a->prof_recs.push_back(rec);
+    return e;
+  };
+  for (const RowSegHost& g : rp->segs) {
+    if (g.orient != orient) {   // transpose psi (and lam) into the other region
+      const int n_r = orient == 0 ? sp->cdn : sp->cup, n_c = orient == 0 ? sp->cup : sp->cdn;
+      for (int v = 0; v < (lam_live ? 2 : 1); ++v) {
+        unsigned char* const* reg = v == 0 ? preg : lreg;
+        hub_ansatz::ProfRec rec{};
+        HUB_CUDA(record(rec, true), "cudaEventRecord");
+        HUB_CUDA(launch_transpose(dtype, reg[cur], reg[cur ^ 1], batch, n_r, n_c, st), "transpose");
+        rec.nv = 4;
+        rec.dtype = dtype;
+        rec.bytes = 2.0 * (double)mat * (double)r2;
+        HUB_CUDA(record(rec, false), "cudaEventRecord");
+      }
+      cur ^= 1;
+      orient = g.orient;
+    }
+    const bool has_lam = (g.flags & RS_HAS_LAM) != 0;
+    if (has_lam && !lam) return fail(HUB_EINVAL, "row engine: lam buffer needed");
+    RowArgs ka;
+    std::memset(&ka, 0, sizeof(ka));
+    ka.ops = (const SmallOpDev*)rp->d_ops.p;
+    ka.op_begin = g.op_begin;
+    ka.op_end = g.op_end;
+    ka.flags = g.flags;
+    ka.psi = preg[cur];
+    ka.lam = has_lam ? lreg[cur] : nullptr;
+    ka.n_rows = orient == 0 ? sp->cdn : sp->cup;
+    ka.row_len = orient == 0 ? sp->cup : sp->cdn;
+    ka.xrow = (const uint32_t*)(orient == 0 ? sp->d_xdn.p : sp->d_xup.p);
+    ka.xin = (const uint32_t*)(orient == 0 ? sp->d_xup.p : sp->d_xdn.p);
+    ka.pairs = (const uint32_t*)sp->d_pairs.p;
+    ka.diag_ops = (const DiagOpDev*)a->d_diag.p;
+    ka.coef = a->d_coef[dtype].p;
+    ka.n_gates = a->n_gates;
+    ka.hcoef = (const double*)a->d_hcoef.p;
+    ka.n_hterms = (int)a->hterms.size();
+    ka.real_tabs = (const double*)a->d_real.p;
+    ka.real_tabs32 = (const float*)a->d_real32.p;
+    ka.real_stride = a->real_stride;
+    ka.phase_tabs = a->d_phase[dtype].p;
+    ka.phase_stride = a->n_tab;
+    ka.n_inst = a->n_inst;
+    ka.s = a->s;
+    ka.upmask = a->upmask;
+    ka.batch = batch;
+    ka.acc = (double*)a->d_acc.p;
+    ka.n_slots = n_slots;
+    ka.slot_E = a->P;
+    ka.slot_N = a->P + 1;
+    ka.prep.kind = a->prep_kind;
+    ka.prep.L = a->L;
+    ka.prep.s = a->s;
+    ka.prep.layout = a->layout;
+    ka.prep.neel_x0 = a->neel_x0;
+    ka.prep.sd = (const double*)a->d_sd.p;
+    ka.prep.sd32 = (const float*)a->d_sd32.p;
+    const size_t smem = rows_smem_bytes(dtype, has_lam ? 2 : 1, ka.row_len, n_slots, a->n_gates, ka.n_hterms);
+    const int per_sm = std::max(1, rows_max_ctas_per_sm(dtype, smem));
+    const int64_t grid = std::min<int64_t>(batch * (int64_t)ka.n_rows, (int64_t)sms * per_sm);
+    hub_ansatz::ProfRec rec{};
+    HUB_CUDA(record(rec, true), "cudaEventRecord");
+    HUB_CUDA(launch_rows(dtype, ka, (int)grid, smem, st), "row kernel launch");
+    rec.nv = 3;
+    rec.dtype = dtype;
+    const int io = ((g.flags & RS_PREP) ? 0 : 1) + ((g.flags & RS_WRITE_PSI) ? 1 : 0) +
+                   ((g.flags & RS_READ_LAM) ? 1 : 0) + ((has_lam && (g.flags & RS_WRITE_LAM)) ? 1 : 0);
+    rec.bytes = (double)io * (double)mat * (double)r2;
+    HUB_CUDA(record(rec, false), "cudaEventRecord");
+    lam_live = lam_live || (has_lam && (g.flags & RS_WRITE_LAM));
+  }
+  HUB_CUDA(launch_finalize((const double*)a->d_acc.p, n_slots, a->P, a->P, E, grad, batch, st), "finalize kernel");
+  return HUB_OK;
+}
+
 hub_status check_call(hub_ansatz* a, int32_t dtype, int64_t batch) {
   if (!a) return fail(HUB_EINVAL, "NULL ansatz");
   if (dtype != HUB_C64 && dtype != HUB_C128) return fail(HUB_EINVAL, "dtype must be HUB_C64 or HUB_C128");
@@ -906,6 +1066,9 @@ extern "C" hub_status energy(ans_t a, const double* theta, void* psi, double* E,
   size_t smem = 0;
   if (SmallPlan* sp = small_plan_for(a, 0, dtype, flags, smem))
     return run_small(a, sp, smem, dtype, theta, batch, E, nullptr, (cudaStream_t)stream);
+  SmallPlan* rsp = nullptr;
+  if (RowPlan* rp = row_plan_for(a, 0, dtype, flags, rsp))
+    return run_rows(a, rsp, rp, dtype, theta, psi, nullptr, batch, E, nullptr, (cudaStream_t)stream);
   Plan* pl;
   if ((s = get_plan(a, 0, dtype, flags & 3u, pl)) != HUB_OK) return s;
   return run_plan(a, pl, dtype, theta, psi, nullptr, nullptr, batch, E, nullptr, (cudaStream_t)stream);
@@ -924,6 +1087,9 @@ extern "C" hub_status energy_grad(ans_t a, const double* theta, void* psi, void*
   size_t smem = 0;
   if (SmallPlan* sp = small_plan_for(a, 1, dtype, flags, smem))
     return run_small(a, sp, smem, dtype, theta, batch, E, grad, (cudaStream_t)stream);
+  SmallPlan* rsp = nullptr;
+  if (RowPlan* rp = row_plan_for(a, 1, dtype, flags, rsp))
+    return run_rows(a, rsp, rp, dtype, theta, psi, lam, batch, E, grad, (cudaStream_t)stream);
   const uint32_t pf = (flags & 3u) | (ckpt ? kPlanCkpt : 0u);
   Plan* pl;
   if ((s = get_plan(a, 1, dtype, pf, pl)) != HUB_OK) return s;
@@ -945,6 +1111,25 @@ extern "C" hub_status ans_plan_stats(ans_t a, int32_t which, int32_t dtype, uint
                                      double* bytes_per_state) {
   if (!a || which < 0 || which > 2 || (dtype != HUB_C64 && dtype != HUB_C128))
     return fail(HUB_EINVAL, "ans_plan_stats: bad arguments");
+  if (flags & HUB_FLAG_ROWS) {   // the row engine's schedule (energy or energy_grad)
+    if (which > 1) return fail(HUB_EINVAL, "ans_plan_stats: the row engine runs energy and energy_grad only");
+    SmallPlan* sp = get_small_plan(a, which);
+    if (!sp) return fail(HUB_EUNSUPPORTED, "ans_plan_stats: no sector plan");
+    RowPlan* rp = nullptr;
+    auto it = a->row_plans.find(which);
+    if (it != a->row_plans.end()) {
+      rp = it->second;
+    } else {
+      if (make_row_plan(a, which, sp, rp) != HUB_OK) rp = nullptr;
+      a->row_plans[which] = rp;
+    }
+    if (!rp) return fail(HUB_EUNSUPPORTED, "ans_plan_stats: no row schedule");
+    int launches = 0;
+    const double by = row_plan_bytes(sp, rp, dtype, &launches);
+    if (n_sweeps) *n_sweeps = launches;
+    if (bytes_per_state) *bytes_per_state = by;
+    return HUB_OK;
+  }
   Plan* pl;
   hub_status s = get_plan(a, which, dtype, flags, pl);
   if (s != HUB_OK) return s;

@@ -67,6 +67,27 @@ struct Plan {
 };
 
 // On-chip plan of a call kind (see SmallOpDev).
+struct RowSegHost {
+  int op_begin = 0, op_end = 0;   // operations of the segment (SmallPlan::ops)
+  int orient = 0;                 // 0: rows = down patterns, 1: rows = up patterns
+  uint32_t flags = 0;             // RowSegFlag
+};
+
+// The row engine's schedule of a call kind (hubsv_rows.cu): the on-chip
+// plan's operations reordered into segments, each a contiguous range of ops.
+struct RowPlan {
+  std::vector<RowSegHost> segs;
+  std::vector<SmallOpDev> ops;
+  DevBuf d_ops;
+  bool uploaded = false;
+};
+
+// Sequence indices of a row segment and its orientation.
+struct RowSched {
+  int orient;
+  std::vector<int> ops;
+};
+
 struct SmallPlan {
   int cup = 0, cdn = 0;
   std::vector<uint32_t> xup, xdn, pairs;
@@ -114,6 +135,7 @@ struct hub_ansatz {
   hubsv::DevBuf d_coef[2], d_phase[2], d_acc;
   std::map<int, hubsv::Plan*> plans;     // key = which*16 + dtype*4 + flags
   std::map<int, hubsv::SmallPlan*> small_plans;   // key = which
+  std::map<int, hubsv::RowPlan*> row_plans;       // key = which
   int tile_override[2] = {0, 0};
   int run_override[2] = {0, 0};         // log2 contiguous amplitudes per run (0 = default)
   bool dev_ready = false;
@@ -139,4 +161,8 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
 // lam = H psi, 3 initial state only), before any tiling.
 std::vector<SeqOp> op_sequence(const hub_ansatz* a, int which, uint32_t flags);
 hub_status make_small_plan(hub_ansatz* a, int which, SmallPlan*& out);
+hub_status make_row_plan(const hub_ansatz* a, int which, const SmallPlan* sp, RowPlan*& out);
+std::vector<RowSched> row_schedule(const hub_ansatz* a, int which);
+// HBM bytes per batch element and kernel launches of a row plan.
+double row_plan_bytes(const SmallPlan* sp, const RowPlan* rp, int dtype, int* n_launches);
 }  // namespace hubsv

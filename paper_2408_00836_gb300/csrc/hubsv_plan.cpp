@@ -224,6 +224,39 @@ void choose_lanes(uint32_t free_bits, uint32_t required, int dtype, uint8_t* lan
 
 }  // namespace
 
+// Row-engine schedule: segments of the fused-preparation sequence, each run
+// in one orientation (0: all up modes in a row, 1: all down modes), found
+// by the same greedy scan as the sweeps with the up modes or the down modes
+// as the tile (diagonal operations fit either); each step takes the
+// orientation that runs more operations, the current one on a tie.
+std::vector<RowSched> row_schedule(const hub_ansatz* a, int which) {
+  const std::vector<SeqOp> seq = build_sequence(a, which, HUB_FLAG_PREP_FUSED);
+  uint64_t upm = 0, dnm = 0;
+  for (int i = 0; i < a->L; ++i) {
+    upm |= 1ull << a->models[0]->up[i];
+    dnm |= 1ull << a->models[0]->dn[i];
+  }
+  auto need = [](const SeqOp& op) -> uint64_t {
+    return op.diagonal ? 0ull : ((1ull << op.p) | (1ull << op.q));
+  };
+  std::vector<int> rem(seq.size());
+  for (size_t i = 0; i < seq.size(); ++i) rem[i] = (int)i;
+  std::vector<RowSched> out;
+  int orient = 0;
+  while (!rem.empty()) {
+    Scan s0 = scan(seq, rem, 0ull, upm, 64, need);
+    Scan s1 = scan(seq, rem, 0ull, dnm, 64, need);
+    int pick = orient;
+    if (s0.exec.size() != s1.exec.size()) pick = s0.exec.size() > s1.exec.size() ? 0 : 1;
+    Scan& sp = pick == 0 ? s0 : s1;
+    if (sp.exec.empty()) return {RowSched{-1, {}}};   // no progress: not schedulable by rows
+    out.push_back({pick, sp.exec});
+    rem.swap(sp.rest);
+    orient = pick;
+  }
+  return out;
+}
+
 std::vector<SeqOp> op_sequence(const hub_ansatz* a, int which, uint32_t flags) {
   return build_sequence(a, which, flags);
 }

@@ -1,0 +1,352 @@
+// Row engine of the Hubbard VQE statevector engine: sector amplitudes in HBM.
+//
+// Every operation of the ansatz (Eq. 7), of H (Eqs. 1, 2, 15, 16) and of the
+// adjoint recursion (Sec. 2.1) conserves N_up and N_dn, so a state prepared
+// in the sector is its C(L, N_up) * C(L, N_dn) sector amplitudes (at 32
+// qubits, N = 8 + 8: 165.6 M of the 2^32).  They are stored per batch
+// element as a matrix with one row per down pattern and one column per up
+// pattern (orientation 0), or transposed (orientation 1).  A hop on two up
+// modes pairs up patterns, i.e. elements of one row in orientation 0; a hop
+// on two down modes pairs elements of one row in orientation 1; diagonal
+// operations act on single elements.  So the call's operation sequence is
+// cut into segments of one orientation, and each segment is one sweep over
+// the rows: a CTA stages whole rows of psi (and lam) in shared memory, runs
+// the segment's operations on them one at a time (a barrier between
+// operations), and writes them back.  Between segments of different
+// orientation the matrix is transposed.
+//
+// Element operations follow the on-chip engine: a pair of in-row ranks from
+// the pair list of the hop's modes, the full index x = xrow[row] | xin[rank]
+// for the Jordan-Wigner parity and the diagonal tables.
+#include <algorithm>
+#include <cstring>
+
+#include "hubsv_host.h"
+#include "hubsv_reduce.cuh"
+
+namespace hubsv {
+
+namespace {
+constexpr int kRowThreads = 512;
+constexpr int kRowWarps = kRowThreads / 32;
+}  // namespace
+
+// The row segments of a call kind: the operations of the on-chip plan
+// (one per sequence entry) in the order of row_schedule, with what each
+// segment reads and writes.
+hub_status make_row_plan(const hub_ansatz* a, int which, const SmallPlan* sp, RowPlan*& out) {
+  const std::vector<RowSched> sched = row_schedule(a, which);
+  for (const RowSched& rs : sched)
+    if (rs.orient < 0) return fail(HUB_EUNSUPPORTED, "row engine: no schedule");
+  RowPlan* rp = new RowPlan();
+  bool lam_live = false;
+  for (const RowSched& rs : sched) {
+    RowSegHost g;
+    g.op_begin = (int)rp->ops.size();
+    g.orient = rs.orient;
+    bool mod_psi = false, mod_lam = false, makes_lam = false, meas = false;
+    for (int idx : rs.ops) {
+      const SmallOpDev& op = sp->ops[idx];
+      rp->ops.push_back(op);
+      const bool lam_op = op.kind == OP_LAM_HOP || op.kind == OP_LAM_DIAG;
+      mod_psi = mod_psi || op.kind == OP_GIV || op.kind == OP_DIAG;
+      mod_lam = mod_lam || lam_op || ((op.kind == OP_GIV || op.kind == OP_DIAG) && (op.flags & OPF_LAM));
+      makes_lam = makes_lam || lam_op;
+      meas = meas || lam_op || op.kind == OP_MEAS_HOP || op.kind == OP_MEAS_DIAG;
+    }
+    g.op_end = (int)rp->ops.size();
+    uint32_t f = 0;
+    if (rp->segs.empty()) f |= RS_PREP | RS_WRITE_PSI;
+    if (mod_psi) f |= RS_WRITE_PSI;
+    if (lam_live || makes_lam) f |= RS_HAS_LAM;
+    if (lam_live) f |= RS_READ_LAM;
+    if (mod_lam) f |= RS_WRITE_LAM;
+    if (meas) f |= RS_MEAS;
+    lam_live = lam_live || makes_lam;
+    g.flags = f;
+    rp->segs.push_back(g);
+  }
+  if (rp->segs.empty()) {   // no operations: prepare psi_0 only (E = 0)
+    RowSegHost g;
+    g.flags = RS_PREP;
+    rp->segs.push_back(g);
+  }
+  if (rp->ops.empty()) rp->ops.push_back(SmallOpDev{});
+  rp->segs.back().flags &= ~(uint32_t)(RS_WRITE_PSI | RS_WRITE_LAM);   // nothing reads them
+  out = rp;
+  return HUB_OK;
+}
+
+double row_plan_bytes(const SmallPlan* sp, const RowPlan* rp, int dtype, int* n_launches) {
+  const double m = (double)sp->cup * (double)sp->cdn * (dtype == 0 ? 8.0 : 16.0);
+  double bytes = 0.0;
+  int launches = 0, orient = rp->segs.empty() ? 0 : rp->segs[0].orient;
+  bool lam_live = false;
+  for (const RowSegHost& g : rp->segs) {
+    if (g.orient != orient) {   // transposes: read + write of psi (and lam)
+      bytes += 2.0 * m * (lam_live ? 2.0 : 1.0);
+      launches += lam_live ? 2 : 1;
+      orient = g.orient;
+    }
+    const bool has_lam = (g.flags & RS_HAS_LAM) != 0;
+    const int io = ((g.flags & RS_PREP) ? 0 : 1) + ((g.flags & RS_WRITE_PSI) ? 1 : 0) +
+                   ((g.flags & RS_READ_LAM) ? 1 : 0) + ((has_lam && (g.flags & RS_WRITE_LAM)) ? 1 : 0);
+    bytes += (double)io * m;
+    ++launches;
+    lam_live = lam_live || (has_lam && (g.flags & RS_WRITE_LAM));
+  }
+  if (n_launches) *n_launches = launches;
+  return bytes;
+}
+
+size_t rows_smem_bytes(int dtype, int nv, int row_len, int n_slots, int n_gates, int n_hterms) {
+  const size_t amp = dtype == 0 ? 8 : 16;
+  size_t s = (size_t)nv * (size_t)row_len * amp;            // rows of psi (, lam)
+  s = (s + 15) & ~(size_t)15;
+  s += amp * (size_t)n_gates;                               // (cos, sin) of the element
+  s += 8 * (size_t)kRowWarps * (size_t)n_slots;             // accumulator rows
+  s += amp / 2 * (size_t)n_hterms;                          // -t of the element's instance
+  return (s + 15) & ~(size_t)15;
+}
+
+namespace {
+
+template <typename R>
+__global__ void __launch_bounds__(kRowThreads, 2) rows_kernel(const RowArgs a) {
+  using T2 = typename CT<R>::T2;
+  constexpr int DT = CT<R>::DT;
+  using AccT = typename std::conditional<DT == 0, float2, double>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const bool has_lam = (a.flags & RS_HAS_LAM) != 0;
+  const int len = a.row_len;
+  T2* prow = reinterpret_cast<T2*>(smem_raw);
+  T2* lrow = prow + len;
+  const size_t rows_b = (((size_t)(has_lam ? 2 : 1) * (size_t)len * sizeof(T2)) + 15) & ~(size_t)15;
+  T2* cs = reinterpret_cast<T2*>(smem_raw + rows_b);
+  AccT* acc = reinterpret_cast<AccT*>(cs + a.n_gates);   // [kRowWarps][n_slots]
+  R* hc = reinterpret_cast<R*>(acc + kRowWarps * a.n_slots);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const R* rtabs = reinterpret_cast<const R*>(DT == 0 ? (const void*)a.real_tabs32 : (const void*)a.real_tabs);
+  const T2* ptabs = reinterpret_cast<const T2*>(a.phase_tabs);
+  const T2* coef = reinterpret_cast<const T2*>(a.coef);
+  const R* sdt = reinterpret_cast<const R*>(DT == 0 ? (const void*)a.prep.sd32 : (const void*)a.prep.sd);
+  const uint32_t upm = (uint32_t)a.upmask;
+  T2* psi = reinterpret_cast<T2*>(a.psi);
+  T2* lam = reinterpret_cast<T2*>(a.lam);
+  const bool meas = (a.flags & RS_MEAS) != 0;
+
+  const int64_t total = a.batch * (int64_t)a.n_rows;
+  int64_t cur_b = -1;
+  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+    const int64_t b = g / a.n_rows;
+    const int rr = (int)(g - b * a.n_rows);
+    const int inst = (int)(b % a.n_inst);
+    __syncthreads();   // the previous row is stored
+    if (b != cur_b) {
+      if (cur_b >= 0) {   // read out the previous element's accumulators
+        for (int i = tid; i < a.n_slots; i += nth) {
+          double x = 0.0;
+          for (int w = 0; w < kRowWarps; ++w) x += row_value(acc[w * a.n_slots + i]);
+          if (x != 0.0) atomicAdd(&a.acc[(size_t)cur_b * a.n_slots + i], x);
+        }
+        __syncthreads();
+      }
+      for (int i = tid; i < kRowWarps * a.n_slots; i += nth) acc[i] = AccT{};
+      for (int i = tid; i < a.n_gates; i += nth) cs[i] = coef[b * a.n_gates + i];
+      for (int i = tid; i < a.n_hterms; i += nth) hc[i] = (R)a.hcoef[(size_t)inst * a.n_hterms + i];
+      cur_b = b;
+    }
+    const uint32_t xr = a.xrow[rr];
+    const size_t base = ((size_t)b * (size_t)a.n_rows + (size_t)rr) * (size_t)len;
+    if (a.flags & RS_PREP) {
+      for (int i = tid; i < len; i += nth) prow[i] = mk<T2, R>(prep_amp<R>(a.prep, sdt, xr | a.xin[i], inst), (R)0);
+    } else {
+      for (int i = tid; i < len; i += nth) prow[i] = psi[base + i];
+    }
+    if (has_lam) {
+      if (a.flags & RS_READ_LAM) {
+        for (int i = tid; i < len; i += nth) lrow[i] = lam[base + i];
+      } else {
+        for (int i = tid; i < len; i += nth) lrow[i] = mk<T2, R>((R)0, (R)0);
+      }
+    }
+    __syncthreads();
+    Tot<R> eacc, nacc;
+    for (int oi = a.op_begin; oi < a.op_end; ++oi) {
+      const SmallOpDev op = a.ops[oi];
+      R part = 0, npart = 0;
+      if (op.kind == OP_GIV || op.kind == OP_MEAS_HOP || op.kind == OP_LAM_HOP || op.kind == OP_GRAD_HOP) {
+        R c = 0, s = 0, tc = 0;
+        if (op.kind == OP_GIV) {
+          const T2 gq = cs[op.gate];
+          c = gq.x;
+          s = (op.flags & OPF_INV) ? -gq.y : gq.y;
+        } else {
+          tc = hc[op.hterm];
+        }
+        const bool dol = (op.flags & OPF_LAM) != 0;
+        // the row's part of the Jordan-Wigner parity (the in-row part is
+        // bit 31 of the pair entry); pair entries are loaded four at a time
+        const uint32_t rpar = (uint32_t)__popc(xr & op.between) & 1u;
+        const uint32_t* pl = a.pairs + op.a;
+        for (int it0 = tid; it0 < op.b; it0 += 4 * nth) {
+          uint32_t prs[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int it = it0 + k * nth;
+            prs[k] = it < op.b ? __ldg(pl + it) : 0u;
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+          if (it0 + k * nth >= op.b) break;
+          const uint32_t pr = prs[k];
+          const int e1 = (int)(pr & 0xffffu), e2 = (int)((pr >> 16) & 0x7fffu);
+          const bool neg = ((pr >> 31) ^ rpar) != 0;
+          T2 u = prow[e1], w = prow[e2];
+          if (op.kind == OP_GIV) {
+            const R ss = neg ? -s : s;
+            rot(u, w, c, ss);
+            prow[e1] = u;
+            prow[e2] = w;
+            if (dol) {
+              T2 lu = lrow[e1], lw = lrow[e2];
+              rot(lu, lw, c, ss);
+              lrow[e1] = lu;
+              lrow[e2] = lw;
+            }
+          } else {
+            const R ts = neg ? -tc : tc;
+            if (op.kind == OP_GRAD_HOP) {
+              const T2 lu = lrow[e1], lw = lrow[e2];
+              part += ts * ((lu.x * w.y - lu.y * w.x) + (lw.x * u.y - lw.y * u.x));
+            } else {
+              part += ts * (u.x * w.x + u.y * w.y);
+              if (op.kind == OP_LAM_HOP) {
+                T2 lu = lrow[e1], lw = lrow[e2];
+                lu.x += ts * w.x; lu.y += ts * w.y;
+                lw.x += ts * u.x; lw.y += ts * u.y;
+                lrow[e1] = lu;
+                lrow[e2] = lw;
+              }
+            }
+          }
+          }
+        }
+        if (op.kind == OP_GRAD_HOP) row_add(acc, a.n_slots, op.slot, (R)2 * part);
+        else if (op.kind != OP_GIV) eacc.add((R)2 * part);
+      } else {   // diagonal operations
+        const DiagOpDev& d = a.diag_ops[op.a];
+        const T2* ptab = ptabs + (size_t)b * a.phase_stride + d.phase_off;
+        const R* rtab = rtabs + (size_t)inst * a.real_stride + d.real_off;
+        const bool inv = (op.flags & OPF_INV) != 0, dol = (op.flags & OPF_LAM) != 0;
+        for (int e = tid; e < len; e += nth) {
+          const uint32_t x = xr | __ldg(a.xin + e);
+          if (op.kind == OP_DIAG) {
+            T2 p = diag_phase<T2, true>(d, ptab, x, a.s, upm);
+            if (inv) p.y = -p.y;
+            prow[e] = cmul(prow[e], p);
+            if (dol) lrow[e] = cmul(lrow[e], p);
+          } else {
+            const R dv = diag_real<R, true>(d, rtab, x, a.s, upm);
+            const T2 u = prow[e];
+            if (op.kind == OP_GRAD_DIAG) {
+              const T2 l = lrow[e];
+              part += dv * (l.x * u.y - l.y * u.x);
+            } else {
+              const R m2 = u.x * u.x + u.y * u.y;
+              part += dv * m2;
+              npart += m2;
+              if (op.kind == OP_LAM_DIAG) {
+                T2 l = lrow[e];
+                l.x += dv * u.x;
+                l.y += dv * u.y;
+                lrow[e] = l;
+              }
+            }
+          }
+        }
+        if (op.kind == OP_GRAD_DIAG) {
+          row_add(acc, a.n_slots, op.slot, (R)2 * part);
+        } else if (op.kind != OP_DIAG) {
+          eacc.add(part);
+          nacc.add(npart);
+        }
+      }
+      __syncthreads();
+    }
+    if (meas) {
+      row_add_tot(acc, a.n_slots, a.slot_E, eacc);
+      row_add_tot(acc, a.n_slots, a.slot_N, nacc);
+    }
+    if (a.flags & RS_WRITE_PSI)
+      for (int i = tid; i < len; i += nth) psi[base + i] = prow[i];
+    if (has_lam && (a.flags & RS_WRITE_LAM))
+      for (int i = tid; i < len; i += nth) lam[base + i] = lrow[i];
+  }
+  __syncthreads();
+  if (cur_b >= 0) {
+    for (int i = tid; i < a.n_slots; i += nth) {
+      double x = 0.0;
+      for (int w = 0; w < kRowWarps; ++w) x += row_value(acc[w * a.n_slots + i]);
+      if (x != 0.0) atomicAdd(&a.acc[(size_t)cur_b * a.n_slots + i], x);
+    }
+  }
+}
+
+// out[b][c][r] = in[b][r][c], 32 x 32 tiles through shared memory (one
+// padding column keeps the column reads free of bank conflicts).
+template <typename T2>
+__global__ void __launch_bounds__(256) transpose_kernel(const T2* __restrict__ in, T2* __restrict__ out,
+                                                        int64_t batch, int n_r, int n_c) {
+  __shared__ T2 tile[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const size_t mat = (size_t)n_r * (size_t)n_c;
+  for (int64_t b = blockIdx.z; b < batch; b += gridDim.z) {
+    const T2* src = in + (size_t)b * mat;
+    T2* dst = out + (size_t)b * mat;
+    for (int j = ty; j < 32; j += 8) {
+      const int r = r0 + j, c = c0 + tx;
+      if (r < n_r && c < n_c) tile[j][tx] = src[(size_t)r * n_c + c];
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+      const int c = c0 + j, r = r0 + tx;
+      if (r < n_r && c < n_c) dst[(size_t)c * n_r + r] = tile[tx][j];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_rows(int dtype, const RowArgs& a, int grid, size_t smem, cudaStream_t st) {
+  const void* f = dtype == 0 ? (const void*)rows_kernel<float> : (const void*)rows_kernel<double>;
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  RowArgs ac = a;
+  void* args[] = {(void*)&ac};
+  return cudaLaunchKernel(f, dim3(grid), dim3(kRowThreads), args, smem, st);
+}
+
+int rows_max_ctas_per_sm(int dtype, size_t smem) {
+  const void* f = dtype == 0 ? (const void*)rows_kernel<float> : (const void*)rows_kernel<double>;
+  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kRowThreads, smem) != cudaSuccess) return 0;
+  return n;
+}
+
+cudaError_t launch_transpose(int dtype, const void* in, void* out, int64_t batch, int n_r, int n_c,
+                             cudaStream_t st) {
+  if (batch <= 0 || n_r <= 0 || n_c <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((n_c + 31) / 32), (unsigned)((n_r + 31) / 32),
+                  (unsigned)std::min<int64_t>(batch, 1024));
+  if (dtype == 0)
+    transpose_kernel<float2><<<grid, dim3(32, 8), 0, st>>>((const float2*)in, (float2*)out, batch, n_r, n_c);
+  else
+    transpose_kernel<double2><<<grid, dim3(32, 8), 0, st>>>((const double2*)in, (double2*)out, batch, n_r, n_c);
+  return cudaGetLastError();
+}
+
+}  // namespace hubsv

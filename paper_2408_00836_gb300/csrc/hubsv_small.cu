@@ -24,7 +24,7 @@
 #include <type_traits>
 
 #include "hubsv_host.h"
-#include "hubsv_sweep.cuh"
+#include "hubsv_reduce.cuh"
 
 namespace hubsv {
 
@@ -91,7 +91,8 @@ hub_status make_small_plan(hub_ansatz* a, int which, SmallPlan*& out) {
           const uint32_t x = xs[r];
           if ((x >> p & 1u) == 0 && (x >> q & 1u) == 1) {
             const uint32_t x2 = x ^ (1u << p) ^ (1u << q);
-            sp->pairs.push_back((uint32_t)r | ((uint32_t)rk.at(x2) << 16));
+            const uint32_t par = (uint32_t)__builtin_popcount(x & d.between) & 1u;
+            sp->pairs.push_back((uint32_t)r | ((uint32_t)rk.at(x2) << 16) | (par << 31));
           }
         }
         it = lists.emplace(std::make_pair(p, q), std::make_pair(off, (int)sp->pairs.size() - off)).first;
@@ -148,62 +149,6 @@ size_t small_smem_bytes(int dtype, int cup, int cdn, int n_pairs, int n_slots, i
 // ---------------------------------------------------------------------------
 
 namespace {
-
-// The complex64 kernel reduces in FP32 and keeps its running totals as
-// float pairs (two_sum, ff_add, warp_sum_f from the sweep kernel's header);
-// the complex128 kernel reduces in FP64.
-
-// Sum of float pairs over the warp, into lane 0's (h, l).
-__device__ __forceinline__ void warp_sum_ff(float& h, float& l) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
-    float s, e;
-    two_sum(h, h2, s, e);
-    e += l + l2;
-    h = s + e;
-    l = e - (h - s);
-  }
-}
-
-// Running totals of one thread (R = float: float pairs; double: FP64).
-template <typename R> struct Tot;
-template <> struct Tot<float> {
-  float h = 0.f, l = 0.f;
-  __device__ __forceinline__ void add(float v) { ff_add(h, l, v); }
-};
-template <> struct Tot<double> {
-  double v = 0.0;
-  __device__ __forceinline__ void add(double x) { v += x; }
-};
-
-// Per-warp accumulator rows: row w, slot i at acc[w * n_slots + i], float
-// pairs (c64) or doubles (c128); lane 0 of warp w alone writes row w, so no
-// atomics are needed, and the rows are summed in FP64 once per element.
-// Adds the warp's sum of v to its row's slot (every lane calls).
-__device__ __forceinline__ void row_add(float2* acc, int n_slots, int slot, float v) {
-  v = warp_sum_f(v);
-  if ((threadIdx.x & 31) == 0) {
-    float2& t = acc[(threadIdx.x >> 5) * n_slots + slot];
-    ff_add(t.x, t.y, v);
-  }
-}
-__device__ __forceinline__ void row_add(double* acc, int n_slots, int slot, double v) {
-  v = warp_sum(v);
-  if ((threadIdx.x & 31) == 0) acc[(threadIdx.x >> 5) * n_slots + slot] += v;
-}
-// Adds the warp's sum of the lanes' running totals to its row (every lane calls).
-__device__ __forceinline__ void row_add_tot(float2* acc, int n_slots, int slot, Tot<float> t) {
-  warp_sum_ff(t.h, t.l);
-  if ((threadIdx.x & 31) == 0) {
-    float2& r = acc[(threadIdx.x >> 5) * n_slots + slot];
-    ff_add(r.x, r.y, t.h);
-    ff_add(r.x, r.y, t.l);
-  }
-}
-__device__ __forceinline__ void row_add_tot(double* acc, int n_slots, int slot, Tot<double> t) {
-  row_add(acc, n_slots, slot, t.v);
-}
 
 // n / d for the n < 2^32 / d met here, with m = ceil(2^32 / d) from
 // small_magic (0 for d = 1): one high multiply instead of a division.
@@ -277,7 +222,7 @@ __global__ void __launch_bounds__(kSmallThreads, sizeof(R) == 4 ? 2 : 1) small_k
         for (int it = tid; it < items; it += nth) {
           const int pi = (int)div_magic((uint32_t)it, mo), ro = it - pi * other;
           const uint32_t pr = pairs[op.a + pi];
-          const int r1 = (int)(pr & 0xffffu), r2 = (int)(pr >> 16);
+          const int r1 = (int)(pr & 0xffffu), r2 = (int)((pr >> 16) & 0x7fffu);
           int e1, e2;
           uint32_t x;
           if (upair) {

@@ -29,7 +29,8 @@ struct SmallArgs {
   int32_t cup, cdn;
   int32_t ld;                      // row pitch of the element matrix: cup | 1
   uint32_t m_cup, m_cdn;           // small_magic(cup), small_magic(cdn)
-  const uint32_t* pairs;           // pattern-rank pairs r | r' << 16 (r: bit p clear, q set)
+  const uint32_t* pairs;           // pattern-rank pairs r | r' << 16 (r: bit p clear, q set),
+                                   // bit 31: parity of the pattern r on the modes between p, q
   int32_t n_pairs;
   const DiagOpDev* diag_ops;
   const void* coef;                // [batch][n_gates] (cos, sin), R2
@@ -59,5 +60,63 @@ size_t small_smem_bytes(int dtype, int cup, int cdn, int n_pairs, int n_slots, i
 uint32_t small_magic(int d);
 cudaError_t launch_small(int dtype, const SmallArgs& a, int grid, size_t smem, cudaStream_t st);
 int small_max_ctas_per_sm(int dtype, size_t smem);
+
+// ---------------------------------------------------------------------------
+// Row engine (hubsv_rows.cu): the sector amplitudes of each batch element
+// stored in HBM as a C_dn x C_up matrix (orientation 0: row r_dn holds the
+// C_up amplitudes of that down pattern, in up-pattern order) or its
+// transpose (orientation 1).  Up-spin hops pair elements of one row in
+// orientation 0, down-spin hops in orientation 1; diagonal operations act
+// element by element in either.  A row sweep stages whole rows in shared
+// memory and runs a segment of the operation sequence on them; the matrix
+// is transposed between segments of different orientation.
+// ---------------------------------------------------------------------------
+
+enum RowSegFlag : uint32_t {
+  RS_PREP = 1u,        // generate psi_0 instead of reading psi
+  RS_WRITE_PSI = 2u,   // the segment changes psi
+  RS_HAS_LAM = 4u,     // rows carry lam
+  RS_READ_LAM = 8u,    // else lam starts at zero
+  RS_WRITE_LAM = 16u,
+  RS_MEAS = 32u,       // the segment adds to E and N
+};
+
+struct RowArgs {
+  const SmallOpDev* ops;           // the call's operation sequence
+  int32_t op_begin, op_end;        // this segment's operations
+  uint32_t flags;                  // RowSegFlag
+  void* psi;                       // [batch][n_rows][row_len] amplitudes, R2
+  void* lam;                       // the same for lam (RS_HAS_LAM)
+  int32_t n_rows, row_len;         // C_dn, C_up (orientation 0) or C_up, C_dn
+  const uint32_t* xrow;            // [n_rows] index bits of each row's pattern
+  const uint32_t* xin;             // [row_len] index bits of each in-row pattern
+  const uint32_t* pairs;           // pattern-rank pairs as SmallArgs::pairs (in-row ranks)
+  const DiagOpDev* diag_ops;
+  const void* coef;                // [batch][n_gates] (cos, sin), R2
+  int32_t n_gates;
+  const double* hcoef;             // [n_inst][n_hterms]
+  int32_t n_hterms;
+  const double* real_tabs;
+  const float* real_tabs32;
+  int32_t real_stride;
+  const void* phase_tabs;          // [batch][phase_stride] R2
+  int32_t phase_stride;
+  int32_t n_inst;
+  int32_t s;
+  uint64_t upmask;
+  int64_t batch;
+  double* acc;                     // [batch][n_slots], added to atomically
+  int32_t n_slots, slot_E, slot_N;
+  PrepDev prep;
+};
+
+// Shared memory of a row sweep: the rows of psi (and lam), the element's
+// Givens coefficients, the accumulator rows and the -t values.
+size_t rows_smem_bytes(int dtype, int nv, int row_len, int n_slots, int n_gates, int n_hterms);
+cudaError_t launch_rows(int dtype, const RowArgs& a, int grid, size_t smem, cudaStream_t st);
+int rows_max_ctas_per_sm(int dtype, size_t smem);
+// out[b][c][r] = in[b][r][c] for a [batch][n_r][n_c] matrix of amplitudes.
+cudaError_t launch_transpose(int dtype, const void* in, void* out, int64_t batch, int n_r, int n_c,
+                             cudaStream_t st);
 
 }  // namespace hubsv
