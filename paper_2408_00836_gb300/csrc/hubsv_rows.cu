@@ -45,8 +45,26 @@ hub_status make_row_plan(const hub_ansatz* a, int which, const SmallPlan* sp, Ro
     g.op_begin = (int)rp->ops.size();
     g.orient = rs.orient;
     bool mod_psi = false, mod_lam = false, makes_lam = false, meas = false;
-    for (int idx : rs.ops) {
-      const SmallOpDev& op = sp->ops[idx];
+    for (size_t j = 0; j < rs.ops.size(); ++j) {
+      const SmallOpDev& op = sp->ops[rs.ops[j]];
+      // a gradient term directly followed by the inverse of its own factor
+      // on psi and lam runs as one operation (one pass over the pairs)
+      if ((op.kind == OP_GRAD_HOP || op.kind == OP_GRAD_DIAG) && j + 1 < rs.ops.size()) {
+        const SmallOpDev& nx = sp->ops[rs.ops[j + 1]];
+        const bool same = op.kind == OP_GRAD_HOP
+                              ? (nx.kind == OP_GIV && nx.a == op.a && nx.b == op.b && nx.between == op.between)
+                              : (nx.kind == OP_DIAG && nx.a == op.a);
+        if (same && (nx.flags & OPF_INV) && (nx.flags & OPF_LAM)) {
+          SmallOpDev f = op;
+          f.kind = op.kind == OP_GRAD_HOP ? OP_GRADINV_HOP : OP_GRADINV_DIAG;
+          f.flags = nx.flags;
+          f.gate = nx.gate;
+          rp->ops.push_back(f);
+          mod_psi = mod_lam = true;
+          ++j;
+          continue;
+        }
+      }
       rp->ops.push_back(op);
       const bool lam_op = op.kind == OP_LAM_HOP || op.kind == OP_LAM_DIAG;
       mod_psi = mod_psi || op.kind == OP_GIV || op.kind == OP_DIAG;
@@ -110,6 +128,98 @@ size_t rows_smem_bytes(int dtype, int nv, int row_len, int n_slots, int n_gates,
 }
 
 namespace {
+
+enum { RH_GIV = 0, RH_MEAS = 1, RH_LAM = 2, RH_GRAD = 3, RH_GRADINV = 4 };
+
+// One hop operation on a staged row: the pairs of its pair list, four entries
+// loaded at a time; returns this thread's share of the measured or gradient
+// term.  K and DOL are fixed per call site, so the loop carries no branches
+// on the operation kind.
+template <int K, bool DOL, typename R, typename T2>
+__device__ __forceinline__ R row_hop(T2* __restrict__ prow, T2* __restrict__ lrow,
+                                     const uint32_t* __restrict__ pl, int nb, uint32_t rpar, R c, R s,
+                                     R tc) {
+  R part = 0;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int it0 = tid; it0 < nb; it0 += 4 * nth) {
+    uint32_t prs[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int it = it0 + k * nth;
+      prs[k] = it < nb ? __ldg(pl + it) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (it0 + k * nth >= nb) break;
+      const uint32_t pr = prs[k];
+      const int e1 = (int)(pr & 0xffffu), e2 = (int)((pr >> 16) & 0x7fffu);
+      const bool neg = ((pr >> 31) ^ rpar) != 0;
+      T2 u = prow[e1], w = prow[e2];
+      if constexpr (K == RH_GIV) {
+        const R ss = neg ? -s : s;
+        rot(u, w, c, ss);
+        prow[e1] = u;
+        prow[e2] = w;
+        if constexpr (DOL) {
+          T2 lu = lrow[e1], lw = lrow[e2];
+          rot(lu, lw, c, ss);
+          lrow[e1] = lu;
+          lrow[e2] = lw;
+        }
+      } else if constexpr (K == RH_GRAD || K == RH_GRADINV) {
+        const R ts = neg ? -tc : tc;
+        T2 lu = lrow[e1], lw = lrow[e2];
+        part += ts * ((lu.x * w.y - lu.y * w.x) + (lw.x * u.y - lw.y * u.x));
+        if constexpr (K == RH_GRADINV) {   // then the inverse factor on both
+          const R ss = neg ? -s : s;
+          rot(u, w, c, ss);
+          prow[e1] = u;
+          prow[e2] = w;
+          rot(lu, lw, c, ss);
+          lrow[e1] = lu;
+          lrow[e2] = lw;
+        }
+      } else {
+        const R ts = neg ? -tc : tc;
+        part += ts * (u.x * w.x + u.y * w.y);
+        if constexpr (K == RH_LAM) {
+          T2 lu = lrow[e1], lw = lrow[e2];
+          lu.x += ts * w.x; lu.y += ts * w.y;
+          lw.x += ts * u.x; lw.y += ts * u.y;
+          lrow[e1] = lu;
+          lrow[e2] = lw;
+        }
+      }
+    }
+  }
+  return part;
+}
+
+// Diagonal value (real, or phase) of an element: on-site terms only (ny =
+// 1 or 2 byte tables of the double-occupancy pattern), or the general form.
+template <typename R, typename T2>
+struct DiagVal {
+  const DiagOpDev* d;
+  int ny;
+  __device__ __forceinline__ R real(const R* rtab, uint32_t x, int s, uint32_t upm) const {
+    if (ny) {
+      const uint32_t y = x & (x >> s) & upm;
+      R v = rtab[1024 + (y & 255u)];
+      if (ny == 2) v += rtab[1280 + ((y >> 8) & 255u)];
+      return v;
+    }
+    return diag_real<R, true>(*d, rtab, x, s, upm);
+  }
+  __device__ __forceinline__ T2 phase(const T2* ptab, uint32_t x, int s, uint32_t upm) const {
+    if (ny) {
+      const uint32_t y = x & (x >> s) & upm;
+      T2 p = ptab[1024 + (y & 255u)];
+      if (ny == 2) p = cmul(p, ptab[1280 + ((y >> 8) & 255u)]);
+      return p;
+    }
+    return diag_phase<T2, true>(*d, ptab, x, s, upm);
+  }
+};
 
 template <typename R>
 __global__ void __launch_bounds__(kRowThreads, 2) rows_kernel(const RowArgs a) {
@@ -175,97 +285,92 @@ __global__ void __launch_bounds__(kRowThreads, 2) rows_kernel(const RowArgs a) {
     for (int oi = a.op_begin; oi < a.op_end; ++oi) {
       const SmallOpDev op = a.ops[oi];
       R part = 0, npart = 0;
-      if (op.kind == OP_GIV || op.kind == OP_MEAS_HOP || op.kind == OP_LAM_HOP || op.kind == OP_GRAD_HOP) {
+      if (op.kind == OP_GIV || op.kind == OP_MEAS_HOP || op.kind == OP_LAM_HOP || op.kind == OP_GRAD_HOP ||
+          op.kind == OP_GRADINV_HOP) {
         R c = 0, s = 0, tc = 0;
-        if (op.kind == OP_GIV) {
+        if (op.kind == OP_GIV || op.kind == OP_GRADINV_HOP) {
           const T2 gq = cs[op.gate];
           c = gq.x;
           s = (op.flags & OPF_INV) ? -gq.y : gq.y;
-        } else {
-          tc = hc[op.hterm];
         }
+        if (op.kind != OP_GIV) tc = hc[op.hterm];
         const bool dol = (op.flags & OPF_LAM) != 0;
         // the row's part of the Jordan-Wigner parity (the in-row part is
-        // bit 31 of the pair entry); pair entries are loaded four at a time
+        // bit 31 of the pair entry)
         const uint32_t rpar = (uint32_t)__popc(xr & op.between) & 1u;
         const uint32_t* pl = a.pairs + op.a;
-        for (int it0 = tid; it0 < op.b; it0 += 4 * nth) {
-          uint32_t prs[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int it = it0 + k * nth;
-            prs[k] = it < op.b ? __ldg(pl + it) : 0u;
-          }
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-          if (it0 + k * nth >= op.b) break;
-          const uint32_t pr = prs[k];
-          const int e1 = (int)(pr & 0xffffu), e2 = (int)((pr >> 16) & 0x7fffu);
-          const bool neg = ((pr >> 31) ^ rpar) != 0;
-          T2 u = prow[e1], w = prow[e2];
-          if (op.kind == OP_GIV) {
-            const R ss = neg ? -s : s;
-            rot(u, w, c, ss);
-            prow[e1] = u;
-            prow[e2] = w;
-            if (dol) {
-              T2 lu = lrow[e1], lw = lrow[e2];
-              rot(lu, lw, c, ss);
-              lrow[e1] = lu;
-              lrow[e2] = lw;
-            }
-          } else {
-            const R ts = neg ? -tc : tc;
-            if (op.kind == OP_GRAD_HOP) {
-              const T2 lu = lrow[e1], lw = lrow[e2];
-              part += ts * ((lu.x * w.y - lu.y * w.x) + (lw.x * u.y - lw.y * u.x));
-            } else {
-              part += ts * (u.x * w.x + u.y * w.y);
-              if (op.kind == OP_LAM_HOP) {
-                T2 lu = lrow[e1], lw = lrow[e2];
-                lu.x += ts * w.x; lu.y += ts * w.y;
-                lw.x += ts * u.x; lw.y += ts * u.y;
-                lrow[e1] = lu;
-                lrow[e2] = lw;
-              }
-            }
-          }
-          }
+        switch (op.kind) {
+          case OP_GIV:
+            if (dol) row_hop<RH_GIV, true>(prow, lrow, pl, op.b, rpar, c, s, tc);
+            else row_hop<RH_GIV, false>(prow, lrow, pl, op.b, rpar, c, s, tc);
+            break;
+          case OP_MEAS_HOP: part = row_hop<RH_MEAS, false>(prow, lrow, pl, op.b, rpar, c, s, tc); break;
+          case OP_LAM_HOP: part = row_hop<RH_LAM, false>(prow, lrow, pl, op.b, rpar, c, s, tc); break;
+          case OP_GRADINV_HOP: part = row_hop<RH_GRADINV, true>(prow, lrow, pl, op.b, rpar, c, s, tc); break;
+          default: part = row_hop<RH_GRAD, false>(prow, lrow, pl, op.b, rpar, c, s, tc); break;
         }
-        if (op.kind == OP_GRAD_HOP) row_add(acc, a.n_slots, op.slot, (R)2 * part);
+        if (op.kind == OP_GRAD_HOP || op.kind == OP_GRADINV_HOP) row_add(acc, a.n_slots, op.slot, (R)2 * part);
         else if (op.kind != OP_GIV) eacc.add((R)2 * part);
       } else {   // diagonal operations
-        const DiagOpDev& d = a.diag_ops[op.a];
-        const T2* ptab = ptabs + (size_t)b * a.phase_stride + d.phase_off;
-        const R* rtab = rtabs + (size_t)inst * a.real_stride + d.real_off;
+        const DiagOpDev* dp = a.diag_ops + op.a;
+        const int hx = __ldg(&dp->has_x), hy = __ldg(&dp->has_y), nvb = __ldg(&dp->n_vb);
+        const DiagVal<R, T2> dv{dp, (hx == 0 && nvb == 0 && (hy == 1 || hy == 2)) ? hy : 0};
+        const T2* ptab = ptabs + (size_t)b * a.phase_stride + __ldg(&dp->phase_off);
+        const R* rtab = rtabs + (size_t)inst * a.real_stride + __ldg(&dp->real_off);
         const bool inv = (op.flags & OPF_INV) != 0, dol = (op.flags & OPF_LAM) != 0;
-        for (int e = tid; e < len; e += nth) {
-          const uint32_t x = xr | __ldg(a.xin + e);
-          if (op.kind == OP_DIAG) {
-            T2 p = diag_phase<T2, true>(d, ptab, x, a.s, upm);
-            if (inv) p.y = -p.y;
-            prow[e] = cmul(prow[e], p);
-            if (dol) lrow[e] = cmul(lrow[e], p);
-          } else {
-            const R dv = diag_real<R, true>(d, rtab, x, a.s, upm);
-            const T2 u = prow[e];
-            if (op.kind == OP_GRAD_DIAG) {
-              const T2 l = lrow[e];
-              part += dv * (l.x * u.y - l.y * u.x);
-            } else {
-              const R m2 = u.x * u.x + u.y * u.y;
-              part += dv * m2;
-              npart += m2;
-              if (op.kind == OP_LAM_DIAG) {
-                T2 l = lrow[e];
-                l.x += dv * u.x;
-                l.y += dv * u.y;
-                lrow[e] = l;
-              }
+        const uint32_t* __restrict__ xin = a.xin;
+        switch (op.kind) {
+          case OP_DIAG:
+            for (int e = tid; e < len; e += nth) {
+              T2 p = dv.phase(ptab, xr | __ldg(xin + e), a.s, upm);
+              if (inv) p.y = -p.y;
+              prow[e] = cmul(prow[e], p);
+              if (dol) lrow[e] = cmul(lrow[e], p);
             }
-          }
+            break;
+          case OP_GRAD_DIAG:
+            for (int e = tid; e < len; e += nth) {
+              const R v = dv.real(rtab, xr | __ldg(xin + e), a.s, upm);
+              const T2 u = prow[e], l = lrow[e];
+              part += v * (l.x * u.y - l.y * u.x);
+            }
+            break;
+          case OP_GRADINV_DIAG:   // the gradient term, then the inverse phase on both
+            for (int e = tid; e < len; e += nth) {
+              const uint32_t x = xr | __ldg(xin + e);
+              const R v = dv.real(rtab, x, a.s, upm);
+              T2 p = dv.phase(ptab, x, a.s, upm);
+              if (inv) p.y = -p.y;
+              const T2 u = prow[e], l = lrow[e];
+              part += v * (l.x * u.y - l.y * u.x);
+              prow[e] = cmul(u, p);
+              lrow[e] = cmul(l, p);
+            }
+            break;
+          case OP_LAM_DIAG:
+            for (int e = tid; e < len; e += nth) {
+              const R v = dv.real(rtab, xr | __ldg(xin + e), a.s, upm);
+              const T2 u = prow[e];
+              const R m2 = u.x * u.x + u.y * u.y;
+              part += v * m2;
+              npart += m2;
+              T2 l = lrow[e];
+              l.x += v * u.x;
+              l.y += v * u.y;
+              lrow[e] = l;
+            }
+            break;
+          default:   // OP_MEAS_DIAG
+            for (int e = tid; e < len; e += nth) {
+              const R v = dv.real(rtab, xr | __ldg(xin + e), a.s, upm);
+              const T2 u = prow[e];
+              const R m2 = u.x * u.x + u.y * u.y;
+              part += v * m2;
+              npart += m2;
+            }
+            break;
         }
-        if (op.kind == OP_GRAD_DIAG) {
+        if (op.kind == OP_GRAD_DIAG || op.kind == OP_GRADINV_DIAG) {
           row_add(acc, a.n_slots, op.slot, (R)2 * part);
         } else if (op.kind != OP_DIAG) {
           eacc.add(part);
