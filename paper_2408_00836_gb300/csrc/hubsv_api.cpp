@@ -849,7 +849,8 @@ RowPlan* row_plan_for(hub_ansatz* a, int which, int dtype, uint32_t flags, Small
   for (const RowSegHost& g : rp->segs) {
     const int nv = (g.flags & RS_HAS_LAM) ? 2 : 1;
     const int len = g.orient == 0 ? sp->cup : sp->cdn;
-    if ((int)rows_smem_bytes(dtype, nv, len, a->P + 2, a->n_gates, (int)a->hterms.size()) > optin) return nullptr;
+    const int nt = rows_threads(dtype, nv, len, a->P + 2, a->n_gates, (int)a->hterms.size());
+    if ((int)rows_smem_bytes(dtype, nv, len, a->P + 2, a->n_gates, (int)a->hterms.size(), nt) > optin) return nullptr;
   }
   sp_out = sp;
   return rp;
@@ -962,12 +963,14 @@ hub_status run_rows(hub_ansatz* a, SmallPlan* sp, RowPlan* rp, int dtype, const 
     ka.prep.neel_x0 = a->neel_x0;
     ka.prep.sd = (const double*)a->d_sd.p;
     ka.prep.sd32 = (const float*)a->d_sd32.p;
-    const size_t smem = rows_smem_bytes(dtype, has_lam ? 2 : 1, ka.row_len, n_slots, a->n_gates, ka.n_hterms);
-    const int per_sm = std::max(1, rows_max_ctas_per_sm(dtype, smem));
+    const int nv = has_lam ? 2 : 1;
+    const int nt = rows_threads(dtype, nv, ka.row_len, n_slots, a->n_gates, ka.n_hterms);
+    const size_t smem = rows_smem_bytes(dtype, nv, ka.row_len, n_slots, a->n_gates, ka.n_hterms, nt);
+    const int per_sm = std::max(1, rows_max_ctas_per_sm(dtype, nt, smem));
     const int64_t grid = std::min<int64_t>(batch * (int64_t)ka.n_rows, (int64_t)sms * per_sm);
     hub_ansatz::ProfRec rec{};
     HUB_CUDA(record(rec, true), "cudaEventRecord");
-    HUB_CUDA(launch_rows(dtype, ka, (int)grid, smem, st), "row kernel launch");
+    HUB_CUDA(launch_rows(dtype, ka, nt, (int)grid, smem, st), "row kernel launch");
     rec.nv = 3;
     rec.dtype = dtype;
     const int io = ((g.flags & RS_PREP) ? 0 : 1) + ((g.flags & RS_WRITE_PSI) ? 1 : 0) +

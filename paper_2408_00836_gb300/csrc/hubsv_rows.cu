@@ -27,8 +27,14 @@
 namespace hubsv {
 
 namespace {
-constexpr int kRowThreads = 512;
-constexpr int kRowWarps = kRowThreads / 32;
+// Row kernels come in CTAs of 256 threads (three or four per SM, where the
+// rows are short enough) and of 512 threads (two per SM, or one for the
+// longest rows with lam): many small CTAs hide the barrier between
+// operations best, but one or two CTAs on an SM need more warps each
+// (measured: 256-thread CTAs everywhere are 19 % slower at 32 qubits and
+// 19 % faster at 28).
+constexpr int kRowThreadsSmall = 256;
+constexpr int kRowThreadsLarge = 512;
 }  // namespace
 
 // The row segments of a call kind: the operations of the on-chip plan
@@ -117,12 +123,12 @@ double row_plan_bytes(const SmallPlan* sp, const RowPlan* rp, int dtype, int* n_
   return bytes;
 }
 
-size_t rows_smem_bytes(int dtype, int nv, int row_len, int n_slots, int n_gates, int n_hterms) {
+size_t rows_smem_bytes(int dtype, int nv, int row_len, int n_slots, int n_gates, int n_hterms, int threads) {
   const size_t amp = dtype == 0 ? 8 : 16;
   size_t s = (size_t)nv * (size_t)row_len * amp;            // rows of psi (, lam)
   s = (s + 15) & ~(size_t)15;
   s += amp * (size_t)n_gates;                               // (cos, sin) of the element
-  s += 8 * (size_t)kRowWarps * (size_t)n_slots;             // accumulator rows
+  s += 8 * (size_t)(threads / 32) * (size_t)n_slots;        // accumulator rows, one per warp
   s += amp / 2 * (size_t)n_hterms;                          // -t of the element's instance
   return (s + 15) & ~(size_t)15;
 }
@@ -221,8 +227,9 @@ struct DiagVal {
   }
 };
 
-template <typename R>
-__global__ void __launch_bounds__(kRowThreads, 2) rows_kernel(const RowArgs a) {
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : 2) rows_kernel(const RowArgs a) {
+  constexpr int kRowWarps = NT / 32;
   using T2 = typename CT<R>::T2;
   constexpr int DT = CT<R>::DT;
   using AccT = typename std::conditional<DT == 0, float2, double>::type;
@@ -425,20 +432,35 @@ __global__ void __launch_bounds__(256) transpose_kernel(const T2* __restrict__ i
 
 }  // namespace
 
-cudaError_t launch_rows(int dtype, const RowArgs& a, int grid, size_t smem, cudaStream_t st) {
-  const void* f = dtype == 0 ? (const void*)rows_kernel<float> : (const void*)rows_kernel<double>;
+namespace {
+const void* rows_fn(int dtype, int threads) {
+  if (threads == kRowThreadsSmall)
+    return dtype == 0 ? (const void*)rows_kernel<float, kRowThreadsSmall>
+                      : (const void*)rows_kernel<double, kRowThreadsSmall>;
+  return dtype == 0 ? (const void*)rows_kernel<float, kRowThreadsLarge>
+                    : (const void*)rows_kernel<double, kRowThreadsLarge>;
+}
+}  // namespace
+
+int rows_threads(int dtype, int nv, int row_len, int n_slots, int n_gates, int n_hterms) {
+  const size_t s = rows_smem_bytes(dtype, nv, row_len, n_slots, n_gates, n_hterms, kRowThreadsSmall);
+  return 3 * (s + 1024) <= (size_t)228 * 1024 ? kRowThreadsSmall : kRowThreadsLarge;
+}
+
+cudaError_t launch_rows(int dtype, const RowArgs& a, int threads, int grid, size_t smem, cudaStream_t st) {
+  const void* f = rows_fn(dtype, threads);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   RowArgs ac = a;
   void* args[] = {(void*)&ac};
-  return cudaLaunchKernel(f, dim3(grid), dim3(kRowThreads), args, smem, st);
+  return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, st);
 }
 
-int rows_max_ctas_per_sm(int dtype, size_t smem) {
-  const void* f = dtype == 0 ? (const void*)rows_kernel<float> : (const void*)rows_kernel<double>;
+int rows_max_ctas_per_sm(int dtype, int threads, size_t smem) {
+  const void* f = rows_fn(dtype, threads);
   if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kRowThreads, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) != cudaSuccess) return 0;
   return n;
 }
 
