@@ -5,15 +5,20 @@ Hubbard HVA statevector engine on one GB300 (replicas on N GPUs).
 Default workload: grid4x4 -- 4x4 open Hubbard lattice, 32 qubits (2^32
 amplitudes, 34.4 GB per complex64 vector), N_up = N_dn = 8, t and U with
 seeded +-10% inhomogeneity, U = 8, 4 HVA layers x 5 groups (20 parameters),
-U = 0 Slater-determinant start generated inside the first sweep, complex64
-amplitudes with FP64 reductions.  One step = one energy + adjoint gradient.
+U = 0 Slater-determinant start generated by the library, complex64
+amplitudes with FP64 totals.  One step = one energy + adjoint gradient, on
+the engine the library picks (``plan.engine``: on chip for sectors that fit
+one CTA, else the row engine over the sector amplitudes in HBM where a row
+fits shared memory, else dense sweeps of the 2^n vector).
 
 Printed: one JSON line (rank 0).  ``value`` = evaluations/s over all ranks
 with inputs resident in HBM; ``e2e`` = the same through the C ABI with the
 parameters copied from pinned host memory and energy + gradient copied back
-every step; ``roofline`` = achieved HBM bandwidth of the dominant kernel
+every step; ``roofline`` = achieved bandwidth of the dominant kernel
 (algorithmic bytes / CUDA-event duration of its launches in the timed
-region); ``cpu_baseline`` = the CPU oracle timed on a bounded sample.
+region); ``dense_sweeps`` = the same evaluation on the dense sweep engine
+(a few steps), where another engine ran; ``cpu_baseline`` = the CPU oracle
+timed on a bounded sample.
 ``--impl reference`` times the oracle alone (the reference arm).
 """
 
@@ -56,9 +61,14 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _kernel_hash():
+def _kernel_hash(kernel_name="sweep_kernel"):
+    """Hash of the sources a kernel family is compiled from (a traffic record
+    taken on other sources is stale)."""
+    files = ["hubsv_sweep.cuh", "hubsv_internal.h"]
+    if kernel_name.startswith("rows_kernel") or kernel_name.startswith("transpose_kernel"):
+        files += ["hubsv_rows.cu", "hubsv_small.h", "hubsv_reduce.cuh"]
     h = hashlib.sha256()
-    for name in ("hubsv_sweep.cuh", "hubsv_internal.h"):
+    for name in files:
         with open(os.path.join(ROOT, "paper_2408_00836_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -74,7 +84,7 @@ def _traffic(kernel_name, workload, dtype):
     except Exception:
         return None
     e = d.get(f"{kernel_name}|{workload}|{dtype}")
-    if not e or e.get("kernel_hash") != _kernel_hash():
+    if not e or e.get("kernel_hash") != _kernel_hash(kernel_name):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -374,11 +384,45 @@ def run_gpu(args, rank, world, dist):
         out["config"]["log2_tile"] = args.tile
     if args.runs:
         out["config"]["log2_run"] = args.runs
+    if rows_engine and not args.sweeps:
+        out["dense_sweeps"] = run_sweeps_leg(args, a, H, torch, theta, psi, lam, E, g, dtype, batch, names)
     del psi, lam
     torch.cuda.empty_cache()
     if args.c128 and dtype == H.C64 and rank == 0:
         out["c128"] = run_c128(args, w, a, H, torch, dev, theta, ms_step)
     return out
+
+
+def run_sweeps_leg(args, a, H, torch, theta, psi, lam, E, g, dtype, batch, names):
+    """The same evaluation on the dense sweep engine (HUB_FLAG_SWEEPS): the
+    2^n-amplitude vectors in HBM, a few steps, for comparison."""
+    steps = max(1, min(args.steps, 2))
+    a.energy_grad(theta, psi, lam, E, g, dtype=dtype, batch=batch, sweeps=True)   # warm-up
+    torch.cuda.synchronize()
+    H.profile(a, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        a.energy_grad(theta, psi, lam, E, g, dtype=dtype, batch=batch, sweeps=True)
+    e1.record()
+    torch.cuda.synchronize()
+    recs = H.profile_read(a)
+    H.profile(a, False)
+    ms = e0.elapsed_time(e1) / steps
+    agg = {}
+    for nv, dt, by, t in recs:
+        s = agg.setdefault(names[(nv, dt)], [0, 0.0, 0.0])
+        s[0] += 1
+        s[1] += by
+        s[2] += t
+    dom = max(agg.items(), key=lambda kv: kv[1][2])
+    peak, peak_kind = _peaks()
+    ach = dom[1][1] / (dom[1][2] / 1e3) / 1e9
+    return {"value": round(batch * 1e3 / ms, 4), "unit": "evals/s", "ms_per_step": round(ms, 3),
+            "steps": steps, "energy": float(E[0].item()),
+            "hbm_bytes_per_eval": sum(v[1] for v in agg.values()) / steps / batch,
+            "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": round(ach, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": peak_kind}}
 
 
 def run_c128(args, w, a, H, torch, dev, theta, ms_c64):

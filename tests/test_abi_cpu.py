@@ -209,3 +209,24 @@ def test_sector_plan_bytes(number):
         dense = a.plan_stats(1, dtype, fused=False)[1]
         assert dense == sum(sum(1 for bit in (2, 4, 16, 32, 64) if (fl & 0xFFFF) & bit)
                             for _, fl, _ in a.plan_describe(1, dtype, flags=0)) * (1 << n) * amp
+
+
+@pytest.mark.parametrize("number", [2, 4, 5])
+def test_row_plan_bytes(number):
+    """The row engine moves whole sector matrices: its bytes per state are a
+    whole number of C(L, N_up) C(L, N_dn) amplitude matrices (row sweeps and
+    transposes), far fewer than the dense sweeps move."""
+    from math import comb
+    w = H.workloads.workload(number, batch_sets=1)
+    bonds, cls = H.square_lattice(w.nx, w.ny, w.order)
+    t, U, V = w.coefficients(bonds)
+    m = H.Model(w.n_sites, bonds, t, U, V if w.V else None, w.n_up, w.n_dn)
+    a = H.Ansatz(m, H.hva_groups(bonds, cls, w.n_sites, w.layers, w.classes), w.layers)
+    C = comb(w.n_sites, w.n_up) * comb(w.n_sites, w.n_dn)
+    for which in (0, 1):
+        for dtype, amp in ((H.C64, 8), (H.C128, 16)):
+            launches, by = a.plan_stats(which, dtype, rows=True)
+            units = by / (C * amp)
+            assert launches >= 1 and abs(units - round(units)) < 1e-9 and round(units) >= 1
+            if w.n_qubits >= 28:
+                assert by < a.plan_stats(which, dtype)[1] / 10
