@@ -28,9 +28,10 @@ class EnergyGradGraph:
     """
 
     def __init__(self, ans: Ansatz, dtype: int = C64, batch: int = 1, ckpt: bool = False,
-                 use_graph: bool = True):
+                 use_graph: bool = True, sweeps: bool = False, rows: bool = False):
         import torch
         self.torch = torch
+        self.sweeps, self.rows = sweeps, rows   # engine selection (see Ansatz.energy_grad)
         self.ans, self.dtype, self.batch = ans, dtype, batch
         td = torch.complex64 if dtype == C64 else torch.complex128
         dev = torch.device("cuda", torch.cuda.current_device())
@@ -62,7 +63,7 @@ class EnergyGradGraph:
 
     def _call(self):
         self.ans.energy_grad(self.theta, self.psi, self.lam, self.E, self.g, ckpt=self.ckpt,
-                             dtype=self.dtype, batch=self.batch)
+                             dtype=self.dtype, batch=self.batch, sweeps=self.sweeps, rows=self.rows)
 
     def __call__(self, theta: np.ndarray):
         torch = self.torch
