@@ -849,8 +849,10 @@ RowPlan* row_plan_for(hub_ansatz* a, int which, int dtype, uint32_t flags, Small
   for (const RowSegHost& g : rp->segs) {
     const int nv = (g.flags & RS_HAS_LAM) ? 2 : 1;
     const int len = g.orient == 0 ? sp->cup : sp->cdn;
-    const int nt = rows_threads(dtype, nv, len, a->P + 2, a->n_gates, (int)a->hterms.size());
-    if ((int)rows_smem_bytes(dtype, nv, len, a->P + 2, a->n_gates, (int)a->hterms.size(), nt) > optin) return nullptr;
+    const int no = g.op_end - g.op_begin;
+    const int nt = rows_threads(dtype, nv, len, a->P + 2, a->n_gates, (int)a->hterms.size(), no);
+    if ((int)rows_smem_bytes(dtype, nv, len, a->P + 2, a->n_gates, (int)a->hterms.size(), nt, no) > optin)
+      return nullptr;
   }
   sp_out = sp;
   return rp;
@@ -964,8 +966,9 @@ hub_status run_rows(hub_ansatz* a, SmallPlan* sp, RowPlan* rp, int dtype, const 
     ka.prep.sd = (const double*)a->d_sd.p;
     ka.prep.sd32 = (const float*)a->d_sd32.p;
     const int nv = has_lam ? 2 : 1;
-    const int nt = rows_threads(dtype, nv, ka.row_len, n_slots, a->n_gates, ka.n_hterms);
-    const size_t smem = rows_smem_bytes(dtype, nv, ka.row_len, n_slots, a->n_gates, ka.n_hterms, nt);
+    const int no = g.op_end - g.op_begin;
+    const int nt = rows_threads(dtype, nv, ka.row_len, n_slots, a->n_gates, ka.n_hterms, no);
+    const size_t smem = rows_smem_bytes(dtype, nv, ka.row_len, n_slots, a->n_gates, ka.n_hterms, nt, no);
     const int per_sm = std::max(1, rows_max_ctas_per_sm(dtype, nt, smem));
     const int64_t grid = std::min<int64_t>(batch * (int64_t)ka.n_rows, (int64_t)sms * per_sm);
     hub_ansatz::ProfRec rec{};

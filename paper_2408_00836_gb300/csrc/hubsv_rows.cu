@@ -123,10 +123,12 @@ double row_plan_bytes(const SmallPlan* sp, const RowPlan* rp, int dtype, int* n_
   return bytes;
 }
 
-size_t rows_smem_bytes(int dtype, int nv, int row_len, int n_slots, int n_gates, int n_hterms, int threads) {
+size_t rows_smem_bytes(int dtype, int nv, int row_len, int n_slots, int n_gates, int n_hterms, int threads,
+                       int n_ops) {
   const size_t amp = dtype == 0 ? 8 : 16;
   size_t s = (size_t)nv * (size_t)row_len * amp;            // rows of psi (, lam)
   s = (s + 15) & ~(size_t)15;
+  s += sizeof(SmallOpDev) * (size_t)n_ops;                  // the segment's operations
   s += amp * (size_t)n_gates;                               // (cos, sin) of the element
   s += 8 * (size_t)(threads / 32) * (size_t)n_slots;        // accumulator rows, one per warp
   s += amp / 2 * (size_t)n_hterms;                          // -t of the element's instance
@@ -239,7 +241,9 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : 2) rows_kerne
   T2* prow = reinterpret_cast<T2*>(smem_raw);
   T2* lrow = prow + len;
   const size_t rows_b = (((size_t)(has_lam ? 2 : 1) * (size_t)len * sizeof(T2)) + 15) & ~(size_t)15;
-  T2* cs = reinterpret_cast<T2*>(smem_raw + rows_b);
+  SmallOpDev* sops = reinterpret_cast<SmallOpDev*>(smem_raw + rows_b);
+  const int n_ops = a.op_end - a.op_begin;
+  T2* cs = reinterpret_cast<T2*>(sops + n_ops);
   AccT* acc = reinterpret_cast<AccT*>(cs + a.n_gates);   // [kRowWarps][n_slots]
   R* hc = reinterpret_cast<R*>(acc + kRowWarps * a.n_slots);
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -252,6 +256,12 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : 2) rows_kerne
   T2* lam = reinterpret_cast<T2*>(a.lam);
   const bool meas = (a.flags & RS_MEAS) != 0;
 
+  {   // the segment's operation records, read by every thread for every row
+    const int4* src = reinterpret_cast<const int4*>(a.ops + a.op_begin);
+    int4* dst = reinterpret_cast<int4*>(sops);
+    const int nw = n_ops * (int)(sizeof(SmallOpDev) / sizeof(int4));
+    for (int i = tid; i < nw; i += nth) dst[i] = src[i];
+  }
   const int64_t total = a.batch * (int64_t)a.n_rows;
   int64_t cur_b = -1;
   for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
@@ -289,8 +299,8 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : 2) rows_kerne
     }
     __syncthreads();
     Tot<R> eacc, nacc;
-    for (int oi = a.op_begin; oi < a.op_end; ++oi) {
-      const SmallOpDev op = a.ops[oi];
+    for (int oi = 0; oi < n_ops; ++oi) {
+      const SmallOpDev op = sops[oi];
       R part = 0, npart = 0;
       if (op.kind == OP_GIV || op.kind == OP_MEAS_HOP || op.kind == OP_LAM_HOP || op.kind == OP_GRAD_HOP ||
           op.kind == OP_GRADINV_HOP) {
@@ -442,8 +452,8 @@ const void* rows_fn(int dtype, int threads) {
 }
 }  // namespace
 
-int rows_threads(int dtype, int nv, int row_len, int n_slots, int n_gates, int n_hterms) {
-  const size_t s = rows_smem_bytes(dtype, nv, row_len, n_slots, n_gates, n_hterms, kRowThreadsSmall);
+int rows_threads(int dtype, int nv, int row_len, int n_slots, int n_gates, int n_hterms, int n_ops) {
+  const size_t s = rows_smem_bytes(dtype, nv, row_len, n_slots, n_gates, n_hterms, kRowThreadsSmall, n_ops);
   return 3 * (s + 1024) <= (size_t)228 * 1024 ? kRowThreadsSmall : kRowThreadsLarge;
 }
 
