@@ -32,9 +32,11 @@ namespace {
 // longest rows with lam): many small CTAs hide the barrier between
 // operations best, but one or two CTAs on an SM need more warps each
 // (measured: 256-thread CTAs everywhere are 19 % slower at 32 qubits and
-// 19 % faster at 28).
+// 19 % faster at 28).  A c64 CTA alone on its SM takes 1024 threads (2 %
+// faster at 32 qubits; the c128 one at 28 qubits is 11 % slower so).
 constexpr int kRowThreadsSmall = 256;
 constexpr int kRowThreadsLarge = 512;
+constexpr int kRowThreadsSolo = 1024;   // a c64 CTA alone on its SM (the longest rows with lam)
 }  // namespace
 
 // The row segments of a call kind: the operations of the on-chip plan
@@ -230,7 +232,8 @@ struct DiagVal {
 };
 
 template <typename R, int NT>
-__global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : 2) rows_kernel(const RowArgs a) {
+__global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowThreadsLarge ? 2 : 1))
+    rows_kernel(const RowArgs a) {
   constexpr int kRowWarps = NT / 32;
   using T2 = typename CT<R>::T2;
   constexpr int DT = CT<R>::DT;
@@ -444,6 +447,9 @@ __global__ void __launch_bounds__(256) transpose_kernel(const T2* __restrict__ i
 
 namespace {
 const void* rows_fn(int dtype, int threads) {
+  if (threads == kRowThreadsSolo)
+    return dtype == 0 ? (const void*)rows_kernel<float, kRowThreadsSolo>
+                      : (const void*)rows_kernel<double, kRowThreadsSolo>;
   if (threads == kRowThreadsSmall)
     return dtype == 0 ? (const void*)rows_kernel<float, kRowThreadsSmall>
                       : (const void*)rows_kernel<double, kRowThreadsSmall>;
@@ -454,7 +460,10 @@ const void* rows_fn(int dtype, int threads) {
 
 int rows_threads(int dtype, int nv, int row_len, int n_slots, int n_gates, int n_hterms, int n_ops) {
   const size_t s = rows_smem_bytes(dtype, nv, row_len, n_slots, n_gates, n_hterms, kRowThreadsSmall, n_ops);
-  return 3 * (s + 1024) <= (size_t)228 * 1024 ? kRowThreadsSmall : kRowThreadsLarge;
+  if (3 * (s + 1024) <= (size_t)228 * 1024) return kRowThreadsSmall;
+  const size_t sl = rows_smem_bytes(dtype, nv, row_len, n_slots, n_gates, n_hterms, kRowThreadsLarge, n_ops);
+  if (2 * (sl + 1024) <= (size_t)228 * 1024 || dtype != 0) return kRowThreadsLarge;
+  return kRowThreadsSolo;
 }
 
 cudaError_t launch_rows(int dtype, const RowArgs& a, int threads, int grid, size_t smem, cudaStream_t st) {

@@ -115,7 +115,8 @@ struct RowArgs {
 // rows and the -t values.
 size_t rows_smem_bytes(int dtype, int nv, int row_len, int n_slots, int n_gates, int n_hterms, int threads,
                        int n_ops);
-// Threads per CTA of a row sweep (256 where three such CTAs fit an SM, else 512).
+// Threads per CTA of a row sweep (256 where three such CTAs fit an SM, 1024
+// for a c64 CTA alone on its SM, else 512).
 int rows_threads(int dtype, int nv, int row_len, int n_slots, int n_gates, int n_hterms, int n_ops);
 cudaError_t launch_rows(int dtype, const RowArgs& a, int threads, int grid, size_t smem, cudaStream_t st);
 int rows_max_ctas_per_sm(int dtype, int threads, size_t smem);
