@@ -179,13 +179,18 @@ HUB_API hub_status energy(ans_t ans, const double* theta, void* psi, double* E,
  * backward un-computation).  grad: device double [batch][P], overwritten.
  * psi and lam are clobbered.
  *
- * Engines (energy and energy_grad alike): with HUB_FLAG_PREP_FUSED, without
- * HUB_FLAG_KEEP_STATE or HUB_FLAG_SWEEPS, and when the (N_up, N_dn) sector's
- * C(L, N_up) * C(L, N_dn) amplitudes of psi and lam fit in one CTA's shared
- * memory, each batch element runs on chip in one CTA and psi, lam and ckpt
- * are not touched (their contents are then unspecified, as always); results
- * agree with the sweep engine to the rounding of the dtype.  Otherwise the
- * call runs as HBM sweeps over psi (and lam, ckpt).                         */
+ * Engines (energy and energy_grad alike).  With HUB_FLAG_PREP_FUSED and
+ * without HUB_FLAG_KEEP_STATE / HUB_FLAG_SWEEPS, only the (N_up, N_dn)
+ * sector's C = C(L, N_up) * C(L, N_dn) amplitudes can be nonzero, and the
+ * call runs (1) on chip, one CTA per batch element, when psi and lam of
+ * that size fit one CTA's shared memory (not with HUB_FLAG_ROWS); else
+ * (2) on the row engine, when a row of the C_dn x C_up sector matrix (with
+ * lam where the call builds it) fits shared memory and 2 C <= 2^n: the
+ * sector matrices and their transposes then live in the first
+ * 2 * batch * C amplitudes of each of psi and lam, and ckpt is unused;
+ * else (3) as HBM sweeps over the dense psi (and lam, ckpt).  Results agree
+ * across engines to the rounding of the dtype; the contents of psi, lam and
+ * ckpt on return are unspecified in every case.                            */
 HUB_API hub_status energy_grad(ans_t ans, const double* theta, void* psi, void* lam,
                        void* ckpt, double* E, double* grad, int32_t dtype,
                        int64_t batch, uint32_t flags, hub_stream_t stream);
