@@ -239,6 +239,9 @@ HUB_API hub_status ans_plan_stats(ans_t ans, int32_t which, int32_t dtype,
  * per diagonal group); then the H terms (one per bond and spin, bonds in
  * lattice order, up before down) and H's diagonal; then (energy_grad) for
  * each factor in reverse order its gradient step followed by its inverse.
+ * With HUB_FLAG_ROWS in flags (energy and energy_grad): the row engine's
+ * segments instead, each as [mask of the modes of its spin, orientation
+ * (0 up, 1 down), n_ops, sequence indices].
  * With buf == NULL only *len is set.                                        */
 HUB_API hub_status ans_plan_describe(ans_t ans, int32_t which, int32_t dtype,
                                      uint32_t flags, int64_t* buf, int32_t cap,

@@ -233,7 +233,9 @@ class Ansatz:
         return ns.value, by.value
 
     def plan_describe(self, which: int, dtype=C64, flags: int = FLAG_PREP_FUSED):
-        """[(tile_mask, sweep_flags, [sequence indices])] of a call kind."""
+        """[(tile_mask, sweep_flags, [sequence indices])] of a call kind (with
+        FLAG_ROWS in flags: the row engine's segments, (spin mode mask,
+        orientation, [sequence indices]))."""
         n = ctypes.c_int32(0)
         check(lib().ans_plan_describe(self._h, which, dtype, flags, None, 0, ctypes.byref(n)))
         buf = (ctypes.c_int64 * n.value)()

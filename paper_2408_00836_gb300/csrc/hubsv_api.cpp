@@ -1148,10 +1148,33 @@ extern "C" hub_status ans_plan_describe(ans_t a, int32_t which, int32_t dtype, u
                                         int32_t cap, int32_t* len) {
   if (!a || !len || which < 0 || which > 2 || (dtype != HUB_C64 && dtype != HUB_C128))
     return fail(HUB_EINVAL, "ans_plan_describe: bad arguments");
+  std::vector<int64_t> out;
+  if (flags & HUB_FLAG_ROWS) {   // the row engine's segments: tile = the modes of one spin
+    if (which > 1) return fail(HUB_EINVAL, "ans_plan_describe: the row engine runs energy and energy_grad only");
+    uint64_t upm = 0, dnm = 0;
+    for (int i = 0; i < a->L; ++i) {
+      upm |= 1ull << a->models[0]->up[i];
+      dnm |= 1ull << a->models[0]->dn[i];
+    }
+    const std::vector<RowSched> sched = row_schedule(a, which);
+    out.push_back((int64_t)sched.size());
+    for (const RowSched& rs : sched) {
+      if (rs.orient < 0) return fail(HUB_EUNSUPPORTED, "ans_plan_describe: no row schedule");
+      out.push_back((int64_t)(rs.orient == 0 ? upm : dnm));
+      out.push_back((int64_t)rs.orient);
+      out.push_back((int64_t)rs.ops.size());
+      for (int id : rs.ops) out.push_back(id);
+    }
+    *len = (int32_t)out.size();
+    if (buf) {
+      if (cap < (int32_t)out.size()) return fail(HUB_EINVAL, "ans_plan_describe: buffer too small");
+      std::copy(out.begin(), out.end(), buf);
+    }
+    return HUB_OK;
+  }
   Plan* pl;
   hub_status s = get_plan(a, which, dtype, flags, pl);
   if (s != HUB_OK) return s;
-  std::vector<int64_t> out;
   out.push_back((int64_t)pl->sweeps.size());
   for (size_t i = 0; i < pl->sweeps.size(); ++i) {
     out.push_back((int64_t)pl->tiles[i]);

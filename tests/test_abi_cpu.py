@@ -230,3 +230,25 @@ def test_row_plan_bytes(number):
             assert launches >= 1 and abs(units - round(units)) < 1e-9 and round(units) >= 1
             if w.n_qubits >= 28:
                 assert by < a.plan_stats(which, dtype)[1] / 10
+
+
+@pytest.mark.parametrize("number", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("which", [0, 1])
+def test_row_schedules_are_valid(number, which):
+    """The row engine's regrouped sequence: every operation once, hops inside
+    the spin of their segment, and no two non-commuting operations swapped."""
+    w = H.workloads.workload(number, batch_sets=1)
+    bonds, cls = H.square_lattice(w.nx, w.ny, w.order)
+    t, U, V = w.coefficients(bonds)
+    m = H.Model(w.n_sites, bonds, t, U, V if w.V else None, w.n_up, w.n_dn)
+    groups = H.hva_groups(bonds, cls, w.n_sites, w.layers, w.classes)
+    a = H.Ansatz(m, groups, w.layers)
+    seq = _sequence(groups, bonds, w.n_sites, which)
+    plan = a.plan_describe(which, H.C64, flags=H.FLAG_PREP_FUSED | H.FLAG_ROWS)
+    L = w.n_sites
+    for tile, orient, ids in plan:
+        assert tile == (((1 << L) - 1) << (L if orient else 0))
+    _check_schedule(plan, seq, w.n_qubits, L, 0, set(range(w.n_qubits)))
+    # consecutive segments alternate spins (a repeat would be one segment)
+    for (_, o1, _), (_, o2, _) in zip(plan, plan[1:]):
+        assert o1 != o2
