@@ -156,7 +156,10 @@ HUB_API int32_t ans_num_qubits(ans_t ans);   /* -1 for a NULL handle */
  * largest-magnitude entry (lowest index on a tie) made positive; psi_0 =
  * prod_m b+_{m,up} prod_m b+_{m,dn} |vac>, b+_m = sum_i Phi_im a+_{mode(i)},
  * i.e. det(Phi_up[occ_up]) det(Phi_dn[occ_dn]) times the sign of ordering
- * the creators by mode.  HUB_PREP_NEEL: the checkerboard state of Sec. 2.1,
+ * the creators by mode.  Where the n_up-th and (n_up+1)-th levels (or those
+ * of n_dn) coincide to 1e-9 relative, the determinant is not unique and the
+ * call returns HUB_EINVAL (pass an orb_perturb that splits the levels).
+ * HUB_PREP_NEEL: the checkerboard state of Sec. 2.1,
  * up on site i when neel_up[i] != 0 (host [L]) and down otherwise.
  * Writes batch * 2^n amplitudes to psi (may be NULL: only the tables used by
  * HUB_FLAG_PREP_FUSED are set).                                               */
@@ -198,8 +201,8 @@ HUB_API hub_status energy_grad(ans_t ans, const double* theta, void* psi, void* 
 /* energy() for callers that cannot allocate device memory.  (The paper has
  * no counterpart: this is an interface addition.)  Some callers cannot call
  * cudaMalloc while they compute -- their framework's allocator already owns
- * the free device memory, an allocation would synchronise a latency-critical
- * loop, or the work is being recorded into a CUDA graph.  energy() allocates
+ * the free device memory, or an allocation would synchronise a
+ * latency-critical loop.  energy() allocates
  * its per-call scratch (coefficient and phase tables, FP64 accumulators) and
  * its static tables on first use; energy_noalloc allocates nothing: it puts
  * every table and all scratch in one static device array of
@@ -224,7 +227,9 @@ HUB_API hub_status hub_apply_h(ans_t ans, const void* psi, void* lam, int32_t dt
 
 /* Plan statistics for the last-planned configuration of a call kind (0 =
  * energy, 1 = energy_grad): number of sweeps and HBM bytes moved per batch
- * element (reads + writes of amplitude vectors).  With HUB_FLAG_ROWS in
+ * element (reads + writes of amplitude vectors) of the dense-sweep plan
+ * that the call runs with these flags and no checkpoint buffer
+ * (HUB_FLAG_SWEEPS does not change it).  With HUB_FLAG_ROWS in
  * flags: the row engine's schedule instead (n_sweeps = its row-sweep and
  * transpose launches), whether or not a call would run on it.              */
 HUB_API hub_status ans_plan_stats(ans_t ans, int32_t which, int32_t dtype,

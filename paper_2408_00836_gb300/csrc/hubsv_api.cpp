@@ -1029,6 +1029,20 @@ extern "C" hub_status state_prepare(ans_t a, int32_t kind, const double* orb_per
             return fail(HUB_EINVAL, "state_prepare: orb_perturb must be symmetric");
       std::vector<double> w, v;
       jacobi_eigh(L, h, w, v);
+      // a degenerate Fermi level (the N-th and (N+1)-th levels equal) leaves
+      // the Slater determinant undetermined: any basis of the degenerate
+      // levels is as good, so refuse rather than pick one
+      for (int sp = 0; sp < 2; ++sp) {
+        const int N = sp == 0 ? m->n_up : m->n_dn;
+        if (N > 0 && N < L) {
+          const double gap = w[N] - w[N - 1];
+          const double scale = std::max(1.0, std::max(std::fabs(w[N]), std::fabs(w[N - 1])));
+          if (gap < 1e-9 * scale)
+            return fail(HUB_EINVAL, "state_prepare: degenerate Fermi level (levels " + std::to_string(N - 1) +
+                                        " and " + std::to_string(N) +
+                                        " coincide): the Slater determinant is not unique; pass orb_perturb");
+        }
+      }
       for (int sp = 0; sp < 2; ++sp) {
         const int N = sp == 0 ? m->n_up : m->n_dn;
         for (uint32_t y = 0; y < tl; ++y) {
@@ -1136,8 +1150,10 @@ extern "C" hub_status ans_plan_stats(ans_t a, int32_t which, int32_t dtype, uint
     if (bytes_per_state) *bytes_per_state = by;
     return HUB_OK;
   }
+  // the plan energy / energy_grad run for these flags (without a checkpoint;
+  // HUB_FLAG_SWEEPS selects the engine, not a different sweep plan)
   Plan* pl;
-  hub_status s = get_plan(a, which, dtype, flags, pl);
+  hub_status s = get_plan(a, which, dtype, flags & 3u, pl);
   if (s != HUB_OK) return s;
   if (n_sweeps) *n_sweeps = (int32_t)pl->sweeps.size();
   if (bytes_per_state) *bytes_per_state = pl->bytes_per_state;
@@ -1173,7 +1189,7 @@ extern "C" hub_status ans_plan_describe(ans_t a, int32_t which, int32_t dtype, u
     return HUB_OK;
   }
   Plan* pl;
-  hub_status s = get_plan(a, which, dtype, flags, pl);
+  hub_status s = get_plan(a, which, dtype, flags & 3u, pl);
   if (s != HUB_OK) return s;
   out.push_back((int64_t)pl->sweeps.size());
   for (size_t i = 0; i < pl->sweeps.size(); ++i) {

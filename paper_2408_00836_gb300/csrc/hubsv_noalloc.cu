@@ -2,9 +2,8 @@
 //
 // Some callers cannot call cudaMalloc while they compute: code that runs
 // while another framework owns the device memory pool (its allocator has
-// reserved the free memory), code on a latency-critical path where an
-// allocation would synchronise the device, or code recorded into a CUDA
-// graph, where an allocation cannot be recorded.  energy() allocates its
+// reserved the free memory), or code on a latency-critical path where an
+// allocation would synchronise the device.  energy() allocates its
 // per-call scratch (coefficient and phase tables, the FP64 accumulators)
 // and its static tables on first use; this entry point instead places every
 // table and all scratch in one file-scope device array of fixed size, so a

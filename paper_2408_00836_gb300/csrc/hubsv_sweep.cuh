@@ -34,9 +34,11 @@
 //  * OP_GRAD_*: the per-parameter reductions 2 Im <lam|G|psi> of the
 //    adjoint recursion of Sec. 2.1.
 //
-// Reductions accumulate per thread in the working precision within one tile,
-// are reduced per warp in FP64 and summed per CTA in shared memory; each CTA
-// adds its totals to the global FP64 accumulators once per batch element.
+// Reductions accumulate per thread in the working precision within one tile
+// and are reduced per warp in that precision (c64: FP32 shuffles into
+// per-warp float-pair rows updated with TwoSum; c128: FP64); the rows are
+// summed in FP64 and each CTA adds its totals to the global FP64
+// accumulators once per batch element.
 #pragma once
 #include <type_traits>
 

@@ -3,6 +3,7 @@ exports every declared entry point, the lattice helper agrees with the
 oracle's geometry, argument validation, and the planner's schedules are
 valid reorderings of the operation sequence."""
 
+import ctypes
 import os
 import re
 
@@ -209,6 +210,27 @@ def test_sector_plan_bytes(number):
         dense = a.plan_stats(1, dtype, fused=False)[1]
         assert dense == sum(sum(1 for bit in (2, 4, 16, 32, 64) if (fl & 0xFFFF) & bit)
                             for _, fl, _ in a.plan_describe(1, dtype, flags=0)) * (1 << n) * amp
+
+
+def test_plan_queries_ignore_the_engine_flag():
+    """HUB_FLAG_SWEEPS picks the engine; the dense-sweep plan that energy and
+    energy_grad run (without a checkpoint) is the same with or without it,
+    and plan_stats / plan_describe report that plan."""
+    w = H.workloads.workload(4, batch_sets=1)
+    bonds, cls = H.square_lattice(w.nx, w.ny, w.order)
+    t, U, V = w.coefficients(bonds)
+    m = H.Model(w.n_sites, bonds, t, U, None, w.n_up, w.n_dn)
+    a = H.Ansatz(m, H.hva_groups(bonds, cls, w.n_sites, w.layers, w.classes), w.layers)
+    for which in (0, 1):
+        for dtype in (H.C64, H.C128):
+            base = a.plan_describe(which, dtype, flags=H.FLAG_PREP_FUSED)
+            assert a.plan_describe(which, dtype, flags=H.FLAG_PREP_FUSED | H.FLAG_SWEEPS) == base
+            ns = ctypes.c_int32(0)
+            by = ctypes.c_double(0.0)
+            H.check(H.lib().ans_plan_stats(a.handle, which, dtype, H.FLAG_PREP_FUSED | H.FLAG_SWEEPS,
+                                           ctypes.byref(ns), ctypes.byref(by)))
+            assert (ns.value, by.value) == a.plan_stats(which, dtype, fused=True)
+            assert ns.value == len(base)
 
 
 @pytest.mark.parametrize("number", [2, 4, 5])

@@ -308,6 +308,101 @@ def test_periodicity_for_integer_generators():
     assert abs(O.energy(m, b, groups, t2, psi0, H) - e) > 1e-6
 
 
+def _generator_sum_residual(m, b, groups, vec, terms_fn=None):
+    """|| sum_g G_g vec - H vec || / || H vec || over one layer of groups.
+
+    Under the reading that each generator is its class's Hamiltonian terms
+    with their coefficients and signs (Sec. 2.2.1: the HVA layer of Eq. 7
+    exponentiates the terms of the Hamiltonian), the generators of one layer
+    that covers every term class (on-site U, NN V, potential, and every
+    hopping class) add up to H exactly.  H itself is pinned by the closed
+    forms above (two-site dimer, U = 0 levels, Neel and Hartree-Fock
+    energies) and by the Kronecker-product Jordan-Wigner construction."""
+    cache = {}
+    if terms_fn is None:
+        acc = sum(O.apply_generator(m, b, g, vec, cache) for g in groups)
+    else:
+        acc = np.zeros_like(vec)
+        for g in groups:
+            for piece in terms_fn(m, b, g):
+                acc = acc + (piece[1] * (piece[2] @ vec) if piece[0] == "hop" else piece[1] * vec)
+    ref = O.hamiltonian(m, b) @ vec
+    return float(np.linalg.norm(acc - ref) / np.linalg.norm(ref))
+
+
+def test_layer_generators_sum_to_hamiltonian():
+    """Every group kind's generator carries exactly its Hamiltonian terms:
+    one layer over all term classes sums to H (disordered t, on-site
+    potential, site-dependent U and bond-dependent V, both JW orders)."""
+    for modes in ("blocked", "interleaved"):
+        lat, m = _model_2x3(modes=modes)
+        rng = np.random.default_rng(21)
+        Vm = np.zeros((6, 6))
+        for (i, j) in lat.bonds:
+            Vm[i, j] = Vm[j, i] = 0.5 + 0.3 * rng.standard_normal()
+        m = O.make_model(lat, m.t, m.U, V=Vm, n_up=3, n_dn=2, modes=modes)
+        b = O.sector_basis(m)
+        vec = rng.standard_normal(len(b)) + 1j * rng.standard_normal(len(b))
+        groups = O.hva_groups(lat, 1, ["U", "V", "eps", "h1", "v1", "h2", "v2"])
+        assert _generator_sum_residual(m, b, groups, vec) < 1e-13
+
+
+def test_energy_period_in_theta_V_is_two_pi_over_V():
+    """Uniform integer V: G_V = V sum n_i n_j has eigenvalues V x (integer),
+    so E is 2 pi / V-periodic in theta_V, and (generically) not pi /
+    V-periodic -- which a doubled V coefficient would make it."""
+    lat = O.square_lattice(2, 3)
+    m = O.make_model(lat, 1.0, 4.0, V=2.0, n_up=3, n_dn=3)
+    b = O.sector_basis(m)
+    pu, pd, _ = O.orbitals(m, perturb=np.diag(1e-3 * np.arange(6)))
+    psi0 = O.slater_state(m, pu, pd)
+    H = O.hamiltonian(m, b)
+    groups = O.hva_groups(lat, 2, ["U", "V", "h1", "v1", "h2"])
+    th = np.random.default_rng(8).uniform(-np.pi, np.pi, 10)
+    e = O.energy(m, b, groups, th, psi0, H)
+    for k in (1, 6):                       # the V parameter of each layer
+        t2 = th.copy()
+        t2[k] += 2 * np.pi / 2.0
+        assert abs(O.energy(m, b, groups, t2, psi0, H) - e) < 1e-11
+        t2 = th.copy()
+        t2[k] += np.pi / 2.0
+        assert abs(O.energy(m, b, groups, t2, psi0, H) - e) > 1e-6
+
+
+def _kron_rz_product(n, theta):
+    """prod_k exp(-i theta Z_k / 2) in the full 2^n space, qubit k = bit k,
+    Z = diag(1, -1) on (|0>, |1>): the textbook single-qubit R_z(theta)."""
+    rz = np.diag([np.exp(-0.5j * theta), np.exp(0.5j * theta)])
+    M = np.ones((1, 1), dtype=complex)
+    for _ in range(n):
+        M = np.kron(M, rz)
+    return M
+
+
+def test_rz_group_equals_product_of_single_qubit_rotations():
+    """The 'rz' group (the R_z pre-layer of Sec. 2.2.1) is exp(-i theta
+    sum_k Z_k / 2) = prod_k R_z(theta) on its modes, global phase included
+    (checked against Kronecker products in the full space, on all modes and
+    on a subset)."""
+    lat = O.square_lattice(1, 3)
+    m = O.make_model(lat, 1.0, 2.0)
+    n = m.n_modes
+    b = O.full_basis(m)
+    rng = np.random.default_rng(9)
+    psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    th = 0.7311
+    got = O.apply_group(m, b, O.Group("rz", tuple(range(n)), 0), th, psi)
+    assert np.allclose(got, _kron_rz_product(n, th) @ psi, atol=1e-13)
+    # a subset of modes: R_z on modes 1 and 4 only
+    I2 = np.eye(2)
+    rz = np.diag([np.exp(-0.5j * th), np.exp(0.5j * th)])
+    M = np.ones((1, 1), dtype=complex)
+    for k in range(n - 1, -1, -1):
+        M = np.kron(M, rz if k in (1, 4) else I2)
+    got = O.apply_group(m, b, O.Group("rz", (1, 4), 0), th, psi)
+    assert np.allclose(got, M @ psi, atol=1e-13)
+
+
 def test_energy_and_gradient_invariant_under_mode_order():
     """Blocked, interleaved (the paper's) and snake site orders describe the
     same fermions: E and the gradient agree."""
@@ -398,3 +493,36 @@ def test_mistakes_are_caught():
     #     fixed by FD (tests above).  A wrong factor does not survive:
     e_half, _ = O.lanczos_ground((0.5 * O.hamiltonian(m, b)).tocsr())
     assert abs(e_half - E0) > 1e-3
+    # (3) coefficient slips in the generators of the diagonal groups and of
+    #     the hops: each fails the layer-sum pin or the R_z pin
+    lat2, m2 = _model_2x3()
+    b2 = O.sector_basis(m2)
+    rng = np.random.default_rng(22)
+    vec = rng.standard_normal(len(b2)) + 1j * rng.standard_normal(len(b2))
+    groups = O.hva_groups(lat2, 1, ["U", "V", "eps", "h1", "v1", "h2", "v2"])
+
+    def slipped(kind, f):
+        def terms(mm, bb, g):
+            pieces = O.group_terms(mm, bb, g)
+            if g.kind != kind:
+                return pieces
+            return [f(p) for p in pieces]
+        return terms
+
+    for kind, f in [("nn_v", lambda p: ("diag", 2.0 * p[1])),
+                    ("eps", lambda p: ("diag", -p[1])),
+                    ("onsite_u", lambda p: ("diag", 0.5 * p[1])),
+                    ("hop", lambda p: ("hop", -p[1], p[2]))]:
+        assert _generator_sum_residual(m2, b2, groups, vec, slipped(kind, f)) > 1e-3, kind
+    assert _generator_sum_residual(m2, b2, groups, vec) < 1e-13
+    # an R_z generator missing its constant 1/2, or with the wrong sign
+    lat3 = O.square_lattice(1, 3)
+    m3 = O.make_model(lat3, 1.0, 2.0)
+    b3 = O.full_basis(m3)
+    psi = rng.standard_normal(1 << 6) + 1j * rng.standard_normal(1 << 6)
+    ref = _kron_rz_product(6, 0.7311) @ psi
+    g = O.Group("rz", tuple(range(6)), 0)
+    d = O.group_terms(m3, b3, g)[0][1]
+    for bad in (d - 3.0, -d):              # constant dropped (sum of 6 halves), sign flipped
+        got = np.exp(-1j * 0.7311 * bad) * psi
+        assert not np.allclose(got, ref, atol=1e-6)
