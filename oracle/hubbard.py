@@ -52,7 +52,8 @@ __all__ = [
     "group_terms", "apply_group", "apply_generator", "ansatz_state",
     "energy", "energy_and_gradient", "fd_gradient", "lanczos_ground",
     "orbitals", "slater_state", "neel_state", "hartree_fock_energy",
-    "neel_energy", "u0_ground_energy",
+    "neel_energy", "u0_ground_energy", "fidelity", "overlap_loss_and_gradient",
+    "overlap_fd_gradient", "spin_correlation",
 ]
 
 # ---------------------------------------------------------------------------
@@ -450,6 +451,70 @@ def fd_gradient(model, basis, groups, theta, psi0, h=1e-4, H=None, cache=None):
         g[k] = (energy(model, basis, groups, tp, psi0, H, cache)
                 - energy(model, basis, groups, tm, psi0, H, cache)) / (2 * h)
     return g
+
+
+# ---------------------------------------------------------------------------
+# overlap loss (Eq. 5), fidelity and spin correlations (Sec. 3)
+# ---------------------------------------------------------------------------
+
+def fidelity(psi, psi_ref) -> float:
+    """F = |<psi_ref|psi>|^2 of two normalised states."""
+    return float(abs(np.vdot(psi_ref, psi)) ** 2)
+
+
+def overlap_loss_and_gradient(model, basis, groups, theta, psi0, psi_ref, cache=None):
+    """The overlap loss of Eq. 5, f = log10(1 - F) with F = |<psi(theta)|
+    psi_ref>|^2, and its gradient by the adjoint recursion of Sec. 2.1.
+
+    The recursion is the energy's with the projector P = |psi_ref><psi_ref|
+    in place of H: F = <psi_K|P|psi_K>, and with lambda_K = P psi_K =
+    psi_ref <psi_ref|psi_K> carried back through the inverse factors,
+    dF/dtheta_k = 2 Im <lambda_k|G_k|psi_k> (the derivative of the overlap
+    a = <psi_ref|psi_K> is -i <chi_k|G_k|psi_k> with chi_k the reference
+    carried back, and dF = 2 Re(conj(a) da)).  Then df/dtheta =
+    -dF/dtheta / ((1 - F) ln 10).  Returns (F, f, df/dtheta)."""
+    cache = {} if cache is None else cache
+    psi = ansatz_state(model, basis, groups, theta, psi0, cache)
+    a = np.vdot(psi_ref, psi)
+    F = float(abs(a) ** 2)
+    lam = psi_ref * a
+    n_par = max(g.param for g in groups) + 1 if groups else 0
+    dF = np.zeros(max(n_par, len(theta)))
+    for g in reversed(groups):
+        Gpsi = apply_generator(model, basis, g, psi, cache)
+        dF[g.param] += 2.0 * float(np.imag(np.vdot(lam, Gpsi)))
+        th = float(theta[g.param])
+        psi = apply_group(model, basis, g, th, psi, cache, inverse=True)
+        lam = apply_group(model, basis, g, th, lam, cache, inverse=True)
+    f = math.log10(1.0 - F)
+    return F, f, (-dF / ((1.0 - F) * math.log(10.0)))[:len(theta)]
+
+
+def overlap_fd_gradient(model, basis, groups, theta, psi0, psi_ref, h=1e-5, cache=None):
+    """Central finite differences of f(theta) = log10(1 - F(theta))."""
+    cache = {} if cache is None else cache
+    theta = np.asarray(theta, dtype=np.float64)
+    g = np.zeros(len(theta))
+
+    def f_of(th):
+        return math.log10(1.0 - fidelity(ansatz_state(model, basis, groups, th, psi0, cache), psi_ref))
+
+    for k in range(len(theta)):
+        tp = theta.copy(); tp[k] += h
+        tm = theta.copy(); tm[k] -= h
+        g[k] = (f_of(tp) - f_of(tm)) / (2 * h)
+    return g
+
+
+def spin_correlation(model: Model, basis: np.ndarray, psi) -> np.ndarray:
+    """C_ij = <S^z_i S^z_j> - <S^z_i><S^z_j> (Sec. 3) for all site pairs,
+    S^z_i = (n_{i up} - n_{i dn}) / 2, expectation values in psi."""
+    p = np.abs(np.asarray(psi)) ** 2
+    nu, nd = _site_occ(model, basis)
+    sz = 0.5 * (nu - nd)                      # [L][basis]
+    m1 = sz @ p                               # <S^z_i>
+    m2 = (sz * p[None, :]) @ sz.T             # <S^z_i S^z_j>
+    return m2 - np.outer(m1, m1)
 
 
 # ---------------------------------------------------------------------------

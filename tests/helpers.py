@@ -7,6 +7,9 @@ Tolerances (relative to the scale of the quantity):
   state        c128 1e-10, c64 1e-6   (relative L2 error of the vector)
 """
 
+import json
+import os
+
 import numpy as np
 
 import oracle as O
@@ -92,3 +95,27 @@ def grad_scale(prob, theta, r=0):
 
 def rel_err(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def grad_err(g, go):
+    """c64/c128 gradient error in units of the stated target: max_p |g_p -
+    g_ref,p| / max(1, |g_ref|_inf)."""
+    return float(np.max(np.abs(np.asarray(g) - np.asarray(go))) / max(1.0, float(np.max(np.abs(go)))))
+
+
+def energy_err(E, Eo):
+    return float(abs(E - Eo) / max(1.0, abs(Eo)))
+
+
+def log_errors(test: str, dtype: int, engine: str, **errs):
+    """Appends the measured errors of one result (relative, see grad_err /
+    energy_err) to the JSON-lines file named by HUBSV_ERR_LOG, if set, so
+    that a GPU run states the error of each result against the oracle."""
+    path = os.environ.get("HUBSV_ERR_LOG")
+    if not path:
+        return
+    rec = {"test": test, "dtype": "c64" if dtype == H.C64 else "c128", "engine": engine,
+           "tol": TOL[dtype]}
+    rec.update({k: float(v) for k, v in errs.items()})
+    with open(path, "a") as f:
+        f.write(json.dumps(rec) + "\n")

@@ -1,6 +1,6 @@
 """GPU tests of the layers above the kernels: the CUDA-graph-captured
-energy + gradient, the L-BFGS VQE driver, the tile autotuner and the
-checkpointed adjoint pass."""
+energy + gradient, the L-BFGS VQE driver and the tile autotuner (the
+checkpointed adjoint pass is tested in test_checkpoint_gpu.py)."""
 
 import numpy as np
 import pytest
@@ -78,25 +78,3 @@ def test_autotune_keeps_results():
             assert np.max(np.abs(cur[1] - ref[1])) < TOL[H.C64] * max(1.0, np.max(np.abs(ref[1])))
     best, times = autotune(a, H.C64, batch=1, which=1, candidates=(11, 12, 13), theta=w.theta()[:1])
     assert best in times and len(times) == 3
-
-
-def test_checkpointed_gradient_matches_oracle_24q():
-    """Workload 6 shape (24 qubits): the adjoint pass with a checkpoint of
-    psi at the middle layer boundary against the oracle's gradient."""
-    w = W.workload(6)
-    bonds, _ = H.square_lattice(3, 4)
-    t, U, _ = w.coefficients(bonds)
-    prob = Problem(3, 4, t=t, U=U, V=None, layers=w.layers, classes=w.classes)
-    theta = w.theta()[0]
-    a = prob.ans
-    a.state_prepare(H.PREP_SLATER, None, None, None, H.C64, 1)
-    th = torch.tensor(theta[None, :], device="cuda")
-    psi = torch.empty((1, 1 << 24), dtype=torch.complex64, device="cuda")
-    lam, ck = torch.empty_like(psi), torch.empty_like(psi)
-    E = torch.empty(1, dtype=torch.float64, device="cuda")
-    g = torch.empty((1, a.P), dtype=torch.float64, device="cuda")
-    a.energy_grad(th, psi, lam, E, g, ckpt=ck, dtype=H.C64)
-    H.sync()
-    Eo, go = prob.oracle_energy_grad(theta)
-    assert abs(float(E[0]) - Eo) < TOL[H.C64] * max(1.0, abs(Eo))
-    assert np.max(np.abs(g.cpu().numpy()[0] - go)) < TOL[H.C64] * max(1.0, np.max(np.abs(go)))

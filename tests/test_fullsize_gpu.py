@@ -121,8 +121,9 @@ def test_28q_periodicity_and_precisions():
 
 def test_32q_c64_energy_gradient_against_c128_and_fd():
     """Workload 5 at full size: c64 energy + adjoint gradient (the benchmarked
-    call) against c128 energies: the energy within the c64 tolerance and the
-    gradient's directional derivative against a central difference."""
+    call, row engine) against c128 energies: the energy within the c64
+    tolerance and the gradient's directional derivative against a central
+    difference; the dense sweeps with the layer checkpoint give the same."""
     w, a, om = _setup(5)
     theta = w.theta()[0]
     n = w.n_qubits
@@ -136,12 +137,14 @@ def test_32q_c64_energy_gradient_against_c128_and_fd():
     H.sync()
     e64 = float(E[0])
     g64 = g.cpu().numpy()[0]
-    # the same with a checkpoint of psi (three 2^32 vectors resident)
+    # the dense 2^32 sweeps with a checkpoint of psi at the middle layer
+    # (three 2^32 vectors resident, 103 GB): the same energy and gradient
     ck = torch.empty_like(psi)
-    a.energy_grad(th, psi, lam, E, g, ckpt=ck, dtype=H.C64, batch=1)
+    a.energy_grad(th, psi, lam, E, g, ckpt=ck, dtype=H.C64, batch=1, sweeps=True)
     H.sync()
     g64c = g.cpu().numpy()[0]
     assert abs(float(E[0]) - e64) < TOL[H.C64] * max(1.0, abs(e64))
+    assert np.max(np.abs(g64c - g64)) < 2 * TOL[H.C64] * max(1.0, np.max(np.abs(g64)))
     del psi, lam, ck
     torch.cuda.empty_cache()
     psi = torch.empty((1, 1 << n), dtype=torch.complex128, device="cuda")

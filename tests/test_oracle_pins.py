@@ -526,3 +526,106 @@ def test_mistakes_are_caught():
     for bad in (d - 3.0, -d):              # constant dropped (sum of 6 halves), sign flipped
         got = np.exp(-1j * 0.7311 * bad) * psi
         assert not np.allclose(got, ref, atol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# overlap loss (Eq. 5), fidelity and spin correlations (Sec. 3)
+# ---------------------------------------------------------------------------
+
+def test_overlap_loss_two_site_closed_form():
+    """One up electron on a two-site chain, one hop factor exp(-i theta G)
+    with G = -(a+_0 a_1 + h.c.): psi = cos(theta)|0> + i sin(theta)|1> (up to
+    the sign of the second amplitude), so with the reference on site 1,
+    F = sin^2 theta, f = log10(cos^2 theta), df/dtheta = -2 tan(theta)/ln 10."""
+    lat = O.square_lattice(1, 2)
+    m = O.make_model(lat, 1.0, 0.0, n_up=1, n_dn=0)
+    b = O.sector_basis(m)
+    assert list(b) == [1, 2]
+    psi0 = np.array([1.0 + 0j, 0.0])
+    ref = np.array([0.0 + 0j, 1.0])
+    groups = [O.Group("hop", ((0, 1),), 0)]
+    for th in (0.3, -1.1, 0.77):
+        F, f, g = O.overlap_loss_and_gradient(m, b, groups, np.array([th]), psi0, ref)
+        assert abs(F - math.sin(th) ** 2) < 1e-15
+        assert abs(f - math.log10(math.cos(th) ** 2)) < 1e-14
+        assert abs(g[0] + 2 * math.tan(th) / math.log(10.0)) < 1e-13
+
+
+def test_overlap_gradient_matches_central_differences():
+    lat, m = _model_2x3()
+    b = O.sector_basis(m)
+    H = O.hamiltonian(m, b)
+    _, ref = O.lanczos_ground(H)
+    pu, pd, _ = O.orbitals(m)
+    psi0 = O.slater_state(m, pu, pd)
+    groups = O.hva_groups(lat, 2, ["U", "V", "eps", "h1", "v1", "h2"])
+    th = np.random.default_rng(12).uniform(-1, 1, 12)
+    F, f, g = O.overlap_loss_and_gradient(m, b, groups, th, psi0, ref)
+    assert 0.0 < F < 1.0
+    fd = O.overlap_fd_gradient(m, b, groups, th, psi0, ref, h=1e-5)
+    assert np.max(np.abs(g - fd)) < 1e-7 * max(1.0, np.max(np.abs(g)))
+    # the reference taken as psi(theta') itself: F(theta') = 1 exactly
+    ref2 = O.ansatz_state(m, b, groups, th, psi0)
+    assert abs(O.fidelity(O.ansatz_state(m, b, groups, th, psi0), ref2) - 1.0) < 1e-13
+
+
+def test_spin_correlation_closed_forms_and_sum_rule():
+    """Two-site Hubbard ground state (one electron per spin): in the basis of
+    the covalent and ionic singlets, H = [[0, -2t], [-2t, U]], so with E0 its
+    lowest eigenvalue the covalent weight is w = 1 / (1 + E0^2 / (4 t^2)),
+    <S^z_0 S^z_1> = -w / 4, <S^z_i> = 0 and C_00 = C_11 = w / 4.  On any
+    state of a fixed (N_up, N_dn) sector S^z_total is a constant, so every
+    row of C sums to zero; a product (Neel) state has C = 0."""
+    lat = O.square_lattice(1, 2)
+    for U in (4.0, 8.0):
+        m = O.make_model(lat, 1.0, U, n_up=1, n_dn=1)
+        b = O.sector_basis(m)
+        e0, v = O.lanczos_ground(O.hamiltonian(m, b))
+        assert abs(e0 - (U - math.sqrt(U * U + 16)) / 2) < 1e-12
+        w = 1.0 / (1.0 + e0 * e0 / 4.0)
+        C = O.spin_correlation(m, b, v)
+        assert np.allclose(C, [[w / 4, -w / 4], [-w / 4, w / 4]], atol=1e-12)
+    lat, m = _model_2x3()
+    b = O.sector_basis(m)
+    rng = np.random.default_rng(13)
+    v = rng.standard_normal(len(b)) + 1j * rng.standard_normal(len(b))
+    v /= np.linalg.norm(v)
+    C = O.spin_correlation(m, b, v)
+    assert np.allclose(C, C.T, atol=1e-14)
+    assert np.max(np.abs(C.sum(axis=1))) < 1e-13
+    psi = O.neel_state(m, lat, b)
+    assert np.max(np.abs(O.spin_correlation(m, b, psi))) < 1e-15
+
+
+def test_overlap_and_correlation_mistakes_are_caught():
+    """Planted mistakes: the adjoint vector not scaled by the overlap
+    (lambda_K = psi_ref) fails the finite differences; charge instead of
+    spin in C fails the two-site closed form."""
+    lat, m = _model_2x3()
+    b = O.sector_basis(m)
+    _, ref = O.lanczos_ground(O.hamiltonian(m, b))
+    pu, pd, _ = O.orbitals(m)
+    psi0 = O.slater_state(m, pu, pd)
+    groups = O.hva_groups(lat, 1, ["U", "h1", "v1", "h2"])
+    th = np.random.default_rng(14).uniform(-1, 1, 4)
+    F, _, _ = O.overlap_loss_and_gradient(m, b, groups, th, psi0, ref)
+    psi = O.ansatz_state(m, b, groups, th, psi0)
+    lam = ref.copy()                               # missing the factor <ref|psi_K>
+    dF = np.zeros(4)
+    for g in reversed(groups):
+        dF[g.param] += 2.0 * float(np.imag(np.vdot(lam, O.apply_generator(m, b, g, psi))))
+        psi = O.apply_group(m, b, g, th[g.param], psi, inverse=True)
+        lam = O.apply_group(m, b, g, th[g.param], lam, inverse=True)
+    bad = -dF / ((1.0 - F) * math.log(10.0))
+    fd = O.overlap_fd_gradient(m, b, groups, th, psi0, ref)
+    assert np.max(np.abs(bad - fd)) > 1e-3
+    lat2 = O.square_lattice(1, 2)
+    m2 = O.make_model(lat2, 1.0, 4.0, n_up=1, n_dn=1)
+    b2 = O.sector_basis(m2)
+    e0, v = O.lanczos_ground(O.hamiltonian(m2, b2))
+    nu, nd = O.hubbard._site_occ(m2, b2)
+    ch = 0.5 * (nu + nd)
+    p = np.abs(v) ** 2
+    Cbad = (ch * p) @ ch.T - np.outer(ch @ p, ch @ p)
+    w = 1.0 / (1.0 + e0 * e0 / 4.0)
+    assert abs(Cbad[0, 1] + w / 4) > 1e-2
