@@ -53,7 +53,8 @@ __all__ = [
     "energy", "energy_and_gradient", "fd_gradient", "lanczos_ground",
     "orbitals", "slater_state", "neel_state", "hartree_fock_energy",
     "neel_energy", "u0_ground_energy", "fidelity", "overlap_loss_and_gradient",
-    "overlap_fd_gradient", "spin_correlation",
+    "overlap_fd_gradient", "spin_correlation", "number_basis", "np_groups", "ep_groups",
+    "np_param_count", "ep_param_count",
 ]
 
 # ---------------------------------------------------------------------------
@@ -199,6 +200,13 @@ def sector_basis(model: Model, n_up: int | None = None,
     return np.sort((a[:, None] | b[None, :]).ravel())
 
 
+def number_basis(model: Model, n_total: int) -> np.ndarray:
+    """Sorted basis states with n_total electrons in all (both spins): the
+    sector that spin-mixing ansatz factors (the on-site NP gate, the EP
+    gates) keep."""
+    return np.sort(_configs(list(model.up) + list(model.dn), n_total))
+
+
 def full_basis(model: Model) -> np.ndarray:
     """All 2^n basis states (small n only)."""
     return np.arange(1 << model.n_modes, dtype=np.uint64)
@@ -301,8 +309,9 @@ def hamiltonian(model: Model, basis: np.ndarray) -> sp.csr_matrix:
 
 @dataclass
 class Group:
-    kind: str               # 'hop' | 'onsite_u' | 'nn_v' | 'eps' | 'rz'
-    terms: tuple            # hop/nn_v: site pairs; onsite_u/eps: sites; rz: modes
+    kind: str               # 'hop' | 'onsite_u' | 'nn_v' | 'eps' | 'rz' | 'givens' | 'cphase'
+    terms: tuple            # hop/nn_v: site pairs; onsite_u/eps: sites; rz: modes;
+                            # givens/cphase: mode pairs
     param: int
 
 
@@ -333,6 +342,73 @@ def hva_groups(lat: Lattice, n_layers: int, classes: Sequence[str],
     return out
 
 
+def np_groups(lat: Lattice, model: Model, n_layers: int, rz: bool = True) -> list:
+    """The number-preserving (NP) ansatz of Sec. 2.2.1, in application order.
+
+    An optional R_z pre-layer (one parameter per qubit, the 'rz' generator
+    Z/2), then per layer the terms of Eq. 7 in its order -- on-site terms,
+    then the h1, v1, h2, v2 hopping classes -- each replaced by its own NP
+    gate U_NP(theta, phi) of Eq. 8 = exp(-i theta G_givens) exp(-i phi
+    G_cphase) on the term's two modes: the on-site term on (up(i), dn(i)),
+    a hopping term on (sigma(i), sigma(j)) for each spin.  Each factor has its
+    own parameter (theta, then phi)."""
+    out = []
+    p = 0
+    if rz:
+        for k in range(model.n_modes):
+            out.append(Group("rz", (k,), p))
+            p += 1
+    for _ in range(n_layers):
+        pairs = [(int(model.up[i]), int(model.dn[i])) for i in range(lat.n_sites)]
+        for cc in ("h1", "v1", "h2", "v2"):
+            for (i, j), k in zip(lat.bonds, lat.bond_class):
+                if k == cc:
+                    for m in (model.up, model.dn):
+                        pairs.append((int(m[i]), int(m[j])))
+        for (a, b) in pairs:
+            a, b = min(a, b), max(a, b)
+            out.append(Group("givens", ((a, b),), p))
+            out.append(Group("cphase", ((a, b),), p + 1))
+            p += 2
+    return out
+
+
+def np_param_count(nx: int, ny: int, n_layers: int, rz: bool = True) -> int:
+    """Parameters of the NP ansatz as the paper counts them (Sec. 2.2.1):
+    (10 Nx Ny - 4 Nx - 4 Ny) per layer plus 2 Nx Ny for the R_z layer."""
+    return (10 * nx * ny - 4 * nx - 4 * ny) * n_layers + (2 * nx * ny if rz else 0)
+
+
+def ep_groups(n_modes: int, n_layers: int) -> list:
+    """The excitation-preserving (EP) ansatz of Sec. 2.2.2, in application
+    order: R_z on every qubit, then per layer the two-qubit gate of Eq. 10
+    on each pair of neighbouring qubits (k, k+1), k = 0 .. n-2, then R_z on
+    every qubit again.  Qubit k is mode k (the paper's interleaved order
+    puts site s on qubits 2s, 2s+1).  Eq. 10's gate U_EP(theta, phi) equals
+    exp(-i theta' G_givens) exp(-i phi' G_cphase) with theta' = -theta / 2
+    and phi' = -phi; the groups here carry theta' and phi' as their
+    parameters (a fixed linear change of variables)."""
+    out = []
+    p = 0
+    for k in range(n_modes):
+        out.append(Group("rz", (k,), p))
+        p += 1
+    for _ in range(n_layers):
+        for k in range(n_modes - 1):
+            out.append(Group("givens", ((k, k + 1),), p))
+            out.append(Group("cphase", ((k, k + 1),), p + 1))
+            p += 2
+    for k in range(n_modes):
+        out.append(Group("rz", (k,), p))
+        p += 1
+    return out
+
+
+def ep_param_count(nx: int, ny: int, n_layers: int) -> int:
+    """4 Nx Ny + 2 (2 Nx Ny - 1) l (Sec. 2.2.2)."""
+    return 4 * nx * ny + 2 * (2 * nx * ny - 1) * n_layers
+
+
 def group_terms(model: Model, basis: np.ndarray, group: Group, cache=None):
     """The group's generator as a list of commuting pieces.
 
@@ -349,6 +425,11 @@ def group_terms(model: Model, basis: np.ndarray, group: Group, cache=None):
             for m in (model.up, model.dn):
                 T = hop_matrix(basis, int(m[i]), int(m[j]))
                 pieces.append(("hop", -model.t[i, j], T))
+    elif group.kind == "givens":
+        # the theta part of the NP gate (Eq. 8): generator -(a+_p a_q + h.c.),
+        # unit coefficient, any two modes (same or opposite spin)
+        for (p, q) in group.terms:
+            pieces.append(("hop", -1.0, hop_matrix(basis, int(p), int(q))))
     else:
         d = np.zeros(len(basis))
         if group.kind == "onsite_u":
@@ -365,6 +446,11 @@ def group_terms(model: Model, basis: np.ndarray, group: Group, cache=None):
         elif group.kind == "rz":
             for k in group.terms:
                 d += 0.5 - number_diag(basis, int(k))
+        elif group.kind == "cphase":
+            # the phi part of the NP gate (Eq. 8): generator -n_p n_q, so that
+            # exp(-i phi G) puts exp(+i phi) on |11>
+            for (p, q) in group.terms:
+                d -= number_diag(basis, int(p)) * number_diag(basis, int(q))
         else:
             raise ValueError(group.kind)
         pieces.append(("diag", d))

@@ -143,7 +143,7 @@ def _paper_gates(theta, phi):
             s = line.strip()
             if not s or s.startswith("#"):
                 continue
-            if s in ("NP", "FSWAP"):
+            if s in ("NP", "FSWAP", "EP"):
                 cur = s
                 mats[cur] = []
             else:
@@ -629,3 +629,79 @@ def test_overlap_and_correlation_mistakes_are_caught():
     Cbad = (ch * p) @ ch.T - np.outer(ch @ p, ch @ p)
     w = 1.0 / (1.0 + e0 * e0 / 4.0)
     assert abs(Cbad[0, 1] + w / 4) > 1e-2
+
+
+# ---------------------------------------------------------------------------
+# NP ansatz (Sec. 2.2.1, Eq. 8) and EP ansatz (Sec. 2.2.2, Eq. 10)
+# ---------------------------------------------------------------------------
+
+def _gate_of_groups(groups, thetas, n=2):
+    """4x4 matrix of a product of oracle groups on a two-mode full space
+    (basis order |00>, |01>, |10>, |11> with bit 0 = mode 0)."""
+    lat = O.square_lattice(1, 1)
+    m = O.make_model(lat, 0.0, 0.0, n_up=0, n_dn=0, modes=(np.array([0]), np.array([1])))
+    basis = np.arange(1 << n, dtype=np.uint64)
+    cols = []
+    for k in range(1 << n):
+        e = np.zeros(1 << n, dtype=complex)
+        e[k] = 1
+        for g in groups:
+            e = O.apply_group(m, basis, g, thetas[g.param], e)
+        cols.append(e)
+    return np.array(cols).T
+
+
+def test_np_and_ep_gates_from_groups_match_the_printed_matrices():
+    th, ph = 0.43, -0.87
+    np_groups = [O.Group("givens", ((0, 1),), 0), O.Group("cphase", ((0, 1),), 1)]
+    assert np.allclose(_gate_of_groups(np_groups, [th, ph]), _paper_gates(th, ph)["NP"], atol=1e-14)
+    # Eq. 10: U_EP(theta, phi) = givens(-theta/2) cphase(-phi)
+    assert np.allclose(_gate_of_groups(np_groups, [-th / 2, -ph]), _paper_gates(th, ph)["EP"], atol=1e-14)
+
+
+def test_np_and_ep_parameter_counts():
+    """The paper prints 1,568 parameters for 12 NP layers on the 4x4 lattice
+    (Sec. 3); the builders give the paper's counts for other sizes too."""
+    lat = O.square_lattice(4, 4)
+    m = O.make_model(lat, 1.0, 2.0)
+    g = O.np_groups(lat, m, 12)
+    assert max(x.param for x in g) + 1 == 1568 == O.np_param_count(4, 4, 12)
+    for (nx, ny, layers) in [(2, 3, 1), (2, 3, 5), (3, 3, 13), (1, 6, 4)]:
+        lat = O.square_lattice(nx, ny)
+        m = O.make_model(lat, 1.0, 2.0)
+        assert max(x.param for x in O.np_groups(lat, m, layers)) + 1 == O.np_param_count(nx, ny, layers)
+        assert max(x.param for x in O.ep_groups(2 * nx * ny, layers)) + 1 == O.ep_param_count(nx, ny, layers)
+
+
+def test_np_ansatz_conserves_total_number_and_mixes_spins():
+    """The on-site NP gate's theta part moves an electron between the two
+    spin modes of a site: N_up + N_dn is conserved, N_up alone is not.  The
+    adjoint gradient in the total-N basis agrees with central differences."""
+    lat = O.square_lattice(2, 2)
+    m = O.make_model(lat, 1.0, 4.0, n_up=2, n_dn=2, modes="interleaved")
+    b = O.number_basis(m, 4)
+    sec = set(int(x) for x in O.sector_basis(m))
+    pu, pd, _ = O.orbitals(m, perturb=np.diag(1e-3 * np.arange(4)))
+    psi0_s = O.slater_state(m, pu, pd)
+    psi0 = np.zeros(len(b), dtype=complex)
+    idx = {int(x): i for i, x in enumerate(b)}
+    for x, v in zip(O.sector_basis(m), psi0_s):
+        psi0[idx[int(x)]] = v
+    groups = O.np_groups(lat, m, 2)
+    P = max(x.param for x in groups) + 1
+    th = np.random.default_rng(31).uniform(-1, 1, P)
+    psi = O.ansatz_state(m, b, groups, th, psi0)
+    assert abs(np.linalg.norm(psi) - 1.0) < 1e-13
+    outside = sum(abs(psi[i]) ** 2 for i, x in enumerate(b) if int(x) not in sec)
+    assert outside > 1e-3
+    Hm = O.hamiltonian(m, b)
+    E, g = O.energy_and_gradient(m, b, groups, th, psi0, Hm)
+    fd = O.fd_gradient(m, b, groups, th, psi0, h=1e-5, H=Hm)
+    assert np.max(np.abs(g - fd)) < 1e-7 * max(1.0, np.max(np.abs(g)))
+    # without the on-site theta (set to zero) the sector is kept exactly
+    th2 = th.copy()
+    for x in groups:
+        if x.kind == "givens" and x.terms[0][1] - x.terms[0][0] == 1 and x.terms[0][0] % 2 == 0:
+            th2[x.param] = 0.0
+    psi2 = O.ansatz_state(m, b, groups, th2, psi0)
+    assert sum(abs(psi2[i]) ** 2 for i, x in enumerate(b) if int(x) not in sec) < 1e-28
