@@ -25,8 +25,17 @@
  *      HUB_G_NN_V    sum_{(i,j) in terms} V_ij n_i n_j
  *      HUB_G_POT     -sum_{i in terms} t_ii (n_{i up} + n_{i dn})
  *      HUB_G_RZ      sum_{k in terms} (1/2 - n_k)  (= Z_k / 2, modes k)
+ *      HUB_G_GIVENS  -sum_{(p,q) in terms} (a+_p a_q + a+_q a_p)  (mode pairs)
+ *      HUB_G_CPHASE  -sum_{(p,q) in terms} n_p n_q                (mode pairs)
+ *    GIVENS and CPHASE build the number-preserving gate of Eq. 8 term by
+ *    term (U_NP(theta, phi) on modes p, q = the GIVENS factor with theta
+ *    times the CPHASE factor with phi; the NP ansatz of Sec. 2.2.1) and the
+ *    gate of Eq. 10 (U_EP(theta, phi) = GIVENS(-theta/2) CPHASE(-phi); the
+ *    EP ansatz of Sec. 2.2.2).  A GIVENS pair may join an up and a down mode
+ *    (the on-site NP gate); then only N_up + N_dn is conserved and every
+ *    call runs as dense sweeps over all tiles.
  *    The terms of one group must commute: hop bonds of a group touch
- *    disjoint sites.
+ *    disjoint sites, Givens pairs of a group disjoint modes.
  *  - Gradient: dE/dtheta_p = sum over groups g with parameter p of
  *    2 Im <lambda_g| G_g |psi_g>, psi_g the state after group g and
  *    lambda_g = U_{g+1}^+ ... U_K^+ H psi_K (Sec. 2.1, standard form of the
@@ -77,7 +86,8 @@ typedef enum {
 typedef enum { HUB_C64 = 0, HUB_C128 = 1 } hub_dtype;
 
 typedef enum {
-  HUB_G_HOP = 0, HUB_G_ONSITE = 1, HUB_G_NN_V = 2, HUB_G_POT = 3, HUB_G_RZ = 4
+  HUB_G_HOP = 0, HUB_G_ONSITE = 1, HUB_G_NN_V = 2, HUB_G_POT = 3, HUB_G_RZ = 4,
+  HUB_G_GIVENS = 5, HUB_G_CPHASE = 6
 } hub_gkind;
 
 typedef enum { HUB_PREP_SLATER = 0, HUB_PREP_NEEL = 1 } hub_prep;
@@ -105,7 +115,9 @@ typedef struct {
 
 /* One ansatz group (one factor of Eq. 7).  terms (host): bond indices of the
  * lattice for HOP and NN_V, site indices for ONSITE and POT, mode indices for
- * RZ.  param indexes theta; groups may share a parameter.                    */
+ * RZ; for GIVENS and CPHASE n_terms mode pairs, terms holding 2 * n_terms
+ * ints (p0, q0, p1, q1, ...; at most 16 pairs in a CPHASE group).  param
+ * indexes theta; groups may share a parameter.                              */
 typedef struct {
   int32_t kind;             /* hub_gkind */
   int32_t n_terms;
@@ -224,6 +236,32 @@ HUB_API hub_status energy_noalloc(ans_t ans, const double* theta, void* psi, dou
  * by callers that need the residual).  psi is read only.                    */
 HUB_API hub_status hub_apply_h(ans_t ans, const void* psi, void* lam, int32_t dtype,
                        int64_t batch, hub_stream_t stream);
+
+/* The overlap loss of Eq. 5 and the fidelity (Sec. 3): for each batch
+ * element, F = |<psi_ref|psi(theta)>|^2 and f = log10(1 - F), with psi(theta)
+ * the ansatz state of energy(), and (grad != NULL) df/dtheta by the adjoint
+ * recursion of Sec. 2.1 with the projector |psi_ref><psi_ref| in place of
+ * H: lam_K = psi_ref <psi_ref|psi_K>, dF/dtheta_p = sum over the groups of
+ * p of 2 Im <lam_g|G_g|psi_g>, df/dtheta = -dF/dtheta / ((1 - F) ln 10).
+ * psi_ref: device [ref_batch][2^n] amplitudes of the call's dtype,
+ * normalised (ref_batch = 1: one reference for every batch element, or
+ * batch).  psi: as energy() (initial state unless HUB_FLAG_PREP_FUSED, the
+ * only flag accepted; clobbered).  lam: device workspace of psi's size, or
+ * NULL when grad is NULL.  F, f: device double [batch] or NULL; grad: device
+ * double [batch][P] or NULL.  Runs as dense sweeps (the paper optimises the
+ * overlap on lattices of up to 24 qubits).  f is -inf when F = 1.          */
+HUB_API hub_status overlap_grad(ans_t ans, const double* theta, const void* psi_ref,
+                                int64_t ref_batch, void* psi, void* lam, double* F,
+                                double* f, double* grad, int32_t dtype, int64_t batch,
+                                uint32_t flags, hub_stream_t stream);
+
+/* Spin correlation of Sec. 3 for each batch element of the state psi
+ * (device [batch][2^n] amplitudes, normalised, read only):
+ * C[b][i][j] = <S^z_i S^z_j> - <S^z_i><S^z_j>, S^z_i = (n_{i up} - n_{i dn})/2,
+ * for all site pairs (C: device double [batch][L][L]).  Reductions in FP64.
+ * Obtain the ansatz state with energy(..., HUB_FLAG_KEEP_STATE, ...).      */
+HUB_API hub_status spin_correlation(ans_t ans, const void* psi, double* C, int32_t dtype,
+                                    int64_t batch, hub_stream_t stream);
 
 /* Plan statistics for the last-planned configuration of a call kind (0 =
  * energy, 1 = energy_grad): number of sweeps and HBM bytes moved per batch

@@ -223,6 +223,29 @@ class Ansatz:
                                 _stream(stream)))
         return lam
 
+    def overlap_grad(self, theta, psi_ref, psi, lam=None, F=None, f=None, grad=None, dtype=C64,
+                     batch: int = 1, fused: bool = True, stream=None):
+        """Fidelity F = |<psi_ref|psi(theta)>|^2, the overlap loss of Eq. 5
+        f = log10(1 - F) and (grad given) df/dtheta; psi_ref holds one
+        reference or one per batch element."""
+        nb = batch * self.amp_bytes(dtype)
+        ref_batch = psi_ref.numel() * psi_ref.element_size() // self.amp_bytes(dtype)
+        if ref_batch not in (1, batch):
+            raise ValueError("psi_ref must hold 1 or batch states")
+        check(lib().overlap_grad(self._h, _ptr(theta, 8 * batch * self.P, "theta"),
+                                 _ptr(psi_ref, ref_batch * self.amp_bytes(dtype), "psi_ref"), ref_batch,
+                                 _ptr(psi, nb, "psi"), _ptr(lam, nb, "lam"), _ptr(F, 8 * batch, "F"),
+                                 _ptr(f, 8 * batch, "f"), _ptr(grad, 8 * batch * self.P, "grad"), dtype, batch,
+                                 FLAG_PREP_FUSED if fused else 0, _stream(stream)))
+        return F, f, grad
+
+    def spin_correlation(self, psi, C, dtype=C64, batch: int = 1, stream=None):
+        """C[b][i][j] = <S^z_i S^z_j> - <S^z_i><S^z_j> of the state psi (Sec. 3)."""
+        L = self.n // 2
+        check(lib().spin_correlation(self._h, _ptr(psi, batch * self.amp_bytes(dtype), "psi"),
+                                     _ptr(C, 8 * batch * L * L, "C"), dtype, batch, _stream(stream)))
+        return C
+
     def plan_stats(self, which: int, dtype=C64, fused: bool = True, rows: bool = False):
         """(sweeps, HBM bytes per state) of the dense sweep plan, or with
         rows=True (launches, HBM bytes per state) of the row engine."""

@@ -17,7 +17,8 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["hubsv_api.cpp", "hubsv_plan.cpp", "hubsv_tables.cu", "hubsv_sweep_f1.cu",
            "hubsv_sweep_f2.cu", "hubsv_sweep_d1.cu", "hubsv_sweep_d2.cu", "hubsv_noalloc.cu",
-           "hubsv_small.cu", "hubsv_sweep_fv.cu", "hubsv_sweep_dv.cu", "hubsv_rows.cu"]
+           "hubsv_small.cu", "hubsv_sweep_fv.cu", "hubsv_sweep_dv.cu", "hubsv_rows.cu",
+           "hubsv_overlap.cu"]
 
 
 def _nvcc():

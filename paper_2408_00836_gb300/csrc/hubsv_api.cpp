@@ -258,7 +258,9 @@ int add_diag_op(hub_ansatz* a, const std::vector<std::vector<double>>& xcoef,
                 const std::vector<double>& xconst,
                 const std::vector<std::vector<double>>& ycoef,
                 const std::vector<std::pair<int, int>>& vbonds,
-                const std::vector<std::vector<double>>& vval, int param) {
+                const std::vector<std::vector<double>>& vval,
+                const std::vector<std::pair<int, int>>& mpairs,
+                const std::vector<std::vector<double>>& mval, int param) {
   DiagOpDev d;
   std::memset(&d, 0, sizeof(d));
   bool any_x = false, any_y = false;
@@ -293,9 +295,15 @@ int add_diag_op(hub_ansatz* a, const std::vector<std::vector<double>>& xcoef,
     if (u1 == u2 || (d.vs_mask[g] >> u1 & 1u)) d.n_vs = -1;   // not a plain bond list
     else d.vs_mask[g] |= 1u << u1;
   }
+  d.n_mp = (int)mpairs.size();
+  for (int m = 0; m < d.n_mp; ++m) {
+    d.mp_p[m] = mpairs[m].first;
+    d.mp_q[m] = mpairs[m].second;
+  }
+  d.mp_roff = 2048 + d.n_vb;
   d.param = param;
   d.real_off = a->real_stride;
-  const int real_len = 2048 + d.n_vb;
+  const int real_len = 2048 + d.n_vb + d.n_mp;
   // real tables per instance (appended; real_stride grows)
   std::vector<std::vector<double>> rt(a->n_inst, std::vector<double>(real_len, 0.0));
   for (int r = 0; r < a->n_inst; ++r) {
@@ -312,6 +320,7 @@ int add_diag_op(hub_ansatz* a, const std::vector<std::vector<double>>& xcoef,
         rt[r][1024 + byte * 256 + j] = vy;
       }
     for (int b = 0; b < d.n_vb; ++b) rt[r][2048 + b] = vval[r][b];
+    for (int m = 0; m < d.n_mp; ++m) rt[r][d.mp_roff + m] = mval[r][m];
   }
   const int old = a->real_stride;
   std::vector<double> nr((size_t)a->n_inst * (old + real_len));
@@ -326,7 +335,8 @@ int add_diag_op(hub_ansatz* a, const std::vector<std::vector<double>>& xcoef,
   if (param >= 0) {
     d.phase_off = a->n_tab;
     const int vlen = d.n_vb == 0 ? 0 : (d.v_uniform ? 4 * d.n_vb + 1 : 5 * d.n_vb);
-    const int len = 2048 + vlen;
+    d.mp_poff = 2048 + vlen;
+    const int len = 2048 + vlen + d.n_mp;
     std::vector<double> nv((size_t)a->n_inst * (a->n_tab + len));
     for (int r = 0; r < a->n_inst; ++r) {
       std::copy(a->tab_val.begin() + (size_t)r * a->n_tab, a->tab_val.begin() + (size_t)(r + 1) * a->n_tab,
@@ -340,6 +350,7 @@ int add_diag_op(hub_ansatz* a, const std::vector<std::vector<double>>& xcoef,
           for (int b = 0; b < d.n_vb; ++b)
             for (int e = 0; e < 5; ++e) dst[2048 + 5 * b + e] = vval[r][b] * e;
       }
+      for (int m = 0; m < d.n_mp; ++m) dst[d.mp_poff + m] = mval[r][m];
     }
     a->tab_val.swap(nv);
     for (int e = 0; e < len; ++e) a->tab_param.push_back(param);
@@ -347,7 +358,7 @@ int add_diag_op(hub_ansatz* a, const std::vector<std::vector<double>>& xcoef,
       for (int j = 0; j < 256; ++j) a->tab_live.push_back(a->n_tab + i * 256 + j);
     for (int i = 0; i < d.has_y; ++i)
       for (int j = 0; j < 256; ++j) a->tab_live.push_back(a->n_tab + 1024 + i * 256 + j);
-    for (int e = 0; e < vlen; ++e) a->tab_live.push_back(a->n_tab + 2048 + e);
+    for (int e = 0; e < vlen + d.n_mp; ++e) a->tab_live.push_back(a->n_tab + 2048 + e);
     a->n_tab += len;
   } else {
     d.phase_off = -1;
@@ -377,6 +388,7 @@ uint64_t diag_support(const hub_ansatz* a, int di) {
     m |= 1ull << d.vb_up2[b];
     m |= 1ull << (d.vb_up2[b] + a->s);
   }
+  for (int k = 0; k < d.n_mp; ++k) m |= (1ull << d.mp_p[k]) | (1ull << d.mp_q[k]);
   return m;
 }
 
@@ -415,7 +427,23 @@ extern "C" hub_status ans_create_multi(const hub_t* models, int32_t n_models, in
     if (gr.n_terms < 0 || (gr.n_terms > 0 && !gr.terms)) return bad("bad term list");
     P = std::max(P, gr.param + 1);
     const bool hop = gr.kind == HUB_G_HOP;
-    if (gr.kind < 0 || gr.kind > HUB_G_RZ) return bad("unknown group kind");
+    if (gr.kind < 0 || gr.kind > HUB_G_CPHASE) return bad("unknown group kind");
+    if (gr.kind == HUB_G_GIVENS || gr.kind == HUB_G_CPHASE) {
+      // terms: n_terms mode pairs (p, q); Givens pairs of one group touch
+      // disjoint modes, so that its factors commute
+      if (gr.kind == HUB_G_CPHASE && gr.n_terms > kMaxModePairs) return bad("too many mode pairs in a CPHASE group");
+      uint64_t used = 0;
+      for (int k = 0; k < gr.n_terms; ++k) {
+        const int p = gr.terms[2 * k], q = gr.terms[2 * k + 1];
+        if (p < 0 || q < 0 || p >= a->n || q >= a->n || p == q) return bad("mode pair out of range");
+        if (gr.kind == HUB_G_GIVENS) {
+          if ((used >> p & 1) || (used >> q & 1)) return bad("Givens pairs of one group must touch disjoint modes");
+          used |= (1ull << p) | (1ull << q);
+          if (((a->upmask >> p) & 1) != ((a->upmask >> q) & 1)) a->spin_mix = true;
+        }
+      }
+      continue;
+    }
     uint64_t seen = 0;
     for (int k = 0; k < gr.n_terms; ++k) {
       const int tm = gr.terms[k];
@@ -443,13 +471,19 @@ extern "C" hub_status ans_create_multi(const hub_t* models, int32_t n_models, in
       if (p > q) std::swap(p, q);
       a->hterms.push_back({p, q});
     }
-  a->hcoef.resize((size_t)R * a->hterms.size());
-  for (int r = 0; r < R; ++r)
+  // columns of the -t table: one per H hop term, then one column of -1 for
+  // the unit generators -(a+_p a_q + h.c.) of HUB_G_GIVENS factors
+  const int unit_col = (int)a->hterms.size();
+  a->n_hcol = unit_col + 1;
+  a->hcoef.assign((size_t)R * a->n_hcol, 0.0);
+  for (int r = 0; r < R; ++r) {
     for (int b = 0; b < nb; ++b)
       for (int sp = 0; sp < 2; ++sp) {
         const auto& bd = m0->bonds[b];
-        a->hcoef[(size_t)r * a->hterms.size() + 2 * b + sp] = -models[r]->t[(size_t)bd.first * L + bd.second];
+        a->hcoef[(size_t)r * a->n_hcol + 2 * b + sp] = -models[r]->t[(size_t)bd.first * L + bd.second];
       }
+    a->hcoef[(size_t)r * a->n_hcol + unit_col] = -1.0;
+  }
   // H diagonal: potential -t_ii on both modes of site i, U_i on double occupancy, V bonds
   {
     std::vector<std::vector<double>> xc(R, std::vector<double>(a->n, 0.0)), yc(R, std::vector<double>(a->n, 0.0)), vv(R);
@@ -469,7 +503,7 @@ extern "C" hub_status ans_create_multi(const hub_t* models, int32_t n_models, in
       }
       for (auto& bd : vb) vv[r].push_back(models[r]->V[(size_t)bd.first * L + bd.second]);
     }
-    a->h_diag = add_diag_op(a, xc, xk, yc, vb, vv, -1);
+    a->h_diag = add_diag_op(a, xc, xk, yc, vb, vv, {}, {}, -1);
   }
   // forward sequence
   a->n_layers = n_layers;
@@ -490,14 +524,36 @@ extern "C" hub_status ans_create_multi(const hub_t* models, int32_t n_models, in
           op.support = (1ull << op.p) | (1ull << op.q);
           op.cls = 0;
           a->gate_param.push_back(gr.param);
+          a->gate_unit.push_back(0);
           a->fwd.push_back(op);
         }
+      }
+    } else if (gr.kind == HUB_G_GIVENS) {
+      for (int k = 0; k < gr.n_terms; ++k) {
+        SeqOp op;
+        op.kind = OP_GIV;
+        op.hterm = unit_col;
+        op.p = std::min(gr.terms[2 * k], gr.terms[2 * k + 1]);
+        op.q = std::max(gr.terms[2 * k], gr.terms[2 * k + 1]);
+        op.gate = a->n_gates++;
+        op.slot = gr.param;
+        op.support = (1ull << op.p) | (1ull << op.q);
+        op.cls = 0;
+        a->gate_param.push_back(gr.param);
+        a->gate_unit.push_back(1);
+        a->fwd.push_back(op);
       }
     } else {
       std::vector<std::vector<double>> xc(R, std::vector<double>(a->n, 0.0)), yc(R, std::vector<double>(a->n, 0.0)), vv(R);
       std::vector<double> xk(R, 0.0);
-      std::vector<std::pair<int, int>> vb;
-      for (int k = 0; k < gr.n_terms; ++k) {
+      std::vector<std::pair<int, int>> vb, mp;
+      std::vector<std::vector<double>> mv(R);
+      for (int k = 0; k < gr.n_terms && gr.kind == HUB_G_CPHASE; ++k) {
+        // generator -n_p n_q: exp(-i phi G) puts exp(+i phi) on |11> (Eq. 8)
+        mp.push_back({gr.terms[2 * k], gr.terms[2 * k + 1]});
+        for (int r = 0; r < R; ++r) mv[r].push_back(-1.0);
+      }
+      for (int k = 0; k < gr.n_terms && gr.kind != HUB_G_CPHASE; ++k) {
         const int tm = gr.terms[k];
         for (int r = 0; r < R; ++r) {
           const hub_model* m = models[r];
@@ -517,7 +573,7 @@ extern "C" hub_status ans_create_multi(const hub_t* models, int32_t n_models, in
       if (vb.size() > 64) return bad("too many V bonds in a group");
       SeqOp op;
       op.kind = OP_DIAG;
-      op.diag = add_diag_op(a, xc, xk, yc, vb, vv, gr.param);
+      op.diag = add_diag_op(a, xc, xk, yc, vb, vv, mp, mv, gr.param);
       op.slot = gr.param;
       op.diagonal = true;
       op.support = diag_support(a, op.diag);
@@ -530,8 +586,12 @@ extern "C" hub_status ans_create_multi(const hub_t* models, int32_t n_models, in
     int gi = 0;
     for (const SeqOp& op : a->fwd)
       if (op.kind == OP_GIV) {
-        const auto& bd = m0->bonds[op.hterm / 2];
-        a->gate_t[(size_t)r * a->n_gates + gi++] = models[r]->t[(size_t)bd.first * L + bd.second];
+        if (a->gate_unit[gi]) {
+          a->gate_t[(size_t)r * a->n_gates + gi++] = 1.0;
+        } else {
+          const auto& bd = m0->bonds[op.hterm / 2];
+          a->gate_t[(size_t)r * a->n_gates + gi++] = models[r]->t[(size_t)bd.first * L + bd.second];
+        }
       }
   }
   *out = a;
@@ -610,7 +670,7 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
     pl->uploaded = true;
   }
   const size_t r2 = dtype == HUB_C64 ? 8 : 16;
-  if ((s = a->d_coef[dtype].ensure(r2 * std::max<int64_t>(1, batch * a->n_gates), "coefficients")) != HUB_OK) return s;
+  if ((s = a->d_coef[dtype].ensure(16 * std::max<int64_t>(1, batch * a->n_gates), "coefficients")) != HUB_OK) return s;
   if ((s = a->d_phase[dtype].ensure(r2 * std::max<int64_t>(1, batch * a->n_tab), "phase tables")) != HUB_OK) return s;
   if ((s = a->d_acc.ensure(8 * (size_t)batch * n_slots, "accumulators")) != HUB_OK) return s;
   HUB_CUDA(launch_zero((double*)a->d_acc.p, batch * n_slots, st), "zero accumulators");
@@ -622,9 +682,10 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
                          a->n_inst, st),
              "coefficient kernel");
   }
-  if (pl->sector) {
+  if (pl->sector && pl->prep) {
     // sweeps visit only the tiles that meet the sector; the amplitudes
-    // outside it, which those tiles also hold, must read as zero
+    // outside it, which those tiles also hold, must read as zero (a
+    // backward-only pass reads a psi that its forward pass left so)
     const size_t vb = (size_t)batch * ((size_t)1 << n) * (dtype == HUB_C64 ? 8 : 16);
     HUB_CUDA(cudaMemsetAsync(psi, 0, vb, st), "clear psi");
     if (lam) HUB_CUDA(cudaMemsetAsync(lam, 0, vb, st), "clear lam");
@@ -643,7 +704,7 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
   ka.coef = a->d_coef[dtype].p;
   ka.n_gates = a->n_gates;
   ka.hcoef = (const double*)a->d_hcoef.p;
-  ka.n_hterms = (int)a->hterms.size();
+  ka.n_hterms = a->n_hcol;
   ka.real_tabs = (const double*)a->d_real.p;
   ka.real_tabs32 = (const float*)a->d_real32.p;
   ka.real_stride = a->real_stride;
@@ -736,7 +797,7 @@ SmallPlan* small_plan_for(hub_ansatz* a, int which, int dtype, uint32_t flags, s
   const uint64_t C = (uint64_t)sp->cup * (uint64_t)sp->cdn;
   if (C * (uint64_t)std::max(sp->cup, sp->cdn) >= (1ull << 32)) return nullptr;
   smem = small_smem_bytes(dtype, sp->cup, sp->cdn, (int)sp->pairs.size(), a->P + 2, a->n_gates,
-                          (int)a->hterms.size());
+                          a->n_hcol);
   if ((int)smem > sweep_max_smem_optin()) return nullptr;
   return sp;
 }
@@ -755,7 +816,7 @@ hub_status run_small(hub_ansatz* a, SmallPlan* sp, size_t smem, int dtype, const
     sp->uploaded = true;
   }
   const size_t r2 = dtype == HUB_C64 ? 8 : 16;
-  if ((s = a->d_coef[dtype].ensure(r2 * std::max<int64_t>(1, batch * a->n_gates), "coefficients")) != HUB_OK) return s;
+  if ((s = a->d_coef[dtype].ensure(16 * std::max<int64_t>(1, batch * a->n_gates), "coefficients")) != HUB_OK) return s;
   if ((s = a->d_phase[dtype].ensure(r2 * std::max<int64_t>(1, batch * a->n_tab), "phase tables")) != HUB_OK) return s;
   if ((s = a->d_acc.ensure(8 * (size_t)batch * n_slots, "accumulators")) != HUB_OK) return s;
   if (theta) {
@@ -783,7 +844,7 @@ hub_status run_small(hub_ansatz* a, SmallPlan* sp, size_t smem, int dtype, const
   ka.coef = a->d_coef[dtype].p;
   ka.n_gates = a->n_gates;
   ka.hcoef = (const double*)a->d_hcoef.p;
-  ka.n_hterms = (int)a->hterms.size();
+  ka.n_hterms = a->n_hcol;
   ka.real_tabs = (const double*)a->d_real.p;
   ka.real_tabs32 = (const float*)a->d_real32.p;
   ka.real_stride = a->real_stride;
@@ -850,8 +911,8 @@ RowPlan* row_plan_for(hub_ansatz* a, int which, int dtype, uint32_t flags, Small
     const int nv = (g.flags & RS_HAS_LAM) ? 2 : 1;
     const int len = g.orient == 0 ? sp->cup : sp->cdn;
     const int no = g.op_end - g.op_begin;
-    const int nt = rows_threads(dtype, nv, len, a->P + 2, a->n_gates, (int)a->hterms.size(), no);
-    if ((int)rows_smem_bytes(dtype, nv, len, a->P + 2, a->n_gates, (int)a->hterms.size(), nt, no) > optin)
+    const int nt = rows_threads(dtype, nv, len, a->P + 2, a->n_gates, a->n_hcol, no);
+    if ((int)rows_smem_bytes(dtype, nv, len, a->P + 2, a->n_gates, a->n_hcol, nt, no) > optin)
       return nullptr;
   }
   sp_out = sp;
@@ -876,7 +937,7 @@ hub_status run_rows(hub_ansatz* a, SmallPlan* sp, RowPlan* rp, int dtype, const 
     rp->uploaded = true;
   }
   const size_t r2 = dtype == HUB_C64 ? 8 : 16;
-  if ((s = a->d_coef[dtype].ensure(r2 * std::max<int64_t>(1, batch * a->n_gates), "coefficients")) != HUB_OK) return s;
+  if ((s = a->d_coef[dtype].ensure(16 * std::max<int64_t>(1, batch * a->n_gates), "coefficients")) != HUB_OK) return s;
   if ((s = a->d_phase[dtype].ensure(r2 * std::max<int64_t>(1, batch * a->n_tab), "phase tables")) != HUB_OK) return s;
   if ((s = a->d_acc.ensure(8 * (size_t)batch * n_slots, "accumulators")) != HUB_OK) return s;
   HUB_CUDA(launch_zero((double*)a->d_acc.p, batch * n_slots, st), "zero accumulators");
@@ -944,7 +1005,7 @@ hub_status run_rows(hub_ansatz* a, SmallPlan* sp, RowPlan* rp, int dtype, const 
     ka.coef = a->d_coef[dtype].p;
     ka.n_gates = a->n_gates;
     ka.hcoef = (const double*)a->d_hcoef.p;
-    ka.n_hterms = (int)a->hterms.size();
+    ka.n_hterms = a->n_hcol;
     ka.real_tabs = (const double*)a->d_real.p;
     ka.real_tabs32 = (const float*)a->d_real32.p;
     ka.real_stride = a->real_stride;
@@ -1125,6 +1186,64 @@ extern "C" hub_status hub_apply_h(ans_t a, const void* psi, void* lam, int32_t d
   if ((s = get_plan(a, 2, dtype, 0, pl)) != HUB_OK) return s;
   return run_plan(a, pl, dtype, nullptr, const_cast<void*>(psi), lam, nullptr, batch, nullptr, nullptr,
                   (cudaStream_t)stream);
+}
+
+extern "C" hub_status overlap_grad(ans_t a, const double* theta, const void* psi_ref, int64_t ref_batch,
+                                   void* psi, void* lam, double* F, double* f, double* grad, int32_t dtype,
+                                   int64_t batch, uint32_t flags, hub_stream_t stream) {
+  hub_status s = check_call(a, dtype, batch);
+  if (s != HUB_OK) return s;
+  if (!psi_ref || !psi || (a->P > 0 && !theta)) return fail(HUB_EINVAL, "overlap_grad: NULL buffer");
+  if (grad && !lam) return fail(HUB_EINVAL, "overlap_grad: the gradient needs lam");
+  if (lam && (lam == psi || lam == psi_ref)) return fail(HUB_EINVAL, "overlap_grad: lam must be a separate buffer");
+  if (psi == psi_ref) return fail(HUB_EINVAL, "overlap_grad: psi and psi_ref must be distinct");
+  if (ref_batch != 1 && ref_batch != batch) return fail(HUB_EINVAL, "overlap_grad: ref_batch must be 1 or batch");
+  if (flags & ~(uint32_t)HUB_FLAG_PREP_FUSED) return fail(HUB_EINVAL, "overlap_grad: unknown flags");
+  const bool fused = (flags & HUB_FLAG_PREP_FUSED) != 0;
+  if (fused && a->prep_kind < 0)
+    return fail(HUB_EINVAL, "overlap_grad: HUB_FLAG_PREP_FUSED needs a prior state_prepare");
+  cudaStream_t st = (cudaStream_t)stream;
+  // forward circuit, psi_K kept in psi
+  Plan* pf;
+  if ((s = get_plan(a, 4, dtype, (fused ? HUB_FLAG_PREP_FUSED : 0u) | HUB_FLAG_KEEP_STATE, pf)) != HUB_OK) return s;
+  if ((s = run_plan(a, pf, dtype, theta, psi, nullptr, nullptr, batch, nullptr, nullptr, st)) != HUB_OK) return s;
+  // a = <psi_ref|psi_K>
+  if ((s = a->d_ovl.ensure(16 * (size_t)batch, "overlaps")) != HUB_OK) return s;
+  double* ov = (double*)a->d_ovl.p;
+  HUB_CUDA(launch_zero(ov, 2 * batch, st), "zero overlaps");
+  HUB_CUDA(launch_overlap(dtype, psi, psi_ref, ref_batch, a->n, batch, ov, st), "overlap kernel");
+  const double* acc = nullptr;
+  if (grad) {
+    // lam_K = psi_ref a, then the backward pass accumulates dF/dtheta
+    HUB_CUDA(launch_scale_ref(dtype, psi_ref, ref_batch, lam, a->n, batch, ov, st), "reference scaling kernel");
+    Plan* pb;
+    if ((s = get_plan(a, 5, dtype, fused ? HUB_FLAG_PREP_FUSED : 0u, pb)) != HUB_OK) return s;
+    if ((s = run_plan(a, pb, dtype, theta, psi, lam, nullptr, batch, nullptr, nullptr, st)) != HUB_OK) return s;
+    acc = (const double*)a->d_acc.p;
+  }
+  HUB_CUDA(launch_overlap_finalize(acc, a->P + 2, a->P, ov, F, f, grad, batch, st), "overlap finalize kernel");
+  return HUB_OK;
+}
+
+extern "C" hub_status spin_correlation(ans_t a, const void* psi, double* C, int32_t dtype, int64_t batch,
+                                       hub_stream_t stream) {
+  hub_status s = check_call(a, dtype, batch);
+  if (s != HUB_OK) return s;
+  if (!psi || !C) return fail(HUB_EINVAL, "spin_correlation: NULL buffer");
+  const int n = a->n, L = a->L;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!a->d_modes.p) {
+    std::vector<int32_t> md(a->models[0]->up);
+    md.insert(md.end(), a->models[0]->dn.begin(), a->models[0]->dn.end());
+    if ((s = a->d_modes.upload(md, "mode maps")) != HUB_OK) return s;
+  }
+  if ((s = a->d_occ.ensure(8 * (size_t)batch * n * n, "occupation correlations")) != HUB_OK) return s;
+  double* M = (double*)a->d_occ.p;
+  HUB_CUDA(launch_zero(M, batch * n * n, st), "zero correlations");
+  HUB_CUDA(launch_occ_corr(dtype, psi, n, batch, M, st), "occupation correlation kernel");
+  const int32_t* md = (const int32_t*)a->d_modes.p;
+  HUB_CUDA(launch_spin_corr(M, n, md, md + L, L, C, batch, st), "spin correlation kernel");
+  return HUB_OK;
 }
 
 extern "C" hub_status ans_plan_stats(ans_t a, int32_t which, int32_t dtype, uint32_t flags, int32_t* n_sweeps,

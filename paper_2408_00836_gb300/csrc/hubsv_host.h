@@ -63,6 +63,7 @@ struct Plan {
   DevBuf ops, phases;
   int k = 0;
   bool sector = false;                    // sweeps visit live (sector) tiles only
+  bool prep = false;                      // the first sweep generates psi_0
   double bytes_per_state = 0;             // amplitude bytes moved per state
 };
 
@@ -119,11 +120,14 @@ struct hub_ansatz {
   int h_diag = -1;                       // DiagOp index of H's diagonal
   std::vector<hubsv::DiagOpDev> diag_ops;
   std::vector<int32_t> gate_param;
+  std::vector<uint8_t> gate_unit;        // 1: a HUB_G_GIVENS factor (unit generator)
+  int n_hcol = 0;                        // columns of hcoef: H hop terms + 1 unit column
+  bool spin_mix = false;                 // a Givens factor couples an up and a down mode
   std::vector<double> gate_t;            // [n_inst][n_gates]
   std::vector<int32_t> tab_param;        // [n_tab]
   std::vector<double> tab_val;           // [n_inst][n_tab]
   std::vector<int32_t> tab_live;         // entries of the phase tables that kernels read
-  std::vector<double> hcoef;             // [n_inst][n_hterms]
+  std::vector<double> hcoef;             // [n_inst][n_hcol]
   std::vector<double> real_tabs;         // [n_inst][real_stride]
   int n_gates = 0, n_tab = 0, real_stride = 0;
   hubsv::DevBuf d_gate_param, d_gate_t, d_tab_param, d_tab_val, d_tab_live, d_hcoef, d_real, d_diag;
@@ -133,6 +137,9 @@ struct hub_ansatz {
   int prep_kind = -1;
   uint64_t neel_x0 = 0;
   hubsv::DevBuf d_coef[2], d_phase[2], d_acc;
+  hubsv::DevBuf d_ovl;                   // overlaps <psi_ref|psi_K> [batch][2]
+  hubsv::DevBuf d_occ;                   // occupation correlations [batch][n][n]
+  hubsv::DevBuf d_modes;                 // site -> mode maps (up, then dn) for C_ij
   std::map<int, hubsv::Plan*> plans;     // key = which*16 + dtype*4 + flags
   std::map<int, hubsv::SmallPlan*> small_plans;   // key = which
   std::map<int, hubsv::RowPlan*> row_plans;       // key = which

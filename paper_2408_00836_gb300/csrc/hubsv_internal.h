@@ -12,6 +12,7 @@ constexpr int kMaxTileBits = 14;
 constexpr int kLaneBits = 5;        // lanes of a warp <-> 5 tile bits
 constexpr int kMaxRegBits = 5;      // amplitudes per thread = 2^r, r <= 5
 constexpr int kMaxWarpBits = 5;
+constexpr int kMaxModePairs = 16;   // mode-pair products in one diagonal operator
 
 // One operation applied to a tile.  Operations are the factors of the ansatz
 // (Eq. 7), the terms of H (Eqs. 1, 2, 15, 16) and the adjoint steps of
@@ -94,10 +95,17 @@ struct DiagOpDev {
   int32_t n_vs;
   int32_t vs_shift[32];
   uint32_t vs_mask[32];          // bit u: a bond from up-mode u to u + shift
+  // mode-pair products sum_m c_m n_p(m) n_q(m) (controlled phases of the NP
+  // and EP gates, Eqs. 8 and 10): real values at real_off + mp_roff, phases
+  // at phase_off + mp_poff, one per pair
+  int32_t n_mp, mp_roff, mp_poff;
+  int32_t mp_p[kMaxModePairs];
+  int32_t mp_q[kMaxModePairs];
 };
-// Real table layout at real_off: [4][256] X, [4][256] Y, [n_vb] v_b.
-// Phase table layout at phase_off: [4][256] X, [4][256] Y, then either
-// [4*n_vb+1] K-table (v_uniform) or [n_vb][5] per-bond powers.
+// Real table layout at real_off: [4][256] X, [4][256] Y, [n_vb] v_b,
+// [n_mp] c_m.  Phase table layout at phase_off: [4][256] X, [4][256] Y,
+// then either [4*n_vb+1] K-table (v_uniform) or [n_vb][5] per-bond powers,
+// then [n_mp] mode-pair phases.
 
 enum SweepFlag : uint32_t {
   SW_PREP = 1u,        // generate psi_0 instead of reading psi
@@ -196,16 +204,16 @@ struct KernelArgs {
 
 // A sweep's operations as the kernel reads them from shared memory: OpDev
 // with its table lookups done for the current batch element (coefficients,
-// table offsets) and one dense case code, so that an operation costs two
-// (c64) or three (c128) 16-byte shared loads and one indirect branch.
+// table offsets) and one dense case code, so that an operation costs three
+// 16-byte shared loads and one indirect branch.
 //   w0 = {code | aux << 8 | slot << 16, sgn, bm_local, bm_global}
-//   hop ops, c64:  w1 = {c, s, tc, 0} (FP32)
+//   hop ops, c64:  w1 = {c, s, c_lo, s_lo}, w2 = {tc, 0, 0, 0} (FP32)
 //   hop ops, c128: w1 = {c, s}, w2 = {tc, 0} (FP64)
 //   diagonal ops:  w1 = {phase-table offset, real-table offset, DiagOp, 0}
-// c, s: the factor's cos / sin (s negated for an inverse factor); tc: -t of
-// the matching Hamiltonian term.
+// c, s: the factor's cos / sin (s negated for an inverse factor; in c64 as
+// FP32 pairs hi + lo, see GC); tc: -t of the matching Hamiltonian term.
 constexpr int kMaxSlots = 65535;     // slot is stored in 16 bits
-inline int res_words(int dtype) { return dtype == 0 ? 2 : 3; }
+inline int res_words(int /*dtype*/) { return 3; }
 enum ResCode : int {
   RC_NOP = 0,
   RC_GIV = 1,          // + pair index (0..9): factor on psi
@@ -264,6 +272,16 @@ cudaError_t launch_coef(int dtype, const double* theta, int P, const int32_t* ga
 cudaError_t launch_zero(double* p, int64_t n, cudaStream_t st);
 cudaError_t launch_finalize(const double* acc, int n_slots, int P, int slot_E,
                             double* E, double* grad, int64_t batch, cudaStream_t st);
+// Overlap loss and spin correlations (hubsv_overlap.cu).
+cudaError_t launch_overlap(int dtype, const void* psi, const void* ref, int64_t ref_batch, int n, int64_t batch,
+                           double* a, cudaStream_t st);
+cudaError_t launch_scale_ref(int dtype, const void* ref, int64_t ref_batch, void* lam, int n, int64_t batch,
+                             const double* a, cudaStream_t st);
+cudaError_t launch_overlap_finalize(const double* acc, int n_slots, int P, const double* a, double* F, double* f,
+                                    double* grad, int64_t batch, cudaStream_t st);
+cudaError_t launch_occ_corr(int dtype, const void* psi, int n, int64_t batch, double* M, cudaStream_t st);
+cudaError_t launch_spin_corr(const double* M, int n, const int32_t* up, const int32_t* dn, int L, double* C,
+                             int64_t batch, cudaStream_t st);
 int sweep_max_smem_optin();
 cudaError_t sweep_set_smem(int dtype, int nv, int r, int threads, bool vp, size_t smem);
 int sweep_regs(int dtype, int nv, int r, int threads, bool vp);

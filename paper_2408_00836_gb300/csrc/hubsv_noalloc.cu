@@ -110,7 +110,7 @@ extern "C" hub_status energy_noalloc(ans_t a, const double* theta, void* psi, do
   const size_t o_sd32 = lay.take(sd_needed ? 4 * sd32.size() : 0);
   const size_t o_ops = lay.take(sizeof(OpDev) * std::max<size_t>(1, pl->hops.size()));
   const size_t o_ph = lay.take(sizeof(PhaseDev) * pl->hphases.size());
-  const size_t o_cf = lay.take(r2 * (size_t)batch * a->n_gates);
+  const size_t o_cf = lay.take(16 * (size_t)batch * a->n_gates);   // Givens (cos, sin): 16 bytes in both dtypes
   const size_t o_pt = lay.take(r2 * (size_t)batch * a->n_tab);
   const size_t o_acc = lay.take(8 * (size_t)batch * n_slots);
   if (lay.used > kScratchBytes)
@@ -161,7 +161,7 @@ extern "C" hub_status energy_noalloc(ans_t a, const double* theta, void* psi, do
   ka.coef = S + o_cf;
   ka.n_gates = a->n_gates;
   ka.hcoef = reinterpret_cast<const double*>(S + o_hc);
-  ka.n_hterms = (int)a->hterms.size();
+  ka.n_hterms = a->n_hcol;
   ka.real_tabs = reinterpret_cast<const double*>(S + o_rt);
   ka.real_tabs32 = reinterpret_cast<const float*>(S + o_r32);
   ka.real_stride = a->real_stride;

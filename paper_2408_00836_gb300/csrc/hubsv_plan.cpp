@@ -48,12 +48,28 @@ SeqOp marker(uint8_t kind) {
 }
 
 // Call kinds: 0 energy, 1 energy + gradient, 2 lam = H psi, 3 initial state
-// only (no operations).  With a checkpoint (energy + gradient), psi is
-// saved after the first half of the layers and reloaded when the backward
-// pass has undone the second half.
+// only (no operations), 4 the forward circuit only (psi_K kept), 5 the
+// backward pass only (gradient steps and inverse factors in reverse order,
+// from psi_K and a given lam_K: the overlap gradient).  With a checkpoint
+// (energy + gradient), psi is saved after the first half of the layers and
+// reloaded when the backward pass has undone the second half.
 std::vector<SeqOp> build_sequence(const hub_ansatz* a, int which, uint32_t flags) {
   std::vector<SeqOp> seq;
   if (which == 3) return seq;
+  if (which == 4) return a->fwd;
+  if (which == 5) {
+    for (int i = (int)a->fwd.size() - 1; i >= 0; --i) {
+      SeqOp g = a->fwd[i];
+      g.kind = g.kind == OP_GIV ? OP_GRAD_HOP : OP_GRAD_DIAG;
+      g.cls = 3;
+      seq.push_back(g);
+      SeqOp v = a->fwd[i];
+      v.flags = OPF_INV | OPF_LAM;
+      v.cls = 3;
+      seq.push_back(v);
+    }
+    return seq;
+  }
   const bool ck = which == 1 && (flags & kPlanCkpt) && a->n_layers >= 2 &&
                   (int)a->layer_begin.size() == a->n_layers;
   const int split = ck ? a->layer_begin[a->n_layers / 2] : -1;
@@ -305,7 +321,9 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
   // every operation keeps it there: sweeps then visit only the tiles that
   // meet the sector (see SweepDev), and a candidate tile is worth the
   // operations it runs per live fraction of the vector it moves.
-  const bool sector = (which == 3 || (flags & HUB_FLAG_PREP_FUSED) != 0) && which != 2;
+  // (with a factor that mixes the spins only N_up + N_dn is conserved: every
+  // tile is visited)
+  const bool sector = (which == 3 || (flags & HUB_FLAG_PREP_FUSED) != 0) && which != 2 && !a->spin_mix;
   const BinomTable binom = make_binom_table();
   auto pad_tile = [&](uint64_t t) {
     for (int b = 0; b < n && popc64(t) < k; ++b) t |= 1ull << b;   // pad with low bits
@@ -398,10 +416,13 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
 
   Plan* pl = new Plan();
   pl->k = k;
-  const bool prep = which == 3 || (flags & HUB_FLAG_PREP_FUSED) != 0;
+  // the backward-only pass reads psi_K and lam_K (in the sector when the
+  // forward pass generated the initial state)
+  const bool prep = (which == 3 || (flags & HUB_FLAG_PREP_FUSED) != 0) && which != 5;
   pl->sector = sector;
+  pl->prep = prep;
   const bool keep = which == 3 || (flags & HUB_FLAG_KEEP_STATE) != 0;
-  bool lam_live = false;
+  bool lam_live = which == 5;
   const double amp = dtype == HUB_C64 ? 8.0 : 16.0;
   double bytes = 0.0;
   for (size_t si = 0; si < sweeps.size(); ++si) {

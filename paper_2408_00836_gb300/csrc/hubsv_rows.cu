@@ -131,7 +131,7 @@ size_t rows_smem_bytes(int dtype, int nv, int row_len, int n_slots, int n_gates,
   size_t s = (size_t)nv * (size_t)row_len * amp;            // rows of psi (, lam)
   s = (s + 15) & ~(size_t)15;
   s += sizeof(SmallOpDev) * (size_t)n_ops;                  // the segment's operations
-  s += amp * (size_t)n_gates;                               // (cos, sin) of the element
+  s += 16 * (size_t)n_gates;                                // (cos, sin) of the element (see GC)
   s += 8 * (size_t)(threads / 32) * (size_t)n_slots;        // accumulator rows, one per warp
   s += amp / 2 * (size_t)n_hterms;                          // -t of the element's instance
   return (s + 15) & ~(size_t)15;
@@ -148,7 +148,7 @@ enum { RH_GIV = 0, RH_MEAS = 1, RH_LAM = 2, RH_GRAD = 3, RH_GRADINV = 4 };
 template <int K, bool DOL, typename R, typename T2>
 __device__ __forceinline__ R row_hop(T2* __restrict__ prow, T2* __restrict__ lrow,
                                      const uint32_t* __restrict__ pl, int nb, uint32_t rpar, R c, R s,
-                                     R tc) {
+                                     R cl, R sl, R tc) {
   R part = 0;
   const int tid = threadIdx.x, nth = blockDim.x;
   for (int it0 = tid; it0 < nb; it0 += 4 * nth) {
@@ -166,13 +166,13 @@ __device__ __forceinline__ R row_hop(T2* __restrict__ prow, T2* __restrict__ lro
       const bool neg = ((pr >> 31) ^ rpar) != 0;
       T2 u = prow[e1], w = prow[e2];
       if constexpr (K == RH_GIV) {
-        const R ss = neg ? -s : s;
-        rot(u, w, c, ss);
+        const R ss = neg ? -s : s, ssl = neg ? -sl : sl;
+        rot(u, w, c, ss, cl, ssl);
         prow[e1] = u;
         prow[e2] = w;
         if constexpr (DOL) {
           T2 lu = lrow[e1], lw = lrow[e2];
-          rot(lu, lw, c, ss);
+          rot(lu, lw, c, ss, cl, ssl);
           lrow[e1] = lu;
           lrow[e2] = lw;
         }
@@ -181,11 +181,11 @@ __device__ __forceinline__ R row_hop(T2* __restrict__ prow, T2* __restrict__ lro
         T2 lu = lrow[e1], lw = lrow[e2];
         part += ts * ((lu.x * w.y - lu.y * w.x) + (lw.x * u.y - lw.y * u.x));
         if constexpr (K == RH_GRADINV) {   // then the inverse factor on both
-          const R ss = neg ? -s : s;
-          rot(u, w, c, ss);
+          const R ss = neg ? -s : s, ssl = neg ? -sl : sl;
+          rot(u, w, c, ss, cl, ssl);
           prow[e1] = u;
           prow[e2] = w;
-          rot(lu, lw, c, ss);
+          rot(lu, lw, c, ss, cl, ssl);
           lrow[e1] = lu;
           lrow[e2] = lw;
         }
@@ -246,13 +246,14 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
   const size_t rows_b = (((size_t)(has_lam ? 2 : 1) * (size_t)len * sizeof(T2)) + 15) & ~(size_t)15;
   SmallOpDev* sops = reinterpret_cast<SmallOpDev*>(smem_raw + rows_b);
   const int n_ops = a.op_end - a.op_begin;
-  T2* cs = reinterpret_cast<T2*>(sops + n_ops);
+  using GT = typename GC<R>::T;
+  GT* cs = reinterpret_cast<GT*>(sops + n_ops);
   AccT* acc = reinterpret_cast<AccT*>(cs + a.n_gates);   // [kRowWarps][n_slots]
   R* hc = reinterpret_cast<R*>(acc + kRowWarps * a.n_slots);
   const int tid = threadIdx.x, nth = blockDim.x;
   const R* rtabs = reinterpret_cast<const R*>(DT == 0 ? (const void*)a.real_tabs32 : (const void*)a.real_tabs);
   const T2* ptabs = reinterpret_cast<const T2*>(a.phase_tabs);
-  const T2* coef = reinterpret_cast<const T2*>(a.coef);
+  const GT* coef = reinterpret_cast<const GT*>(a.coef);
   const R* sdt = reinterpret_cast<const R*>(DT == 0 ? (const void*)a.prep.sd32 : (const void*)a.prep.sd);
   const uint32_t upm = (uint32_t)a.upmask;
   T2* psi = reinterpret_cast<T2*>(a.psi);
@@ -307,11 +308,13 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
       R part = 0, npart = 0;
       if (op.kind == OP_GIV || op.kind == OP_MEAS_HOP || op.kind == OP_LAM_HOP || op.kind == OP_GRAD_HOP ||
           op.kind == OP_GRADINV_HOP) {
-        R c = 0, s = 0, tc = 0;
+        R c = 0, s = 0, cl = 0, sl = 0, tc = 0;
         if (op.kind == OP_GIV || op.kind == OP_GRADINV_HOP) {
-          const T2 gq = cs[op.gate];
+          const GT gq = cs[op.gate];
           c = gq.x;
           s = (op.flags & OPF_INV) ? -gq.y : gq.y;
+          cl = GC<R>::cl(gq);
+          sl = (op.flags & OPF_INV) ? -GC<R>::sl(gq) : GC<R>::sl(gq);
         }
         if (op.kind != OP_GIV) tc = hc[op.hterm];
         const bool dol = (op.flags & OPF_LAM) != 0;
@@ -321,20 +324,20 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
         const uint32_t* pl = a.pairs + op.a;
         switch (op.kind) {
           case OP_GIV:
-            if (dol) row_hop<RH_GIV, true>(prow, lrow, pl, op.b, rpar, c, s, tc);
-            else row_hop<RH_GIV, false>(prow, lrow, pl, op.b, rpar, c, s, tc);
+            if (dol) row_hop<RH_GIV, true>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc);
+            else row_hop<RH_GIV, false>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc);
             break;
-          case OP_MEAS_HOP: part = row_hop<RH_MEAS, false>(prow, lrow, pl, op.b, rpar, c, s, tc); break;
-          case OP_LAM_HOP: part = row_hop<RH_LAM, false>(prow, lrow, pl, op.b, rpar, c, s, tc); break;
-          case OP_GRADINV_HOP: part = row_hop<RH_GRADINV, true>(prow, lrow, pl, op.b, rpar, c, s, tc); break;
-          default: part = row_hop<RH_GRAD, false>(prow, lrow, pl, op.b, rpar, c, s, tc); break;
+          case OP_MEAS_HOP: part = row_hop<RH_MEAS, false>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc); break;
+          case OP_LAM_HOP: part = row_hop<RH_LAM, false>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc); break;
+          case OP_GRADINV_HOP: part = row_hop<RH_GRADINV, true>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc); break;
+          default: part = row_hop<RH_GRAD, false>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc); break;
         }
         if (op.kind == OP_GRAD_HOP || op.kind == OP_GRADINV_HOP) row_add(acc, a.n_slots, op.slot, (R)2 * part);
         else if (op.kind != OP_GIV) eacc.add((R)2 * part);
       } else {   // diagonal operations
         const DiagOpDev* dp = a.diag_ops + op.a;
-        const int hx = __ldg(&dp->has_x), hy = __ldg(&dp->has_y), nvb = __ldg(&dp->n_vb);
-        const DiagVal<R, T2> dv{dp, (hx == 0 && nvb == 0 && (hy == 1 || hy == 2)) ? hy : 0};
+        const int hx = __ldg(&dp->has_x), hy = __ldg(&dp->has_y), nvb = __ldg(&dp->n_vb), nmp = __ldg(&dp->n_mp);
+        const DiagVal<R, T2> dv{dp, (hx == 0 && nvb == 0 && nmp == 0 && (hy == 1 || hy == 2)) ? hy : 0};
         const T2* ptab = ptabs + (size_t)b * a.phase_stride + __ldg(&dp->phase_off);
         const R* rtab = rtabs + (size_t)inst * a.real_stride + __ldg(&dp->real_off);
         const bool inv = (op.flags & OPF_INV) != 0, dol = (op.flags & OPF_LAM) != 0;

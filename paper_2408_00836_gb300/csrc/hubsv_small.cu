@@ -53,6 +53,8 @@ std::vector<uint32_t> patterns(const std::vector<int>& modes, int N) {
 hub_status make_small_plan(hub_ansatz* a, int which, SmallPlan*& out) {
   const hub_model* m = a->models[0];
   if (a->n > 32) return fail(HUB_EUNSUPPORTED, "on-chip path: more than 32 qubits");
+  // the sector layout needs N_up and N_dn conserved separately
+  if (a->spin_mix) return fail(HUB_EUNSUPPORTED, "sector engines: a Givens factor mixes the spins");
   SmallPlan* sp = new SmallPlan();
   sp->xup = patterns(m->up, m->n_up);
   sp->xdn = patterns(m->dn, m->n_dn);
@@ -137,7 +139,7 @@ size_t small_smem_bytes(int dtype, int cup, int cdn, int n_pairs, int n_slots, i
   const size_t amp = dtype == 0 ? 8 : 16;
   const size_t c = (size_t)(cup | 1) * (size_t)cdn;       // rows of odd pitch
   size_t s = 2 * c * amp;                                   // psi, lam
-  s += amp * (size_t)n_gates;                               // (cos, sin) of the element
+  s += 16 * (size_t)n_gates;                                // (cos, sin) of the element (see GC)
   s += 8 * (size_t)kSmallWarps * (size_t)n_slots;          // accumulators, one row per warp
   s += amp / 2 * (size_t)n_hterms;                          // -t of the element's instance
   s += 4 * ((size_t)cup + (size_t)cdn + (size_t)n_pairs);   // patterns, pair lists
@@ -166,9 +168,10 @@ __global__ void __launch_bounds__(kSmallThreads, sizeof(R) == 4 ? 2 : 1) small_k
   constexpr int DT = CT<R>::DT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int C = a.cup * a.cdn, ld = a.ld;
+  using GT = typename GC<R>::T;
   T2* psi = reinterpret_cast<T2*>(smem_raw);
   T2* lam = psi + (size_t)ld * a.cdn;
-  T2* cs = lam + (size_t)ld * a.cdn;
+  GT* cs = reinterpret_cast<GT*>(lam + (size_t)ld * a.cdn);
   using AccT = typename std::conditional<DT == 0, float2, double>::type;
   AccT* acc = reinterpret_cast<AccT*>(cs + a.n_gates);   // [kSmallWarps][n_slots]
   R* hc = reinterpret_cast<R*>(acc + kSmallWarps * a.n_slots);
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(kSmallThreads, sizeof(R) == 4 ? 2 : 1) small_k
   const int tid = threadIdx.x, nth = blockDim.x;
   const R* rtabs = reinterpret_cast<const R*>(DT == 0 ? (const void*)a.real_tabs32 : (const void*)a.real_tabs);
   const T2* ptabs = reinterpret_cast<const T2*>(a.phase_tabs);
-  const T2* coef = reinterpret_cast<const T2*>(a.coef);
+  const GT* coef = reinterpret_cast<const GT*>(a.coef);
   const R* sdt = reinterpret_cast<const R*>(DT == 0 ? (const void*)a.prep.sd32 : (const void*)a.prep.sd);
   const uint32_t upm = (uint32_t)a.upmask;
 
@@ -206,11 +209,13 @@ __global__ void __launch_bounds__(kSmallThreads, sizeof(R) == 4 ? 2 : 1) small_k
       if (oi + 1 < a.n_ops) nxt = a.ops[oi + 1];   // in flight during this operation
       R part = 0, npart = 0;   // this thread's share of one operation
       if (op.kind == OP_GIV || op.kind == OP_MEAS_HOP || op.kind == OP_LAM_HOP || op.kind == OP_GRAD_HOP) {
-        R c = 0, s = 0, tc = 0;
+        R c = 0, s = 0, cl = 0, sl = 0, tc = 0;
         if (op.kind == OP_GIV) {
-          const T2 g = cs[op.gate];
+          const GT g = cs[op.gate];
           c = g.x;
           s = (op.flags & OPF_INV) ? -g.y : g.y;
+          cl = GC<R>::cl(g);
+          sl = (op.flags & OPF_INV) ? -GC<R>::sl(g) : GC<R>::sl(g);
         } else {
           tc = hc[op.hterm];
         }
@@ -237,13 +242,13 @@ __global__ void __launch_bounds__(kSmallThreads, sizeof(R) == 4 ? 2 : 1) small_k
           const bool neg = (__popc(x & op.between) & 1) != 0;
           T2 u = psi[e1], w = psi[e2];
           if (op.kind == OP_GIV) {
-            const R ss = neg ? -s : s;
-            rot(u, w, c, ss);
+            const R ss = neg ? -s : s, ssl = neg ? -sl : sl;
+            rot(u, w, c, ss, cl, ssl);
             psi[e1] = u;
             psi[e2] = w;
             if (dol) {
               T2 lu = lam[e1], lw = lam[e2];
-              rot(lu, lw, c, ss);
+              rot(lu, lw, c, ss, cl, ssl);
               lam[e1] = lu;
               lam[e2] = lw;
             }

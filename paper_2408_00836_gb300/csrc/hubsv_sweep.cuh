@@ -50,6 +50,25 @@ template <typename R> struct CT;
 template <> struct CT<float> { using T2 = float2; static constexpr int DT = 0; };
 template <> struct CT<double> { using T2 = double2; static constexpr int DT = 1; };
 
+// Givens coefficients of one factor, (cos, sin) of its angle, 16 bytes in
+// both precisions.  complex64 keeps each as an FP32 pair hi + lo (GC<float>
+// = {c, s, c_lo, s_lo}): rounding cos and sin to FP32 alone moves each
+// rotation's angle by up to ~1e-7, the same shift on every factor of a
+// shared parameter, and that coherent shift gave complex64 gradients
+// errors of ~1e-6 relative; the pair keeps the angle exact to ~1e-14.
+// complex128 keeps doubles (GC<double> = {c, s}).
+template <typename R> struct GC;
+template <> struct GC<float> {
+  using T = float4;
+  __device__ static float cl(const float4& g) { return g.z; }
+  __device__ static float sl(const float4& g) { return g.w; }
+};
+template <> struct GC<double> {
+  using T = double2;
+  __device__ static double cl(const double2&) { return 0.0; }
+  __device__ static double sl(const double2&) { return 0.0; }
+};
+
 template <typename T2, typename R>
 __device__ __forceinline__ T2 mk(R x, R y) { T2 r; r.x = x; r.y = y; return r; }
 
@@ -216,6 +235,8 @@ __device__ __forceinline__ R diag_real(const DiagOpDev& d, const R* tab, uint32_
       v += vb[b] * (R)(ni * nj);
     }
   }
+  for (int m = 0; m < d.n_mp; ++m)
+    if ((x >> d.mp_p[m]) & (x >> d.mp_q[m]) & 1u) v += tab[d.mp_roff + m];
   return v;
 }
 
@@ -250,6 +271,8 @@ __device__ __forceinline__ T2 diag_phase(const DiagOpDev& d, const T2* tab, uint
       }
     }
   }
+  for (int m = 0; m < d.n_mp; ++m)
+    if ((x >> d.mp_p[m]) & (x >> d.mp_q[m]) & 1u) ph = cmul(ph, tab[d.mp_poff + m]);
   return ph;
 }
 
@@ -300,6 +323,23 @@ __device__ __forceinline__ void rot(T2& u, T2& w, R c, R s) {
   w = mk<T2, R>(c * w0.x - s * u0.y, c * w0.y + s * u0.x);
 }
 
+// The same rotation with (cos, sin) given as FP32 pairs c + cl, s + sl
+// (complex64; see GC): the low parts enter as one more product each, so the
+// rotation angle is exact to the pair's ~1e-14 while the amplitudes stay
+// FP32.  For complex128 (cl = sl = 0) it is rot().
+template <typename T2, typename R>
+__device__ __forceinline__ void rot(T2& u, T2& w, R c, R s, R cl, R sl) {
+  if constexpr (sizeof(R) == 4) {
+    const T2 u0 = u, w0 = w;
+    u = mk<T2, R>(fmaf(c, u0.x, fmaf(-s, w0.y, fmaf(cl, u0.x, -sl * w0.y))),
+                  fmaf(c, u0.y, fmaf(s, w0.x, fmaf(cl, u0.y, sl * w0.x))));
+    w = mk<T2, R>(fmaf(c, w0.x, fmaf(-s, u0.y, fmaf(cl, w0.x, -sl * u0.y))),
+                  fmaf(c, w0.y, fmaf(s, u0.x, fmaf(cl, w0.y, sl * u0.x))));
+  } else {
+    rot(u, w, c, s);
+  }
+}
+
 // x with its sign flipped when bit e of m is set (m: per-op sign mask; e is
 // a constant after unrolling, so this is a shift and two logic ops).
 __device__ __forceinline__ float sflip(float x, uint32_t m, int e) {
@@ -310,12 +350,12 @@ __device__ __forceinline__ double sflip(double x, uint32_t m, int e) {
 }
 
 template <int A, int B, int NE, typename T2, typename R>
-__device__ __forceinline__ void pair_giv(T2 (&v)[NE], R c, R s, uint32_t sm) {
+__device__ __forceinline__ void pair_giv(T2 (&v)[NE], R c, R s, R cl, R sl, uint32_t sm) {
 #pragma unroll
   for (int e = 0; e < NE; ++e) {
     if (((e >> A) & 1) == 0 && ((e >> B) & 1) == 1) {
       constexpr int F = (1 << A) | (1 << B);
-      rot(v[e], v[e ^ F], c, sflip(s, sm, e));
+      rot(v[e], v[e ^ F], c, sflip(s, sm, e), cl, sflip(sl, sm, e));
     }
   }
 }
@@ -349,7 +389,7 @@ __device__ __forceinline__ R pair_hop(T2 (&v)[NE], T2 (&l)[NE], R tc, uint32_t s
 // factor on psi and lam (the reduction uses the values before the inverse;
 // the factor commutes with its own generator, so either order is exact).
 template <int A, int B, int NE, typename T2, typename R>
-__device__ __forceinline__ R pair_gradinv(T2 (&v)[NE], T2 (&l)[NE], R c, R s, R tc, uint32_t sm) {
+__device__ __forceinline__ R pair_gradinv(T2 (&v)[NE], T2 (&l)[NE], R c, R s, R cl, R sl, R tc, uint32_t sm) {
   R part = 0;
 #pragma unroll
   for (int e = 0; e < NE; ++e) {
@@ -357,9 +397,9 @@ __device__ __forceinline__ R pair_gradinv(T2 (&v)[NE], T2 (&l)[NE], R c, R s, R 
       constexpr int F = (1 << A) | (1 << B);
       const T2 u = v[e], w = v[e ^ F], lu = l[e], lw = l[e ^ F];
       part += sflip(tc, sm, e) * ((lu.x * w.y - lu.y * w.x) + (lw.x * u.y - lw.y * u.x));
-      const R ss = sflip(s, sm, e);
-      rot(v[e], v[e ^ F], c, ss);
-      rot(l[e], l[e ^ F], c, ss);
+      const R ss = sflip(s, sm, e), ssl = sflip(sl, sm, e);
+      rot(v[e], v[e ^ F], c, ss, cl, ssl);
+      rot(l[e], l[e ^ F], c, ss, cl, ssl);
     }
   }
   return part;
@@ -387,11 +427,11 @@ __device__ __forceinline__ uint32_t f2u(float x) { return __float_as_uint(x); }
 template <typename R>
 __device__ void resolve_ops(const SweepDev& sw, const KernelArgs& a, uint4* sres, int b, int inst,
                             int* s_meas) {
-  using T2 = typename CT<R>::T2;
+  using GT = typename GC<R>::T;
   constexpr int DT = CT<R>::DT;
-  constexpr int NW = DT == 0 ? 2 : 3;
+  constexpr int NW = 3;
   const int nops = sw.op_end - sw.op_begin;
-  const T2* coef = reinterpret_cast<const T2*>(a.coef) + (size_t)b * a.n_gates;
+  const GT* coef = reinterpret_cast<const GT*>(a.coef) + (size_t)b * a.n_gates;
   const double* hc = a.hcoef + (size_t)inst * a.n_hterms;
   for (int i = threadIdx.x; i <= nops; i += blockDim.x) {
     uint4 w[3];
@@ -401,19 +441,23 @@ __device__ void resolve_ops(const SweepDev& sw, const KernelArgs& a, uint4* sres
       const int pidx = pair_index(o.a, o.b);
       int code = RC_NOP, aux = 0, slot = 0;
       bool hop = true;
-      R c = 0, s = 0, tc = 0;
+      R c = 0, s = 0, cl = 0, sl = 0, tc = 0;
       switch (o.kind) {
         case OP_GIV: {
-          const T2 cs = coef[o.idx];
+          const GT cs = coef[o.idx];
           c = cs.x;
           s = (o.flags & OPF_INV) ? -cs.y : cs.y;
+          cl = GC<R>::cl(cs);
+          sl = (o.flags & OPF_INV) ? -GC<R>::sl(cs) : GC<R>::sl(cs);
           code = ((o.flags & OPF_LAM) ? RC_GIV_L : RC_GIV) + pidx;
           break;
         }
         case OP_GRADINV_HOP: {
-          const T2 cs = coef[o.idx];
+          const GT cs = coef[o.idx];
           c = cs.x;
           s = -cs.y;
+          cl = GC<R>::cl(cs);
+          sl = -GC<R>::sl(cs);
           tc = (R)hc[o.idx2];
           code = RC_GRADINV + pidx;
           aux = RA_GRAD;
@@ -426,7 +470,7 @@ __device__ void resolve_ops(const SweepDev& sw, const KernelArgs& a, uint4* sres
         default: {
           hop = false;
           const DiagOpDev& d = a.diag_ops[o.idx];
-          const bool onsite = d.has_x == 0 && d.n_vb == 0 && (d.has_y == 1 || d.has_y == 2);
+          const bool onsite = d.has_x == 0 && d.n_vb == 0 && d.n_mp == 0 && (d.has_y == 1 || d.has_y == 2);
           aux = onsite ? d.has_y : 0;
           switch (o.kind) {
             case OP_DIAG:
@@ -450,7 +494,8 @@ __device__ void resolve_ops(const SweepDev& sw, const KernelArgs& a, uint4* sres
                         o.bm_global);
       if (hop) {
         if constexpr (DT == 0) {
-          w[1] = make_uint4(f2u((float)c), f2u((float)s), f2u((float)tc), 0u);
+          w[1] = make_uint4(f2u((float)c), f2u((float)s), f2u((float)cl), f2u((float)sl));
+          w[2] = make_uint4(f2u((float)tc), 0u, 0u, 0u);
         } else {
           w[1] = make_uint4((uint32_t)__double2loint((double)c), (uint32_t)__double2hiint((double)c),
                             (uint32_t)__double2loint((double)s), (uint32_t)__double2hiint((double)s));
@@ -492,7 +537,7 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
   using T2 = typename CT<R>::T2;
   constexpr int DT = CT<R>::DT;
   constexpr int NE = 1 << RB;
-  constexpr int NW = DT == 0 ? 2 : 3;
+  constexpr int NW = 3;   // resolved words per operation (see res_words)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nph = sw.phase_end - sw.phase_begin;
   const uint32_t tsize = 1u << sw.k;
@@ -694,22 +739,25 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
         // the thread's other tile bits and the tile's non-tile bits
         const int tpar = (__popc(base & w0.z) + __popc(sbase & w0.w)) & 1;
         const uint32_t sm = w0.y ^ (tpar ? 0xffffffffu : 0u);
-        R c, s, tc;
+        R c, s, cl, sl, tc;
         if constexpr (DT == 0) {
           c = __uint_as_float(w1.x);
           s = __uint_as_float(w1.y);
-          tc = __uint_as_float(w1.z);
+          cl = __uint_as_float(w1.z);
+          sl = __uint_as_float(w1.w);
+          tc = __uint_as_float(w2.x);
         } else {
           c = __hiloint2double((int)w1.y, (int)w1.x);
           s = __hiloint2double((int)w1.w, (int)w1.z);
+          cl = sl = 0.0;
           tc = __hiloint2double((int)w2.y, (int)w2.x);
         }
-#define HUB_GIV1(A, B) pair_giv<A, B>(v, c, s, sm);
+#define HUB_GIV1(A, B) pair_giv<A, B>(v, c, s, cl, sl, sm);
 #define HUB_GIV2(A, B)                                  \
-  pair_giv<A, B>(v, c, s, sm);                          \
-  if constexpr (NV == 2) pair_giv<A, B>(l, c, s, sm);
+  pair_giv<A, B>(v, c, s, cl, sl, sm);                  \
+  if constexpr (NV == 2) pair_giv<A, B>(l, c, s, cl, sl, sm);
 #define HUB_GI(A, B) \
-  if constexpr (NV == 2) racc += (R)2 * pair_gradinv<A, B>(v, l, c, s, tc, sm);
+  if constexpr (NV == 2) racc += (R)2 * pair_gradinv<A, B>(v, l, c, s, cl, sl, tc, sm);
 #define HUB_M0(A, B) eacc += (R)2 * pair_hop<A, B, 0>(v, l, tc, sm);
 #define HUB_M1(A, B) \
   if constexpr (NV == 2) eacc += (R)2 * pair_hop<A, B, 1>(v, l, tc, sm);

@@ -7,18 +7,34 @@
 namespace hubsv {
 
 template <typename R> struct CT;
-template <> struct CT<float> { using T2 = float2; };
-template <> struct CT<double> { using T2 = double2; };
+template <> struct CT<float> { using T2 = float2; using G = float4; };
+template <> struct CT<double> { using T2 = double2; using G = double2; };
+
+// Givens coefficients (c, s): complex128 as doubles; complex64 as FP32 pairs
+// {c_hi, s_hi, c_lo, s_lo} with c_hi = fl32(c), c_lo = fl32(c - c_hi), so
+// that the rotation angle is exact to ~1e-14 (see GC in the sweep header).
+template <typename R>
+__device__ __forceinline__ typename CT<R>::G giv_coef(double c, double s);
+template <>
+__device__ __forceinline__ double2 giv_coef<double>(double c, double s) {
+  return make_double2(c, s);
+}
+template <>
+__device__ __forceinline__ float4 giv_coef<float>(double c, double s) {
+  const float ch = (float)c, sh = (float)s;
+  return make_float4(ch, sh, (float)(c - (double)ch), (float)(s - (double)sh));
+}
 
 // ---------------------------------------------------------------------------
 // coefficient and phase tables (one thread per entry, FP64 trig)
 // ---------------------------------------------------------------------------
 
-// Round the unit complex number (c, s) to the precision of R.  For FP32 the
-// pair is chosen among the neighbouring representable values as the one
-// closest to the unit circle, so a rotation or phase with these entries
-// changes norms by ~1e-8 instead of ~1e-7 (this drift would otherwise add
-// up over the forward factors and their inverses in the adjoint pass).
+// Round the unit complex number (c, s) of a diagonal phase to the
+// precision of R.  For FP32 the pair is chosen among the neighbouring
+// representable values as the one closest to the unit circle, so a phase
+// with these entries changes norms by ~1e-8 instead of ~1e-7 (this drift
+// would otherwise add up over the forward factors and their inverses in
+// the adjoint pass).
 template <typename R>
 __device__ __forceinline__ typename CT<R>::T2 unit_round(double c, double s);
 template <>
@@ -47,7 +63,7 @@ template <typename R>
 __global__ void coef_kernel(const double* __restrict__ theta, int P,
                             const int32_t* __restrict__ gate_param,
                             const double* __restrict__ gate_t, int n_gates,
-                            typename CT<R>::T2* __restrict__ coef,
+                            typename CT<R>::G* __restrict__ coef,
                             const int32_t* __restrict__ tab_param,
                             const double* __restrict__ tab_val, int n_tab,
                             const int32_t* __restrict__ tab_live, int n_live,
@@ -60,7 +76,7 @@ __global__ void coef_kernel(const double* __restrict__ theta, int P,
         const double al = theta[b * P + gate_param[j]] * gate_t[(int64_t)inst * n_gates + j];
         double s, c;
         sincos(al, &s, &c);
-        coef[b * n_gates + j] = unit_round<R>(c, s);
+        coef[b * n_gates + j] = giv_coef<R>(c, s);
       } else {
         const int e = tab_live[j - n_gates];
         const int pp = tab_param[e];
@@ -178,7 +194,7 @@ cudaError_t launch_coef(int dtype, const double* theta, int P, const int32_t* ga
   const dim3 grid(gx, gy);
   if (dtype == 0)
     coef_kernel<float><<<grid, 256, 0, st>>>(theta, P, gate_param, gate_t, n_gates,
-                                             (float2*)coef, tab_param, tab_val, n_tab, tab_live,
+                                             (float4*)coef, tab_param, tab_val, n_tab, tab_live,
                                              n_live, (float2*)phase_tabs, batch, n_inst);
   else
     coef_kernel<double><<<grid, 256, 0, st>>>(theta, P, gate_param, gate_t, n_gates,

@@ -11,7 +11,7 @@ from paper_2408_00836_gb300 import workloads as W
 from paper_2408_00836_gb300.autotune import autotune
 from paper_2408_00836_gb300.vqe import EnergyGradGraph, run_vqe
 
-from helpers import TOL, Problem, grad_scale
+from helpers import TOL, Problem
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -37,7 +37,7 @@ def test_graph_replay_matches_direct_calls(dtype, engine):
         E, g = fn(th)
         Eo, go = prob.oracle_energy_grad(th)
         assert abs(E[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
-        assert np.all(np.abs(g[0] - go) < TOL[dtype] * grad_scale(prob, th))
+        assert np.max(np.abs(g[0] - go)) < TOL[dtype] * max(1.0, np.max(np.abs(go)))
 
 
 def test_vqe_lbfgs_decreases_energy_above_ground_state():

@@ -103,8 +103,7 @@ def test_disordered_extended_2x3_all_group_kinds(modes, dtype, engine):
     log_errors(f"disordered_2x3[{modes}]", dtype, engine, energy=energy_err(E2[0], Eo),
                grad=grad_err(g[0], go))
     assert abs(E2[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
-    # strong disorder (t = 1 +- 0.8, potentials +- 0.8): per-term scale, see grad_scale
-    assert np.all(np.abs(g[0] - go) < TOL[dtype] * grad_scale(prob, theta))
+    assert grad_err(g[0], go) < TOL[dtype], grad_err(g[0], go)
     assert g[0][6] == 0.0 and g[0][13] == 0.0      # v2 is empty on two rows
     E3, _, _ = _run(prob, theta, dtype, grad=False, engine=engine)
     assert abs(E3[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
@@ -127,7 +126,7 @@ def test_bond_dependent_V_2x3(modes, dtype, engine):
     E, g, _ = _run(prob, theta, dtype, engine=engine)
     log_errors(f"bond_V_2x3[{modes}]", dtype, engine, energy=energy_err(E[0], Eo), grad=grad_err(g[0], go))
     assert abs(E[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
-    assert np.all(np.abs(g[0] - go) < TOL[dtype] * grad_scale(prob, theta))
+    assert grad_err(g[0], go) < TOL[dtype], grad_err(g[0], go)
 
 
 @pytest.mark.parametrize("fill", [(0, 3), (6, 2), (1, 5), (3, 0), (6, 6)])
@@ -143,12 +142,20 @@ def test_edge_sectors_all_engines(fill, dtype):
                    classes=("U", "V", "h1", "v1", "h2"))
     theta = np.random.default_rng(9).uniform(-math.pi, math.pi, prob.P)
     Eo, go = prob.oracle_energy_grad(theta)
-    gs = grad_scale(prob, theta)
+    # The filled lattice (6, 6) is a single basis state: g = 0 exactly while
+    # each adjoint term 2 Im<lam_k|G_k|psi_k> is of size ||H psi|| ||G psi||
+    # (~500), so its rounding is judged against those terms (grad_scale);
+    # every other sector takes the stated bound 1e-6 max(1, |g|inf).
+    single = n_up in (0, 6) and n_dn in (0, 6)
+    gs = grad_scale(prob, theta) if single else None
     for engine in ("auto", "rows", "sweeps"):
         E, g, _ = _run(prob, theta, dtype, engine=engine)
         log_errors(f"edge_sector{fill}", dtype, engine, energy=energy_err(E[0], Eo), grad=grad_err(g[0], go))
         assert abs(E[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
-        assert np.all(np.abs(g[0] - go) < TOL[dtype] * gs)
+        if single:
+            assert np.all(np.abs(g[0] - go) < TOL[dtype] * gs)
+        else:
+            assert grad_err(g[0], go) < TOL[dtype], grad_err(g[0], go)
     if n_up in (0, 6) and n_dn in (0, 6):   # one basis state: no hopping can act
         assert np.max(np.abs(go)) < 1e-12
 
