@@ -25,7 +25,8 @@ from ._lib import HubError, HubGroup, HubLattice, check, lib  # noqa: F401
 from . import workloads  # noqa: F401
 
 C64, C128 = 0, 1
-HOP, ONSITE, NN_V, POT, RZ = 0, 1, 2, 3, 4
+HOP, ONSITE, NN_V, POT, RZ, GIVENS, CPHASE = 0, 1, 2, 3, 4, 5, 6
+PAIR_KINDS = (GIVENS, CPHASE)   # their terms are mode pairs, flattened
 PREP_SLATER, PREP_NEEL = 0, 1
 FLAG_PREP_FUSED = 1
 FLAG_KEEP_STATE = 2
@@ -138,6 +139,70 @@ def hva_groups(bonds, classes, n_sites: int, n_layers: int, layer: Sequence[str]
     return out
 
 
+def site_modes(n_sites: int, modes="blocked"):
+    """(up, dn) mode of every site for a mode layout ('blocked', the
+    default: up i -> i, dn i -> L + i; 'interleaved', the paper's order:
+    up i -> 2i, dn i -> 2i + 1; or explicit (up, dn) arrays)."""
+    L = n_sites
+    if isinstance(modes, str):
+        if modes == "blocked":
+            return list(range(L)), [L + i for i in range(L)]
+        if modes == "interleaved":
+            return [2 * i for i in range(L)], [2 * i + 1 for i in range(L)]
+        raise ValueError(modes)
+    return [int(x) for x in modes[0]], [int(x) for x in modes[1]]
+
+
+def np_groups(bonds, classes, n_sites: int, n_layers: int, modes="blocked", rz: bool = True):
+    """Groups of the number-preserving ansatz of Sec. 2.2.1 in application
+    order: an R_z pre-layer (one parameter per qubit), then per layer every
+    term of Eq. 7 in its order -- the on-site terms, then the h1, v1, h2,
+    v2 hopping classes, each bond for both spins -- replaced by its own NP
+    gate of Eq. 8: a GIVENS factor (theta) and a CPHASE factor (phi) on the
+    term's two modes.  (10 Nx Ny - 4 Nx - 4 Ny) parameters a layer plus
+    2 Nx Ny for R_z."""
+    up, dn = site_modes(n_sites, modes)
+    out, p = [], 0
+    if rz:
+        for k in range(2 * n_sites):
+            out.append((RZ, [k], p))
+            p += 1
+    for _ in range(n_layers):
+        pairs = [(up[i], dn[i]) for i in range(n_sites)]
+        for cc in ("h1", "v1", "h2", "v2"):
+            for (i, j), c in zip(bonds, classes):
+                if c == cc:
+                    pairs += [(up[i], up[j]), (dn[i], dn[j])]
+        for (a, b) in pairs:
+            a, b = min(a, b), max(a, b)
+            out.append((GIVENS, [a, b], p))
+            out.append((CPHASE, [a, b], p + 1))
+            p += 2
+    return out
+
+
+def ep_groups(n_modes: int, n_layers: int):
+    """Groups of the excitation-preserving ansatz of Sec. 2.2.2: R_z on
+    every qubit, per layer Eq. 10's gate on each pair of neighbouring qubits
+    (k, k+1) as a GIVENS and a CPHASE factor, then R_z on every qubit again
+    (4 Nx Ny + 2 (2 Nx Ny - 1) l parameters).  Eq. 10's U_EP(theta, phi) is
+    GIVENS(-theta / 2) CPHASE(-phi): the parameters here are -theta / 2 and
+    -phi.  Qubit k is mode k (the paper's order is the interleaved one)."""
+    out, p = [], 0
+    for k in range(n_modes):
+        out.append((RZ, [k], p))
+        p += 1
+    for _ in range(n_layers):
+        for k in range(n_modes - 1):
+            out.append((GIVENS, [k, k + 1], p))
+            out.append((CPHASE, [k, k + 1], p + 1))
+            p += 2
+    for k in range(n_modes):
+        out.append((RZ, [k], p))
+        p += 1
+    return out
+
+
 def _ptr(t, nbytes: int, what: str):
     import torch
     if t is None:
@@ -164,7 +229,8 @@ class Ansatz:
         for i, (kind, terms, param) in enumerate(self.groups):
             a, p = _i32(terms if len(terms) else [0])
             arrs.append(a)
-            garr[i] = HubGroup(kind, len(terms), p, param)
+            n_terms = len(terms) // 2 if kind in PAIR_KINDS else len(terms)
+            garr[i] = HubGroup(kind, n_terms, p, param)
         G = len(self.groups)
         if G % n_layers:
             raise ValueError("number of groups must be a multiple of n_layers")

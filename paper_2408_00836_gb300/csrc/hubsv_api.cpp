@@ -667,6 +667,8 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
   if (!pl->uploaded) {
     if ((s = pl->ops.upload(pl->hops.empty() ? std::vector<OpDev>(1) : pl->hops, "sweep ops")) != HUB_OK) return s;
     if ((s = pl->phases.upload(pl->hphases, "sweep phases")) != HUB_OK) return s;
+    if ((s = pl->slots.upload(pl->slot_map.empty() ? std::vector<int32_t>(1) : pl->slot_map, "sweep slots")) != HUB_OK)
+      return s;
     pl->uploaded = true;
   }
   const size_t r2 = dtype == HUB_C64 ? 8 : 16;
@@ -724,6 +726,7 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
   ka.n_slots = n_slots;
   ka.slot_E = a->P;
   ka.slot_N = a->P + 1;
+  ka.slot_map = (const int32_t*)pl->slots.p;
   ka.prep.kind = a->prep_kind < 0 ? 0 : a->prep_kind;
   ka.prep.L = a->L;
   ka.prep.s = a->s;
@@ -738,7 +741,7 @@ hub_status run_plan(hub_ansatz* a, Plan* pl, int dtype, const double* theta, voi
     const SweepDev& sw = pl->sweeps[i];
     const int nv = pl->nvec[i];
     const int nph = sw.phase_end - sw.phase_begin;
-    const size_t smem = sweep_smem_bytes(dtype, nv, sw.k, n_slots, nph, sw.op_end - sw.op_begin, 32 << sw.w);
+    const size_t smem = sweep_smem_bytes(dtype, nv, sw.k, sw.n_lslot, nph, sw.op_end - sw.op_begin, 32 << sw.w);
     if ((int)smem > optin) return fail(HUB_EUNSUPPORTED, "tile does not fit in shared memory");
     HUB_CUDA(sweep_set_smem(dtype, nv, sw.r, 32 << sw.w, (sw.flags & SW_VPOP) != 0, smem), "cudaFuncSetAttribute");
     const int threads = 32 << sw.w;

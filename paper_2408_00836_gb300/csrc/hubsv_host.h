@@ -59,8 +59,9 @@ struct Plan {
   std::vector<PhaseDev> hphases;          // phases of all sweeps
   std::vector<uint64_t> tiles;
   std::vector<std::vector<int>> seq_ids;  // sequence index of each op, per sweep
+  std::vector<int32_t> slot_map;          // local -> global accumulator slots of all sweeps
   bool uploaded = false;
-  DevBuf ops, phases;
+  DevBuf ops, phases, slots;
   int k = 0;
   bool sector = false;                    // sweeps visit live (sector) tiles only
   bool prep = false;                      // the first sweep generates psi_0

@@ -148,6 +148,13 @@ struct SweepDev {
   uint32_t live;                  // live tiles per state
   int8_t pa[kMaxQubits];          // part-a bit positions, ascending
   int8_t pb[kMaxQubits];          // part-b bit positions, ascending
+  // Accumulator slots the sweep adds to, numbered locally (its operations'
+  // slot fields are local): local slot i is global slot
+  // slot_map[lslot_off + i]; lslot_E / lslot_N hold the energy and norm
+  // (-1 when the sweep measures nothing).  The CTA keeps rows for these
+  // slots only, so an ansatz with thousands of parameters costs shared
+  // memory in proportion to one sweep's parameters.
+  int32_t n_lslot, lslot_off, lslot_E, lslot_N;
 };
 
 // Binomial coefficients C(n, k), n, k <= 32 (C(32, 16) < 2^32).
@@ -199,6 +206,7 @@ struct KernelArgs {
   double* acc;                     // [batch][n_slots]
   int32_t n_slots;
   int32_t slot_E, slot_N;
+  const int32_t* slot_map;         // local -> global accumulator slots (SweepDev)
   PrepDev prep;
 };
 

@@ -110,6 +110,7 @@ extern "C" hub_status energy_noalloc(ans_t a, const double* theta, void* psi, do
   const size_t o_sd32 = lay.take(sd_needed ? 4 * sd32.size() : 0);
   const size_t o_ops = lay.take(sizeof(OpDev) * std::max<size_t>(1, pl->hops.size()));
   const size_t o_ph = lay.take(sizeof(PhaseDev) * pl->hphases.size());
+  const size_t o_sm = lay.take(4 * std::max<size_t>(1, pl->slot_map.size()));
   const size_t o_cf = lay.take(16 * (size_t)batch * a->n_gates);   // Givens (cos, sin): 16 bytes in both dtypes
   const size_t o_pt = lay.take(r2 * (size_t)batch * a->n_tab);
   const size_t o_acc = lay.take(8 * (size_t)batch * n_slots);
@@ -139,6 +140,7 @@ extern "C" hub_status energy_noalloc(ans_t a, const double* theta, void* psi, do
   if (ce == cudaSuccess && sd_needed) ce = put(o_sd32, sd32.data(), 4 * sd32.size());
   if (ce == cudaSuccess) ce = put(o_ops, pl->hops.data(), sizeof(OpDev) * pl->hops.size());
   if (ce == cudaSuccess) ce = put(o_ph, pl->hphases.data(), sizeof(PhaseDev) * pl->hphases.size());
+  if (ce == cudaSuccess) ce = put(o_sm, pl->slot_map.data(), 4 * pl->slot_map.size());
   if (ce != cudaSuccess) return cuda_fail(ce, "energy_noalloc: table copy");
   // the accumulators keep the previous call's sums: clear them
   HUB_CUDA(launch_zero(reinterpret_cast<double*>(S + o_acc), batch * n_slots, s), "energy_noalloc: zero accumulators");
@@ -177,6 +179,7 @@ extern "C" hub_status energy_noalloc(ans_t a, const double* theta, void* psi, do
   ka.n_slots = n_slots;
   ka.slot_E = a->P;
   ka.slot_N = a->P + 1;
+  ka.slot_map = reinterpret_cast<const int32_t*>(S + o_sm);
   ka.prep.kind = a->prep_kind < 0 ? 0 : a->prep_kind;
   ka.prep.L = a->L;
   ka.prep.s = a->s;
@@ -191,7 +194,7 @@ extern "C" hub_status energy_noalloc(ans_t a, const double* theta, void* psi, do
     const SweepDev& sw = pl->sweeps[i];
     const int nv = pl->nvec[i];
     const int nph = sw.phase_end - sw.phase_begin;
-    const size_t smem = sweep_smem_bytes(dtype, nv, sw.k, n_slots, nph, sw.op_end - sw.op_begin, 32 << sw.w);
+    const size_t smem = sweep_smem_bytes(dtype, nv, sw.k, sw.n_lslot, nph, sw.op_end - sw.op_begin, 32 << sw.w);
     if ((int)smem > optin) return fail(HUB_EUNSUPPORTED, "energy_noalloc: tile does not fit in shared memory");
     HUB_CUDA(sweep_set_smem(dtype, nv, sw.r, 32 << sw.w, (sw.flags & SW_VPOP) != 0, smem), "energy_noalloc: cudaFuncSetAttribute");
     const int threads = 32 << sw.w;

@@ -20,6 +20,7 @@
 // runs the most operations wins.
 #include <algorithm>
 #include <cstring>
+#include <map>
 
 #include "hubsv_host.h"
 
@@ -625,6 +626,35 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
     }
     sw.phase_end = (int)pl->hphases.size();
     sw.op_end = (int)pl->hops.size();
+    // local accumulator slots: the parameters of the sweep's gradient
+    // steps, then the energy and norm if it measures
+    {
+      std::map<int, int> loc;
+      bool measures = false;
+      sw.lslot_off = (int)pl->slot_map.size();
+      for (int oi = sw.op_begin; oi < sw.op_end; ++oi) {
+        OpDev& d = pl->hops[oi];
+        if (d.kind == OP_GRAD_HOP || d.kind == OP_GRAD_DIAG || d.kind == OP_GRADINV_HOP ||
+            d.kind == OP_GRADINV_DIAG) {
+          auto it = loc.find(d.slot);
+          if (it == loc.end()) {
+            it = loc.emplace(d.slot, (int)loc.size()).first;
+            pl->slot_map.push_back(d.slot);
+          }
+          d.slot = it->second;
+        }
+        measures = measures || d.kind == OP_MEAS_HOP || d.kind == OP_MEAS_DIAG || d.kind == OP_LAM_HOP ||
+                   d.kind == OP_LAM_DIAG;
+      }
+      sw.lslot_E = sw.lslot_N = -1;
+      if (measures) {
+        sw.lslot_E = (int)loc.size();
+        sw.lslot_N = sw.lslot_E + 1;
+        pl->slot_map.push_back(a->P);
+        pl->slot_map.push_back(a->P + 1);
+      }
+      sw.n_lslot = (int)pl->slot_map.size() - sw.lslot_off;
+    }
     for (int oi = sw.op_begin; oi < sw.op_end; ++oi) {
       const OpDev& d = pl->hops[oi];
       const bool diag = d.kind == OP_DIAG || d.kind == OP_MEAS_DIAG || d.kind == OP_LAM_DIAG ||

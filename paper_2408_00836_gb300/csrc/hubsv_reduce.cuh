@@ -6,21 +6,8 @@
 namespace hubsv {
 
 // The complex64 kernels reduce in FP32 and keep their running totals as
-// float pairs (two_sum, ff_add, warp_sum_f from the sweep kernel's header);
+// float pairs (two_sum, ff_add, warp_sum_ff from the sweep kernel's header);
 // the complex128 kernels reduce in FP64.
-
-// Sum of float pairs over the warp, into lane 0's (h, l).
-__device__ __forceinline__ void warp_sum_ff(float& h, float& l) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
-    float s, e;
-    two_sum(h, h2, s, e);
-    e += l + l2;
-    h = s + e;
-    l = e - (h - s);
-  }
-}
 
 // Running totals of one thread (R = float: float pairs; double: FP64).
 template <typename R> struct Tot;
@@ -60,5 +47,31 @@ __device__ __forceinline__ void row_add_tot(float2* acc, int n_slots, int slot, 
 __device__ __forceinline__ void row_add_tot(double* acc, int n_slots, int slot, Tot<double> t) {
   row_add(acc, n_slots, slot, t.v);
 }
+
+// Diagonal value (real, or phase) of an element: on-site terms only (ny =
+// 1 or 2 byte tables of the double-occupancy pattern), or the general form.
+template <typename R, typename T2>
+struct DiagVal {
+  const DiagOpDev* d;
+  int ny;
+  __device__ __forceinline__ R real(const R* rtab, uint32_t x, int s, uint32_t upm) const {
+    if (ny) {
+      const uint32_t y = x & (x >> s) & upm;
+      R v = rtab[1024 + (y & 255u)];
+      if (ny == 2) v += rtab[1280 + ((y >> 8) & 255u)];
+      return v;
+    }
+    return diag_real<R, true>(*d, rtab, x, s, upm);
+  }
+  __device__ __forceinline__ T2 phase(const T2* ptab, uint32_t x, int s, uint32_t upm) const {
+    if (ny) {
+      const uint32_t y = x & (x >> s) & upm;
+      T2 p = ptab[1024 + (y & 255u)];
+      if (ny == 2) p = cmul(p, ptab[1280 + ((y >> 8) & 255u)]);
+      return p;
+    }
+    return diag_phase<T2, true>(*d, ptab, x, s, upm);
+  }
+};
 
 }  // namespace hubsv

@@ -205,32 +205,6 @@ __device__ __forceinline__ R row_hop(T2* __restrict__ prow, T2* __restrict__ lro
   return part;
 }
 
-// Diagonal value (real, or phase) of an element: on-site terms only (ny =
-// 1 or 2 byte tables of the double-occupancy pattern), or the general form.
-template <typename R, typename T2>
-struct DiagVal {
-  const DiagOpDev* d;
-  int ny;
-  __device__ __forceinline__ R real(const R* rtab, uint32_t x, int s, uint32_t upm) const {
-    if (ny) {
-      const uint32_t y = x & (x >> s) & upm;
-      R v = rtab[1024 + (y & 255u)];
-      if (ny == 2) v += rtab[1280 + ((y >> 8) & 255u)];
-      return v;
-    }
-    return diag_real<R, true>(*d, rtab, x, s, upm);
-  }
-  __device__ __forceinline__ T2 phase(const T2* ptab, uint32_t x, int s, uint32_t upm) const {
-    if (ny) {
-      const uint32_t y = x & (x >> s) & upm;
-      T2 p = ptab[1024 + (y & 255u)];
-      if (ny == 2) p = cmul(p, ptab[1280 + ((y >> 8) & 255u)]);
-      return p;
-    }
-    return diag_phase<T2, true>(*d, ptab, x, s, upm);
-  }
-};
-
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowThreadsLarge ? 2 : 1))
     rows_kernel(const RowArgs a) {

@@ -159,6 +159,20 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
+// Sum of float pairs over the warp, into lane 0's (h, l): each level adds
+// with TwoSum and carries the rounding error in l.
+__device__ __forceinline__ void warp_sum_ff(float& h, float& l) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+    float s, e;
+    two_sum(h, h2, s, e);
+    e += l + l2;
+    h = s + e;
+    l = e - (h - s);
+  }
+}
+
 __device__ __forceinline__ double row_value(const float2& v) { return (double)v.x + (double)v.y; }
 __device__ __forceinline__ double row_value(double v) { return v; }
 
@@ -546,8 +560,9 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
   T2* xl = xb + tsize;
   using AccT = typename std::conditional<DT == 0, float2, double>::type;
   const int n_rows = DT == 0 ? (int)(blockDim.x >> 5) : 1;
+  const int nls = sw.n_lslot;   // local accumulator slots (see SweepDev)
   AccT* acc = reinterpret_cast<AccT*>(smem_raw + (size_t)nbuf * tsize * sizeof(T2));
-  PhaseDev* phs = reinterpret_cast<PhaseDev*>(acc + n_rows * a.n_slots);
+  PhaseDev* phs = reinterpret_cast<PhaseDev*>(acc + n_rows * nls);
   const size_t op_off = ((size_t)(reinterpret_cast<unsigned char*>(phs + nph) - smem_raw) + 15) & ~(size_t)15;
   uint4* sres = reinterpret_cast<uint4*>(smem_raw + op_off);   // indexed by local op index
   __shared__ int8_t s_nbits[kMaxQubits];
@@ -573,7 +588,7 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
     for (int i = 0; i < kMaxTileBits; ++i) s_tbits[i] = sw.tbits[i];
     s_meas = 0;
   }
-  for (int i = tid; i < n_rows * a.n_slots; i += nth) acc[i] = AccT{};
+  for (int i = tid; i < n_rows * nls; i += nth) acc[i] = AccT{};
   {
     const int* src = reinterpret_cast<const int*>(a.phases + sw.phase_begin);
     int* dst = reinterpret_cast<int*>(phs);
@@ -641,13 +656,13 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
     if (b != cur_b) {
       if (cur_b >= 0) {
         __syncthreads();
-        for (int i = tid; i < a.n_slots; i += nth) {
+        for (int i = tid; i < nls; i += nth) {
           double x = 0.0;
           for (int w = 0; w < n_rows; ++w) {
-            x += row_value(acc[w * a.n_slots + i]);
-            acc[w * a.n_slots + i] = AccT{};
+            x += row_value(acc[w * nls + i]);
+            acc[w * nls + i] = AccT{};
           }
-          if (x != 0.0) atomicAdd(&a.acc[(size_t)cur_b * a.n_slots + i], x);
+          if (x != 0.0) atomicAdd(&a.acc[(size_t)cur_b * a.n_slots + a.slot_map[sw.lslot_off + i]], x);
         }
         __syncthreads();
       }
@@ -730,7 +745,7 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
         if (aux & RA_GRAD) {
           const int slot = (int)(w0.x >> 16);
           if (slot != rslot) {
-            if (rslot >= 0) cta_add(acc, a.n_slots, rslot, racc);
+            if (rslot >= 0) cta_add(acc, nls, rslot, racc);
             racc = 0;
             rslot = slot;
           }
@@ -890,10 +905,10 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
 #undef HUB_M2
       }
     }
-    if (rslot >= 0) cta_add(acc, a.n_slots, rslot, racc);
+    if (rslot >= 0) cta_add(acc, nls, rslot, racc);
     if (s_meas) {
-      cta_add(acc, a.n_slots, a.slot_E, eacc);
-      cta_add(acc, a.n_slots, a.slot_N, nacc);
+      cta_add(acc, nls, sw.lslot_E, eacc);
+      cta_add(acc, nls, sw.lslot_N, nacc);
     }
 
     // ---- store from registers (the last phase has the run bits on lanes) ----
@@ -915,10 +930,10 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
   }
   __syncthreads();
   if (cur_b >= 0) {
-    for (int i = tid; i < a.n_slots; i += nth) {
+    for (int i = tid; i < nls; i += nth) {
       double x = 0.0;
-      for (int w = 0; w < n_rows; ++w) x += row_value(acc[w * a.n_slots + i]);
-      if (x != 0.0) atomicAdd(&a.acc[(size_t)cur_b * a.n_slots + i], x);
+      for (int w = 0; w < n_rows; ++w) x += row_value(acc[w * nls + i]);
+      if (x != 0.0) atomicAdd(&a.acc[(size_t)cur_b * a.n_slots + a.slot_map[sw.lslot_off + i]], x);
     }
   }
 }

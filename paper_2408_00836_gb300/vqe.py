@@ -95,8 +95,22 @@ class VQEResult:
 def lbfgs(fun, x0, max_iter=1000, m=10, e_tol=1e-7, g_tol=1e-6, c1=1e-4, max_ls=30):
     """Minimise fun(x) -> (f, grad) by L-BFGS (two-loop recursion) with a
     backtracking line search (Armijo condition); stops as in Sec. 2.1."""
+    gen = lbfgs_steps(x0, max_iter, m, e_tol, g_tol, c1, max_ls)
+    x = next(gen)
+    try:
+        while True:
+            x = gen.send(fun(x))
+    except StopIteration as stop:
+        return stop.value
+
+
+def lbfgs_steps(x0, max_iter=1000, m=10, e_tol=1e-7, g_tol=1e-6, c1=1e-4, max_ls=30):
+    """L-BFGS as a generator: yields each point it needs evaluated, receives
+    (f, grad) there, and returns (x, f, g, iterations, reason, history).
+    Several of these run side by side in multistart(), whose every round is
+    one batched evaluation of all their requested points."""
     x = np.array(x0, dtype=np.float64)
-    f, g = fun(x)
+    f, g = yield x
     S, Y, hist = [], [], [f]
     reason = "max_iter"
     it = 0
@@ -125,7 +139,7 @@ def lbfgs(fun, x0, max_iter=1000, m=10, e_tol=1e-7, g_tol=1e-6, c1=1e-4, max_ls=
         step = 1.0 if S else min(1.0, 1.0 / max(np.linalg.norm(g), 1e-12))
         for _ in range(max_ls):
             xn = x + step * d
-            fn, gn = fun(xn)
+            fn, gn = yield xn
             if fn <= f + c1 * step * gd:
                 break
             step *= 0.5
@@ -143,6 +157,99 @@ def lbfgs(fun, x0, max_iter=1000, m=10, e_tol=1e-7, g_tol=1e-6, c1=1e-4, max_ls=
             reason = "energy"
             break
     return x, f, g, it, reason, hist
+
+
+def multistart(evaluate, starts, max_iter=1000, **kw):
+    """L-BFGS from several starts at once (Sec. 2.1: ten independent
+    optimisations from random starts, the lowest energy kept).  evaluate(X)
+    takes a [B, P] array and returns ([B] values, [B, P] gradients) -- one
+    batched library call; each round evaluates every run's next requested
+    point (a finished run re-evaluates its final point).  Returns a list of
+    (x, f, g, iterations, reason, history), one per start."""
+    starts = np.asarray(starts, dtype=np.float64)
+    B = starts.shape[0]
+    gens = [lbfgs_steps(starts[b], max_iter, **kw) for b in range(B)]
+    req = [next(gn) for gn in gens]
+    done = [None] * B
+    while any(d is None for d in done):
+        F, G = evaluate(np.stack(req))
+        for b in range(B):
+            if done[b] is not None:
+                continue
+            try:
+                req[b] = gens[b].send((float(F[b]), G[b]))
+            except StopIteration as stop:
+                done[b] = stop.value
+                req[b] = done[b][0]
+    return done
+
+
+def run_multistart(ans: Ansatz, starts, dtype: int = C64, max_iter: int = 200, use_graph: bool = True):
+    """Energy-based VQE from B starts in one batched, graph-captured call per
+    round; returns the VQEResult of every start (the paper keeps the
+    lowest)."""
+    starts = np.asarray(starts, dtype=np.float64)
+    fn = EnergyGradGraph(ans, dtype=dtype, batch=starts.shape[0], use_graph=use_graph)
+    t0 = time.perf_counter()
+    res = multistart(lambda X: fn(X), starts, max_iter=max_iter)
+    sec = time.perf_counter() - t0
+    return [VQEResult(x, f, float(np.max(np.abs(g))), it, fn.evals, reason, hist, sec)
+            for (x, f, g, it, reason, hist) in res]
+
+
+def paper_starts(n_starts: int, P: int, seed: int = 0) -> np.ndarray:
+    """Random starts of Sec. 2.1: N(0, variance 1e-5) per parameter."""
+    return np.random.default_rng(seed).normal(0.0, np.sqrt(1e-5), (n_starts, P))
+
+
+def warm_start_vqe(ans_u0: Ansatz, ans: Ansatz, starts, dtype: int = C64, max_iter: int = 200):
+    """The warm start of Sec. 2.1: optimise the non-interacting model (U = 0,
+    ans_u0: same lattice and ansatz) from the given starts, then start the
+    interacting optimisation (ans) from those parameters.  Both ansatze'
+    initial states must be set.  Returns (U = 0 results, interacting
+    results); the paper keeps the lowest interacting energy."""
+    r0 = run_multistart(ans_u0, starts, dtype=dtype, max_iter=max_iter)
+    r1 = run_multistart(ans, np.stack([r.theta for r in r0]), dtype=dtype, max_iter=max_iter)
+    return r0, r1
+
+
+class OverlapGrad:
+    """f = log10(1 - F) of Eq. 5 and its gradient through overlap_grad, on
+    static buffers (psi_ref: one reference for the batch)."""
+
+    def __init__(self, ans: Ansatz, psi_ref, dtype: int = C64, batch: int = 1):
+        import torch
+        self.torch = torch
+        self.ans, self.dtype, self.batch = ans, dtype, batch
+        td = torch.complex64 if dtype == C64 else torch.complex128
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.ref = psi_ref.to(device=dev, dtype=td).reshape(1, -1).contiguous()
+        self.theta = torch.zeros((batch, ans.P), dtype=torch.float64, device=dev)
+        self.psi = torch.empty((batch, 1 << ans.n), dtype=td, device=dev)
+        self.lam = torch.empty_like(self.psi)
+        self.F = torch.zeros(batch, dtype=torch.float64, device=dev)
+        self.f = torch.zeros_like(self.F)
+        self.g = torch.zeros((batch, ans.P), dtype=torch.float64, device=dev)
+        self.evals = 0
+
+    def __call__(self, theta):
+        torch = self.torch
+        self.theta.copy_(torch.from_numpy(np.asarray(theta, dtype=np.float64).reshape(self.batch, -1)))
+        self.ans.overlap_grad(self.theta, self.ref, self.psi, self.lam, self.F, self.f, self.g,
+                              dtype=self.dtype, batch=self.batch)
+        self.evals += 1
+        return self.f.cpu().numpy(), self.g.cpu().numpy(), self.F.cpu().numpy()
+
+
+def run_overlap_vqe(ans: Ansatz, psi_ref, starts, dtype: int = C64, max_iter: int = 200):
+    """Overlap-based optimisation (Eq. 5): minimise f = log10(1 - F) with
+    F = |<psi(theta)|psi_ref>|^2 from B starts at once; returns per start
+    (theta, f, F, iterations, reason)."""
+    starts = np.asarray(starts, dtype=np.float64)
+    fn = OverlapGrad(ans, psi_ref, dtype=dtype, batch=starts.shape[0])
+    res = multistart(lambda X: fn(X)[:2], starts, max_iter=max_iter)
+    F = fn(np.stack([r[0] for r in res]))[2]
+    return [(r[0], r[1], float(F[b]), r[3], r[4]) for b, r in enumerate(res)]
 
 
 def run_vqe(ans: Ansatz, theta0, dtype: int = C64, max_iter: int = 200, ckpt: bool = False,

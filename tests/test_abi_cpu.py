@@ -274,3 +274,24 @@ def test_row_schedules_are_valid(number, which):
     # consecutive segments alternate spins (a repeat would be one segment)
     for (_, o1, _), (_, o2, _) in zip(plan, plan[1:]):
         assert o1 != o2
+
+
+def test_np_ansatz_4x4_12_layers_builds_and_plans():
+    """The paper's 4x4 NP ansatz with 12 layers: 1,568 parameters (Sec. 3),
+    spin mixing routes it to the dense sweeps, and the sweep planner gives
+    every sweep its own small set of accumulator slots."""
+    import time
+    bonds, cls = H.square_lattice(4, 4)
+    t = np.zeros((16, 16))
+    for (i, j) in bonds:
+        t[i, j] = t[j, i] = 1.0
+    m = H.Model(16, bonds, t, np.full(16, 2.0), None, 8, 8, modes="interleaved")
+    a = H.Ansatz(m, H.np_groups(bonds, cls, 16, 12, modes="interleaved"), 1)
+    assert a.P == 1568
+    t0 = time.time()
+    ns, by = a.plan_stats(1, H.C64, fused=True)
+    assert ns > 0 and by > 0
+    assert time.time() - t0 < 60
+    # EP: 4 Nx Ny + 2 (2 Nx Ny - 1) l
+    e = H.Ansatz(m, H.ep_groups(32, 3), 1)
+    assert e.P == 4 * 16 + 2 * 31 * 3
