@@ -330,8 +330,11 @@ def run_gpu(args, rank, world, dist):
         a.set_runs(dtype, args.runs)
     theta_h = torch.tensor(w.theta(), dtype=torch.float64).pin_memory()
     theta = theta_h.to(dev)
-    psi = torch.empty((batch, 1 << w.n_qubits), dtype=tdt, device=dev)
-    lam = torch.empty_like(psi)
+    # workspaces of the size the call needs (the row engine: the sector
+    # matrix and its transpose; on chip: none; dense sweeps: 2^n amplitudes)
+    ws_bytes, ws_engine = a.workspace(1, dtype, batch, sweeps=args.sweeps)
+    psi = H.workspace_tensor(a, 1, dtype, batch, device=dev, sweeps=args.sweeps)
+    lam = H.workspace_tensor(a, 1, dtype, batch, device=dev, sweeps=args.sweeps)
     E = torch.empty(batch, dtype=torch.float64, device=dev)
     g = torch.empty((batch, a.P), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
@@ -437,7 +440,9 @@ def run_gpu(args, rank, world, dist):
            "dtype": args.dtype, "data": "synthetic (seeded inputs of the named workload)",
            "config": {"workload": WORKLOAD_TEXT.get(args.workload, w.name), "qubits": w.n_qubits,
                       "params": a.P, "batch_per_gpu": batch, "parallelism": f"replicas x{world}",
-                      "l2": "inputs larger than L2 (psi = %.1f GB for the batch)" % (batch * a.amp_bytes(dtype) / 1e9)},
+                      "workspace_gb_per_vector": round(ws_bytes / 1e9, 3),
+                      "l2": "inputs larger than L2 (dense psi = %.1f GB for the batch; the engine's "
+                            "working set is larger than L2 too)" % (batch * a.amp_bytes(dtype) / 1e9)},
            "hbm_tbs": round(hbm_tbs, 3),
            "plan": ({"engine": "on-chip (one CTA per state, sector amplitudes in shared memory)",
                      "hbm_bytes_per_eval": 0} if on_chip else
@@ -452,12 +457,29 @@ def run_gpu(args, rank, world, dist):
         out["config"]["log2_tile"] = args.tile
     if args.runs:
         out["config"]["log2_run"] = args.runs
-    if rows_engine and not args.sweeps:
-        out["dense_sweeps"] = run_sweeps_leg(args, a, H, torch, theta, psi, lam, E, g, dtype, batch, names)
     del psi, lam
     torch.cuda.empty_cache()
+    if rows_engine and not args.sweeps and args.dense:
+        psi = torch.empty((batch, 1 << w.n_qubits), dtype=tdt, device=dev)
+        lam = torch.empty_like(psi)
+        out["dense_sweeps"] = run_sweeps_leg(args, a, H, torch, theta, psi, lam, E, g, dtype, batch, names)
+        del psi, lam
+        torch.cuda.empty_cache()
     if args.c128 and dtype == H.C64 and rank == 0:
         out["c128"] = run_c128(args, w, a, H, torch, dev, theta, ms_step)
+        # the c64 / c128 ratio on one engine: dense sweeps at this size (the
+        # row engine cannot hold a c128 row with lam here), rows at 28 qubits
+        c128_eng = out["c128"].get("engine")
+        prec = {}
+        if c128_eng == "sweeps" and "dense_sweeps" in out:
+            prec["sweeps_" + str(w.n_qubits) + "q"] = {
+                "c64_evals_per_s": out["dense_sweeps"]["value"], "c128_evals_per_s": out["c128"]["value"],
+                "c64_speedup_same_engine": round(out["dense_sweeps"]["value"] / out["c128"]["value"], 3)}
+        if args.workload == 5:
+            prec["rows_28q"] = run_precision_28q(H, torch, dev)
+        out["precision"] = prec
+    if args.np_leg and rank == 0 and args.workload == 5:
+        out["np_ansatz"] = run_np_leg(H, torch, dev)
     return out
 
 
@@ -493,6 +515,71 @@ def run_sweeps_leg(args, a, H, torch, theta, psi, lam, E, g, dtype, batch, names
                          "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": peak_kind}}
 
 
+def run_precision_28q(H, torch, dev, steps=5):
+    """complex64 against complex128 on the same engine: the 28-qubit
+    workload (grid2x7) on the row engine, both precisions, a few steps."""
+    w, a = build_problem(4, H)
+    out = {"workload": WORKLOAD_TEXT[4]}
+    theta = torch.tensor(w.theta(), dtype=torch.float64, device=dev)
+    for name, dt in (("c64", H.C64), ("c128", H.C128)):
+        a.state_prepare(H.PREP_SLATER, w.orbital_perturbation(), None, None, dt, 1)
+        _, eng = a.workspace(1, dt, 1)
+        psi = H.workspace_tensor(a, 1, dt, 1, device=dev)
+        lam = H.workspace_tensor(a, 1, dt, 1, device=dev)
+        E = torch.empty(1, dtype=torch.float64, device=dev)
+        g = torch.empty((1, a.P), dtype=torch.float64, device=dev)
+        a.energy_grad(theta, psi, lam, E, g, dtype=dt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            a.energy_grad(theta, psi, lam, E, g, dtype=dt)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"engine": ["on-chip", "rows", "sweeps"][eng], "evals_per_s": round(1e3 / ms, 3),
+                     "ms_per_step": round(ms, 3), "energy": float(E[0].item())}
+        del psi, lam
+        torch.cuda.empty_cache()
+    out["c64_speedup_same_engine"] = round(out["c64"]["evals_per_s"] / out["c128"]["evals_per_s"], 3)
+    return out
+
+
+def run_np_leg(H, torch, dev, layers=12, steps=1):
+    """The paper's NP ansatz on the 4x4 lattice (Sec. 2.2.1 and Sec. 3): 12
+    layers = 1,568 parameters, interleaved qubit order, on the grid4x4
+    Hamiltonian, complex64 energy + adjoint gradient.  The on-site NP gates
+    mix the spins, so it runs on the dense sweeps over all tiles."""
+    import numpy as np
+    w = H.workloads.workload(5)
+    bonds, cls = H.square_lattice(4, 4)
+    t, U, _ = w.coefficients(bonds)
+    m = H.Model(16, bonds, t, U, None, 8, 8, modes="interleaved")
+    a = H.Ansatz(m, H.np_groups(bonds, cls, 16, layers, modes="interleaved"), 1)
+    a.state_prepare(H.PREP_SLATER, w.orbital_perturbation(), None, None, H.C64, 1)
+    theta = torch.tensor(np.random.default_rng(5).uniform(-0.1, 0.1, (1, a.P)), device=dev)
+    psi = H.workspace_tensor(a, 1, H.C64, 1, device=dev)
+    lam = H.workspace_tensor(a, 1, H.C64, 1, device=dev)
+    E = torch.empty(1, dtype=torch.float64, device=dev)
+    g = torch.empty((1, a.P), dtype=torch.float64, device=dev)
+    a.energy_grad(theta, psi, lam, E, g, dtype=H.C64)   # warm-up (plans, tables)
+    torch.cuda.synchronize()
+    n_sweeps, by = a.plan_stats(1, H.C64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        a.energy_grad(theta, psi, lam, E, g, dtype=H.C64)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    del psi, lam
+    torch.cuda.empty_cache()
+    return {"ansatz": f"NP, {layers} layers, R_z pre-layer, 4x4 (32 qubits)", "params": a.P,
+            "engine": "sweeps (all tiles: the on-site gates mix the spins)", "sweeps": n_sweeps,
+            "evals_per_s": round(1e3 / ms, 5), "ms_per_step": round(ms, 1), "steps": steps, "warmup": 1,
+            "hbm_tbs": round(by / (ms / 1e3) / 1e12, 3), "energy": float(E[0].item())}
+
+
 def run_c128(args, w, a, H, torch, dev, theta, ms_c64):
     """The same evaluation in complex128 (psi + lam = 2 x 68.7 GB at 32
     qubits), fewer steps: it is FP64-bound on this part."""
@@ -501,8 +588,10 @@ def run_c128(args, w, a, H, torch, dev, theta, ms_c64):
     if need > free * 0.95:
         return {"skipped": f"needs {need / 1e9:.1f} GB, {free / 1e9:.1f} GB free"}
     a.state_prepare(H.PREP_SLATER, w.orbital_perturbation(), None, None, H.C128, w.batch)
-    psi = torch.empty((w.batch, 1 << w.n_qubits), dtype=torch.complex128, device=dev)
-    lam = torch.empty_like(psi)
+    _, eng = a.workspace(1, H.C128, w.batch, sweeps=args.sweeps)
+    eng_name = ["on-chip", "rows", "sweeps"][eng]
+    psi = H.workspace_tensor(a, 1, H.C128, w.batch, device=dev, sweeps=args.sweeps)
+    lam = H.workspace_tensor(a, 1, H.C128, w.batch, device=dev, sweeps=args.sweeps)
     E = torch.empty(w.batch, dtype=torch.float64, device=dev)
     g = torch.empty((w.batch, a.P), dtype=torch.float64, device=dev)
     a.energy_grad(theta, psi, lam, E, g, dtype=H.C128, batch=w.batch, sweeps=args.sweeps)   # warm-up
@@ -518,8 +607,8 @@ def run_c128(args, w, a, H, torch, dev, theta, ms_c64):
     del psi, lam
     torch.cuda.empty_cache()
     return {"value": round(w.batch * 1e3 / ms, 5), "unit": "evals/s", "ms_per_step": round(ms, 3),
-            "steps": steps, "warmup": 1, "energy": float(E[0].item()),
-            "c64_speedup": round(ms / ms_c64, 3)}
+            "steps": steps, "warmup": 1, "energy": float(E[0].item()), "engine": eng_name,
+            "c64_speedup_vs_headline_engine": round(ms / ms_c64, 3)}
 
 
 def main():
@@ -533,6 +622,10 @@ def main():
     ap.add_argument("--no-c128", dest="c128", action="store_false")
     ap.add_argument("--c128-steps", type=int, default=1)
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
+    ap.add_argument("--no-dense", dest="dense", action="store_false",
+                    help="skip the dense-sweeps comparison leg (and its 2^n-amplitude buffers)")
+    ap.add_argument("--no-np", dest="np_leg", action="store_false",
+                    help="skip the 32-qubit NP-ansatz entry (1,568 parameters)")
     ap.add_argument("--tile", type=int, default=0, help="log2 tile override (0 = planner default)")
     ap.add_argument("--autotune", action="store_true", help="pick the tile size by timing first")
     ap.add_argument("--runs", type=int, default=0, help="log2 contiguous amplitudes per HBM run (0 = default)")

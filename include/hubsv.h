@@ -182,6 +182,8 @@ HUB_API hub_status state_prepare(ans_t ans, int32_t kind, const double* orb_pert
 /* Energy E(theta) = <psi|H|psi> of Eq. 4 for each batch element.
  * theta: device double [batch][P].  psi: device [batch][2^n] amplitudes; on
  * entry the initial state (unless HUB_FLAG_PREP_FUSED), on return clobbered.
+ * With HUB_FLAG_PREP_FUSED psi is workspace only and needs just the bytes
+ * ans_workspace_bytes reports for the call.
  * E: device double [batch].  The sum over H's terms is fused into the last
  * sweeps; H|psi> is never written.                                          */
 HUB_API hub_status energy(ans_t ans, const double* theta, void* psi, double* E,
@@ -209,6 +211,20 @@ HUB_API hub_status energy(ans_t ans, const double* theta, void* psi, double* E,
 HUB_API hub_status energy_grad(ans_t ans, const double* theta, void* psi, void* lam,
                        void* ckpt, double* E, double* grad, int32_t dtype,
                        int64_t batch, uint32_t flags, hub_stream_t stream);
+
+/* Device workspace of a call (0 = energy, 1 = energy_grad) with these
+ * flags and batch: *bytes receives the bytes that psi and lam must each
+ * hold (not part of the paper: buffer sizing).  The engine the call runs on
+ * (*engine, may be NULL: 0 on chip, 1 rows, 2 dense sweeps) decides it:
+ * on chip the state lives in shared memory and psi and lam are not touched
+ * (0 bytes); the row engine keeps the sector matrix and its transpose,
+ * 2 * batch * C(L, N_up) * C(L, N_dn) amplitudes (32 qubits, N = 8 + 8,
+ * complex64: 2.65 GB instead of the 34.4 GB of a dense vector); the dense
+ * sweeps need batch * 2^n amplitudes, as does a checkpoint buffer.  The
+ * engine choice reads the device's shared-memory limit: query with the
+ * device that will run the call current.                                   */
+HUB_API hub_status ans_workspace_bytes(ans_t ans, int32_t which, int32_t dtype, uint32_t flags,
+                                       int64_t batch, uint64_t* bytes, int32_t* engine);
 
 /* energy() for callers that cannot allocate device memory.  (The paper has
  * no counterpart: this is an interface addition.)  Some callers cannot call

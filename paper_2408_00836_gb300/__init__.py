@@ -263,24 +263,38 @@ class Ansatz:
         check(lib().state_prepare(self._h, kind, pp, npp, ptr, dtype, batch, _stream(stream)))
         del pa, na
 
+    @staticmethod
+    def _flags(fused=True, keep_state=False, sweeps=False, rows=False):
+        return ((FLAG_PREP_FUSED if fused else 0) | (FLAG_KEEP_STATE if keep_state else 0)
+                | (FLAG_SWEEPS if sweeps else 0) | (FLAG_ROWS if rows else 0))
+
+    def workspace(self, which: int, dtype=C64, batch: int = 1, fused: bool = True, keep_state: bool = False,
+                  sweeps: bool = False, rows: bool = False):
+        """(bytes psi and lam must each hold, engine) of a call (which: 0
+        energy, 1 energy_grad); engine 0 on chip, 1 rows, 2 dense sweeps."""
+        by = ctypes.c_uint64(0)
+        eng = ctypes.c_int32(0)
+        check(lib().ans_workspace_bytes(self._h, which, dtype, self._flags(fused, keep_state, sweeps, rows),
+                                        batch, ctypes.byref(by), ctypes.byref(eng)))
+        return by.value, eng.value
+
     def energy(self, theta, psi, E, dtype=C64, batch: int = 1, fused: bool = True,
                keep_state: bool = False, sweeps: bool = False, rows: bool = False, stream=None):
-        flags = ((FLAG_PREP_FUSED if fused else 0) | (FLAG_KEEP_STATE if keep_state else 0)
-                 | (FLAG_SWEEPS if sweeps else 0) | (FLAG_ROWS if rows else 0))
+        flags = self._flags(fused, keep_state, sweeps, rows)
+        nb = self.workspace(0, dtype, batch, fused, keep_state, sweeps, rows)[0]
         check(lib().energy(self._h, _ptr(theta, 8 * batch * self.P, "theta"),
-                           _ptr(psi, batch * self.amp_bytes(dtype), "psi"), _ptr(E, 8 * batch, "E"),
+                           _ptr(psi, max(nb, 1), "psi"), _ptr(E, 8 * batch, "E"),
                            dtype, batch, flags, _stream(stream)))
         return E
 
     def energy_grad(self, theta, psi, lam, E, grad, ckpt=None, dtype=C64, batch: int = 1,
                     fused: bool = True, sweeps: bool = False, rows: bool = False, stream=None):
-        nb = batch * self.amp_bytes(dtype)
-        check(lib().energy_grad(self._h, _ptr(theta, 8 * batch * self.P, "theta"), _ptr(psi, nb, "psi"),
-                                _ptr(lam, nb, "lam"), _ptr(ckpt, nb, "ckpt"), _ptr(E, 8 * batch, "E"),
+        nb = self.workspace(1, dtype, batch, fused, False, sweeps, rows)[0]
+        dense = batch * self.amp_bytes(dtype)
+        check(lib().energy_grad(self._h, _ptr(theta, 8 * batch * self.P, "theta"), _ptr(psi, max(nb, 1), "psi"),
+                                _ptr(lam, max(nb, 1), "lam"), _ptr(ckpt, dense, "ckpt"), _ptr(E, 8 * batch, "E"),
                                 _ptr(grad, 8 * batch * self.P, "grad"), dtype, batch,
-                                (FLAG_PREP_FUSED if fused else 0) | (FLAG_SWEEPS if sweeps else 0)
-                                | (FLAG_ROWS if rows else 0),
-                                _stream(stream)))
+                                self._flags(fused, False, sweeps, rows), _stream(stream)))
         return E, grad
 
     def apply_h(self, psi, lam, dtype=C64, batch: int = 1, stream=None):
@@ -347,6 +361,14 @@ class Ansatz:
 
 def sync(stream=None):
     check(lib().hub_sync(_stream(stream)))
+
+
+def workspace_tensor(ans: "Ansatz", which: int, dtype=C64, batch: int = 1, device="cuda", **flags):
+    """A psi / lam buffer of exactly the size the call needs (ans.workspace)."""
+    import torch
+    nb, _ = ans.workspace(which, dtype, batch, **flags)
+    td = torch.complex64 if dtype == C64 else torch.complex128
+    return torch.empty(max(1, nb // (8 if dtype == C64 else 16)), dtype=td, device=device)
 
 
 def empty_state(n_qubits: int, dtype=C64, batch: int = 1, device="cuda"):

@@ -22,7 +22,7 @@ EXPORTS = [
     "ans_destroy", "ans_num_params", "ans_num_qubits", "state_prepare", "energy",
     "energy_grad", "hub_apply_h", "ans_plan_stats", "ans_set_tile", "ans_set_runs", "hub_sync",
     "hub_last_error", "ans_plan_describe", "ans_profile", "ans_profile_read", "energy_noalloc",
-    "overlap_grad", "spin_correlation",
+    "overlap_grad", "spin_correlation", "ans_workspace_bytes",
 ]
 
 
@@ -77,6 +77,8 @@ def lib():
         "overlap_grad": (st, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p,
                               c_void_p, c_int32, c_int64, c_uint32, c_void_p]),
         "spin_correlation": (st, [c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_void_p]),
+        "ans_workspace_bytes": (st, [c_void_p, c_int32, c_int32, c_uint32, c_int64, POINTER(ctypes.c_uint64),
+                                     POINTER(c_int32)]),
         "ans_plan_stats": (st, [c_void_p, c_int32, c_int32, c_uint32, POINTER(c_int32), POINTER(c_double)]),
         "ans_set_tile": (st, [c_void_p, c_int32, c_int32]),
         "ans_set_runs": (st, [c_void_p, c_int32, c_int32]),

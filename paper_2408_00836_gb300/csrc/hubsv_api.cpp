@@ -1191,6 +1191,29 @@ extern "C" hub_status hub_apply_h(ans_t a, const void* psi, void* lam, int32_t d
                   (cudaStream_t)stream);
 }
 
+extern "C" hub_status ans_workspace_bytes(ans_t a, int32_t which, int32_t dtype, uint32_t flags, int64_t batch,
+                                           uint64_t* bytes, int32_t* engine) {
+  if (!a || !bytes || which < 0 || which > 1 || (dtype != HUB_C64 && dtype != HUB_C128) || batch < 1)
+    return fail(HUB_EINVAL, "ans_workspace_bytes: bad arguments");
+  const uint64_t amp = dtype == HUB_C64 ? 8 : 16;
+  size_t smem = 0;
+  if (small_plan_for(a, which, dtype, flags, smem)) {
+    *bytes = 0;   // the state lives in shared memory only
+    if (engine) *engine = 0;
+    return HUB_OK;
+  }
+  SmallPlan* sp = nullptr;
+  if (row_plan_for(a, which, dtype, flags, sp)) {
+    // the sector matrix and its transpose
+    *bytes = 2ull * (uint64_t)batch * (uint64_t)sp->cup * (uint64_t)sp->cdn * amp;
+    if (engine) *engine = 1;
+    return HUB_OK;
+  }
+  *bytes = (uint64_t)batch * (1ull << a->n) * amp;
+  if (engine) *engine = 2;
+  return HUB_OK;
+}
+
 extern "C" hub_status overlap_grad(ans_t a, const double* theta, const void* psi_ref, int64_t ref_batch,
                                    void* psi, void* lam, double* F, double* f, double* grad, int32_t dtype,
                                    int64_t batch, uint32_t flags, hub_stream_t stream) {

@@ -217,7 +217,7 @@ struct KernelArgs {
 //   w0 = {code | aux << 8 | slot << 16, sgn, bm_local, bm_global}
 //   hop ops, c64:  w1 = {c, s, c_lo, s_lo}, w2 = {tc, 0, 0, 0} (FP32)
 //   hop ops, c128: w1 = {c, s}, w2 = {tc, 0} (FP64)
-//   diagonal ops:  w1 = {phase-table offset, real-table offset, DiagOp, 0}
+//   diagonal ops:  w1 = {phase-table offset, real-table offset, DiagOp, mode pair (RA_MP)}
 // c, s: the factor's cos / sin (s negated for an inverse factor; in c64 as
 // FP32 pairs hi + lo, see GC); tc: -t of the matching Hamiltonian term.
 constexpr int kMaxSlots = 65535;     // slot is stored in 16 bits
@@ -240,6 +240,8 @@ enum ResAux : int {
   RA_NY = 3,       // diagonal ops: number of y tables when only on-site terms (1, 2), else 0
   RA_INV = 4,      // diagonal factor: inverse
   RA_LAM = 8,      // diagonal factor: also on lam
+  RA_MP = 16,      // diagonal ops: a single mode-pair product c n_p n_q (p | q << 8 in w1.w;
+                   // real value at real offset + 2048, phase at phase offset + 2048)
   RA_GRAD = 128,   // reduces into the accumulator slot
 };
 // Register slot pair (a < b) -> dense index 0..9.

@@ -34,6 +34,72 @@ namespace hubsv {
 
 namespace {
 
+// Order a hop's pair list so that the row kernel's half-warps meet no
+// shared-memory bank conflicts where possible.  Lane i of a warp takes
+// entry 32 w + i of the list (per pass), and an 8-byte access of 16 lanes
+// is conflict-free when their element indices are distinct modulo 16 (one
+// bank pair each).  The pairs of one hop are independent, so any order is
+// valid: groups of 16 are formed as perfect matchings between the classes
+// e1 mod 16 and e2 mod 16 (augmenting paths over the remaining pairs);
+// pairs left when no perfect matching remains follow in their old order.
+void order_pairs_for_banks(std::vector<uint32_t>& pl) {
+  const size_t n = pl.size();
+  if (n < 32) return;
+  std::vector<std::vector<int>> bucket(256);   // (e1 % 16) * 16 + e2 % 16 -> entries
+  for (size_t i = 0; i < n; ++i) {
+    const uint32_t e1 = pl[i] & 0xffffu, e2 = (pl[i] >> 16) & 0x7fffu;
+    bucket[(e1 & 15u) * 16 + (e2 & 15u)].push_back((int)i);
+  }
+  for (auto& b : bucket) std::reverse(b.begin(), b.end());   // pop from the back = old order
+  std::vector<uint32_t> out;
+  out.reserve(n);
+  std::vector<char> used(n, 0);
+  while (true) {
+    int match_col[16];   // e2 class -> e1 class
+    for (int c = 0; c < 16; ++c) match_col[c] = -1;
+    bool ok = true;
+    for (int r = 0; r < 16 && ok; ++r) {
+      // augmenting path from e1 class r (breadth first over the classes)
+      int from_r[16], seen[16] = {0};
+      for (int c = 0; c < 16; ++c) from_r[c] = -1;
+      std::vector<int> queue = {r};
+      int found = -1;
+      for (size_t qi = 0; qi < queue.size() && found < 0; ++qi) {
+        const int rr = queue[qi];
+        for (int c = 0; c < 16 && found < 0; ++c) {
+          if (seen[c] || bucket[rr * 16 + c].empty()) continue;
+          seen[c] = 1;
+          from_r[c] = rr;
+          if (match_col[c] < 0) found = c;
+          else queue.push_back(match_col[c]);
+        }
+      }
+      if (found < 0) { ok = false; break; }
+      // flip the path back to r
+      for (int c = found;;) {
+        const int rr = from_r[c];
+        int prev = -1;
+        for (int cc = 0; cc < 16; ++cc)
+          if (match_col[cc] == rr) prev = cc;
+        match_col[c] = rr;
+        if (rr == r) break;
+        c = prev;
+      }
+    }
+    if (!ok) break;
+    for (int c = 0; c < 16; ++c) {
+      auto& b = bucket[match_col[c] * 16 + c];
+      const int idx = b.back();
+      b.pop_back();
+      used[idx] = 1;
+      out.push_back(pl[idx]);
+    }
+  }
+  for (size_t i = 0; i < n; ++i)
+    if (!used[i]) out.push_back(pl[i]);
+  pl.swap(out);
+}
+
 std::vector<uint32_t> patterns(const std::vector<int>& modes, int N) {
   std::vector<uint32_t> out;
   const int L = (int)modes.size();
@@ -97,6 +163,9 @@ hub_status make_small_plan(hub_ansatz* a, int which, SmallPlan*& out) {
             sp->pairs.push_back((uint32_t)r | ((uint32_t)rk.at(x2) << 16) | (par << 31));
           }
         }
+        std::vector<uint32_t> pl(sp->pairs.begin() + off, sp->pairs.end());
+        order_pairs_for_banks(pl);
+        std::copy(pl.begin(), pl.end(), sp->pairs.begin() + off);
         it = lists.emplace(std::make_pair(p, q), std::make_pair(off, (int)sp->pairs.size() - off)).first;
       }
       d.a = it->second.first;

@@ -485,7 +485,8 @@ __device__ void resolve_ops(const SweepDev& sw, const KernelArgs& a, uint4* sres
           hop = false;
           const DiagOpDev& d = a.diag_ops[o.idx];
           const bool onsite = d.has_x == 0 && d.n_vb == 0 && d.n_mp == 0 && (d.has_y == 1 || d.has_y == 2);
-          aux = onsite ? d.has_y : 0;
+          const bool mp1 = d.has_x == 0 && d.has_y == 0 && d.n_vb == 0 && d.n_mp == 1;
+          aux = onsite ? d.has_y : (mp1 ? RA_MP : 0);
           switch (o.kind) {
             case OP_DIAG:
               code = RC_DIAG;
@@ -498,7 +499,8 @@ __device__ void resolve_ops(const SweepDev& sw, const KernelArgs& a, uint4* sres
             default: code = RC_NOP; break;
           }
           w[1] = make_uint4((uint32_t)((size_t)b * a.phase_stride + d.phase_off),
-                            (uint32_t)((size_t)inst * a.real_stride + d.real_off), (uint32_t)o.idx, 0u);
+                            (uint32_t)((size_t)inst * a.real_stride + d.real_off), (uint32_t)o.idx,
+                            mp1 ? (uint32_t)d.mp_p[0] | ((uint32_t)d.mp_q[0] << 8) : 0u);
           break;
         }
       }
@@ -794,6 +796,21 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
             const bool dol = (NV == 2) && (aux & RA_LAM);
             const uint32_t xb0 = sbase | gob;
             const int ny = aux & RA_NY;
+            if (aux & RA_MP) {
+              // one controlled phase (NP / EP gate): exp(i phi) where both modes are occupied
+              T2 pv = ptab[2048];
+              if (inv) pv.y = -pv.y;
+              const uint32_t mp = w1.w & 255u, mq = (w1.w >> 8) & 255u;
+#pragma unroll
+              for (int e = 0; e < NE; ++e) {
+                const uint32_t x = xb0 | comb<RB>(so, e);
+                if ((x >> mp) & (x >> mq) & 1u) {
+                  v[e] = cmul(v[e], pv);
+                  if (dol) l[e] = cmul(l[e], pv);
+                }
+              }
+              break;
+            }
             if (ny) {
               // on-site factor only: phase of the double-occupancy pattern
               const T2* ty = ptab + 1024;
@@ -828,8 +845,25 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
               const R* rtab = rtabs + w1.y;
               const int ny = aux & RA_NY;
               const uint32_t xb0 = sbase | gob;
-              const DiagOpDev* dp = ny ? nullptr : &a.diag_ops[w1.z];
               R pe = 0;
+              if (aux & RA_MP) {
+                const R dv0 = rtab[2048];
+                T2 pv = ptab[2048];
+                pv.y = -pv.y;
+                const uint32_t mp = w1.w & 255u, mq = (w1.w >> 8) & 255u;
+#pragma unroll
+                for (int e = 0; e < NE; ++e) {
+                  const uint32_t x = xb0 | comb<RB>(so, e);
+                  if ((x >> mp) & (x >> mq) & 1u) {
+                    pe += dv0 * (l[e].x * v[e].y - l[e].y * v[e].x);
+                    v[e] = cmul(v[e], pv);
+                    l[e] = cmul(l[e], pv);
+                  }
+                }
+                racc += (R)2 * pe;
+                break;
+              }
+              const DiagOpDev* dp = ny ? nullptr : &a.diag_ops[w1.z];
 #pragma unroll
               for (int e = 0; e < NE; ++e) {
                 const uint32_t x = xb0 | comb<RB>(so, e);
@@ -864,9 +898,22 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
 #pragma unroll
             for (int j = 0; j < RB; ++j) so[j] = ph.so[j];
             const int ny = aux & RA_NY;
-            const DiagOpDev* dp = ny ? nullptr : &a.diag_ops[w1.z];
             R pe = 0, pn = 0;
             const uint32_t xb0 = sbase | gob;
+            if ((aux & RA_MP) && code == RC_GRAD_DIAG) {
+              if constexpr (NV == 2) {
+                const R dv0 = rtab[2048];
+                const uint32_t mp = w1.w & 255u, mq = (w1.w >> 8) & 255u;
+#pragma unroll
+                for (int e = 0; e < NE; ++e) {
+                  const uint32_t x = xb0 | comb<RB>(so, e);
+                  if ((x >> mp) & (x >> mq) & 1u) pe += dv0 * (l[e].x * v[e].y - l[e].y * v[e].x);
+                }
+                racc += (R)2 * pe;
+              }
+              break;
+            }
+            const DiagOpDev* dp = ny ? nullptr : &a.diag_ops[w1.z];
 #pragma unroll
             for (int e = 0; e < NE; ++e) {
               const uint32_t x = xb0 | comb<RB>(so, e);

@@ -100,3 +100,35 @@ def test_dense_path_state_over_all_sectors(dtype):
     H.sync()
     assert abs(E.item() - Eo) < TOL[dtype] * max(1.0, abs(Eo))
     a.set_tile(dtype, 0)
+
+
+@pytest.mark.parametrize("dtype", [H.C64, H.C128])
+def test_sector_sized_workspaces(dtype):
+    """ans_workspace_bytes: the row engine needs only the sector matrix and
+    its transpose (24 qubits: 2 x 853 776 amplitudes instead of 2^24), the
+    on-chip engine none; calls on buffers of exactly that size give the
+    oracle's energy and gradient."""
+    w = W.workload(6)
+    bonds, _ = H.square_lattice(3, 4)
+    t, U, _ = w.coefficients(bonds)
+    prob = Problem(3, 4, t=t, U=U, V=None, layers=w.layers, classes=w.classes)
+    a = prob.ans
+    nb, eng = a.workspace(1, dtype, 1)
+    amp = 8 if dtype == H.C64 else 16
+    assert eng == 1 and nb == 2 * 924 * 924 * amp
+    assert a.workspace(1, dtype, 1, sweeps=True) == ((1 << 24) * amp, 2)
+    theta = w.theta()[0]
+    a.state_prepare(H.PREP_SLATER, None, None, None, dtype, 1)
+    psi = H.workspace_tensor(a, 1, dtype, 1)
+    lam = H.workspace_tensor(a, 1, dtype, 1)
+    assert psi.numel() * psi.element_size() == nb
+    E = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty((1, a.P), dtype=torch.float64, device="cuda")
+    a.energy_grad(torch.tensor(theta[None, :], device="cuda"), psi, lam, E, g, dtype=dtype)
+    H.sync()
+    Eo, go = prob.oracle_energy_grad(theta)
+    assert abs(E.item() - Eo) < TOL[dtype] * max(1.0, abs(Eo))
+    assert np.max(np.abs(g.cpu().numpy()[0] - go)) < TOL[dtype] * max(1.0, np.max(np.abs(go)))
+    # on chip: no workspace at all (a one-element buffer is passed)
+    p2, _ = _grid2x4()
+    assert p2.ans.workspace(1, dtype, 4)[1] == 0 and p2.ans.workspace(1, dtype, 4)[0] == 0
