@@ -116,8 +116,10 @@ enum SweepFlag : uint32_t {
   SW_WRITE_LAM = 32u,
   SW_CKPT_WRITE = 64u, // also store psi to the checkpoint buffer
   SW_CKPT_READ = 128u, // read psi from the checkpoint buffer
-  SW_VPOP = 256u,      // a diagonal operation has uniform V terms: the kernel
-                       // variant that counts them with popcounts is used
+  SW_VPOP = 256u,      // a diagonal operation has uniform V terms or is a single
+                       // controlled phase: the kernel variant with their fast
+                       // paths (V counted with popcounts; the phase of one mode
+                       // pair read once per operation) is used
 };
 
 struct SweepDev {

@@ -662,6 +662,7 @@ hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*&
       if (!diag) continue;
       const DiagOpDev& g = a->diag_ops[d.idx];
       if (g.n_vb > 0 && g.v_uniform && g.n_vs >= 0) sw.flags |= SW_VPOP;
+      if (g.has_x == 0 && g.has_y == 0 && g.n_vb == 0 && g.n_mp == 1) sw.flags |= SW_VPOP;
     }
     bytes += amp * (double)tiles_per_state * (double)(1ull << k) *
              (((f & SW_READ_PSI) ? 1 : 0) + ((f & SW_WRITE_PSI) ? 1 : 0) +

@@ -796,7 +796,7 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
             const bool dol = (NV == 2) && (aux & RA_LAM);
             const uint32_t xb0 = sbase | gob;
             const int ny = aux & RA_NY;
-            if (aux & RA_MP) {
+            if (VP && (aux & RA_MP)) {
               // one controlled phase (NP / EP gate): exp(i phi) where both modes are occupied
               T2 pv = ptab[2048];
               if (inv) pv.y = -pv.y;
@@ -846,7 +846,7 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
               const int ny = aux & RA_NY;
               const uint32_t xb0 = sbase | gob;
               R pe = 0;
-              if (aux & RA_MP) {
+              if (VP && (aux & RA_MP)) {
                 const R dv0 = rtab[2048];
                 T2 pv = ptab[2048];
                 pv.y = -pv.y;
@@ -900,7 +900,7 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
             const int ny = aux & RA_NY;
             R pe = 0, pn = 0;
             const uint32_t xb0 = sbase | gob;
-            if ((aux & RA_MP) && code == RC_GRAD_DIAG) {
+            if (VP && (aux & RA_MP) && code == RC_GRAD_DIAG) {
               if constexpr (NV == 2) {
                 const R dv0 = rtab[2048];
                 const uint32_t mp = w1.w & 255u, mq = (w1.w >> 8) & 255u;

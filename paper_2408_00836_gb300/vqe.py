@@ -38,9 +38,11 @@ class EnergyGradGraph:
         n = ans.n
         self.theta_h = torch.zeros((batch, ans.P), dtype=torch.float64).pin_memory()
         self.theta = torch.zeros((batch, ans.P), dtype=torch.float64, device=dev)
-        self.psi = torch.empty((batch, 1 << n), dtype=td, device=dev)
-        self.lam = torch.empty_like(self.psi)
-        self.ckpt = torch.empty_like(self.psi) if ckpt else None
+        # workspaces of the size the call's engine needs (ans.workspace)
+        from . import workspace_tensor
+        self.psi = workspace_tensor(ans, 1, dtype, batch, device=dev, sweeps=sweeps, rows=rows)
+        self.lam = workspace_tensor(ans, 1, dtype, batch, device=dev, sweeps=sweeps, rows=rows)
+        self.ckpt = torch.empty((batch, 1 << n), dtype=td, device=dev) if ckpt else None
         self.E = torch.zeros(batch, dtype=torch.float64, device=dev)
         self.g = torch.zeros((batch, ans.P), dtype=torch.float64, device=dev)
         self.E_h = torch.zeros(batch, dtype=torch.float64).pin_memory()

@@ -98,3 +98,34 @@ def test_energy_fn_autograd_matches_oracle_gradient(dtype):
         ref = (float(w[b]) + 2.0 * Eo) * go          # dL/dtheta_b = (w_b + 2 E_b) dE_b/dtheta_b
         scale = abs(float(w[b]) + 2.0 * Eo)
         assert np.max(np.abs(gt[b] - ref)) < TOL[dtype] * scale * max(1.0, np.max(np.abs(go))), b
+
+
+def test_engine_autotuner_and_graph_captured_batch():
+    """The engine autotuner on the 4096-state batch times the library's
+    choice, the row engine and the dense sweeps, and leaves a valid choice;
+    the whole batched evaluation captured in a CUDA graph and replayed
+    gives the direct call's results."""
+    from paper_2408_00836_gb300.autotune import autotune_engine
+    from paper_2408_00836_gb300.vqe import EnergyGradGraph
+    w, prob = _workload2()
+    a = prob.ans
+    batch = w.batch
+    a.state_prepare(H.PREP_SLATER, prob.perturb, None, None, H.C64, batch)
+    best, times = autotune_engine(a, H.C64, batch=batch, which=1, theta=w.theta(), tiles=(12,), reps=1,
+                                  warmup=1)
+    assert {"auto", "rows", "sweeps_tile12"} <= set(times)
+    assert best["name"] == min(times, key=times.get)
+    assert best["engine"] in ("on-chip", "rows", "sweeps")
+    a.set_tile(H.C64, 0)
+    fn = EnergyGradGraph(a, dtype=H.C64, batch=batch, use_graph=True, sweeps=best["sweeps"], rows=best["rows"])
+    direct = EnergyGradGraph(a, dtype=H.C64, batch=batch, use_graph=False, sweeps=best["sweeps"],
+                             rows=best["rows"])
+    theta = w.theta()
+    E, g = fn(theta)
+    Ed, gd = direct(theta)
+    assert np.max(np.abs(E - Ed)) < 1e-12 * max(1.0, np.max(np.abs(Ed)))
+    assert np.max(np.abs(g - gd)) < 1e-12 * max(1.0, np.max(np.abs(gd)))
+    for b in (0, 2047, 4095):
+        Eo, go = prob.oracle_energy_grad(theta[b], r=b % 4)
+        assert abs(E[b] - Eo) < TOL[H.C64] * max(1.0, abs(Eo))
+        assert grad_err(g[b], go) < TOL[H.C64]
