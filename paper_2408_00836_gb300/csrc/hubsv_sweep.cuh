@@ -354,6 +354,56 @@ __device__ __forceinline__ void rot(T2& u, T2& w, R c, R s, R cl, R sl) {
   }
 }
 
+// Packed FP32 pair arithmetic: on sm_100-family GPUs fma.rn.f32x2 and
+// mul.rn.f32x2 work on both halves of a 64-bit register pair in one
+// instruction, each half rounded exactly as the scalar fmaf / multiply.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 splat2(float x) { return make_float2(x, x); }
+
+// i * sigma * w as a float pair, sigma = -1 where m = 0x80000000, +1 where
+// m = 0: (-sigma w.y, sigma w.x), two sign-bit logic ops.
+__device__ __forceinline__ float2 iswap(float2 w, uint32_t m) {
+  return make_float2(__int_as_float(__float_as_int(w.y) ^ (int)(m ^ 0x80000000u)),
+                     __int_as_float(__float_as_int(w.x) ^ (int)m));
+}
+// sigma * w
+__device__ __forceinline__ float2 sflip2(float2 w, uint32_t m) {
+  return make_float2(__int_as_float(__float_as_int(w.x) ^ (int)m), __int_as_float(__float_as_int(w.y) ^ (int)m));
+}
+
+// The complex64 rotation of rot(u, w, c, sigma s, cl, sigma sl) in packed
+// form: u' = c u + i sigma s w (+ the low parts), w' likewise; C, S, CL, SL
+// hold each coefficient in both halves.  The same products and sums as the
+// scalar form, so the results are bitwise equal.  su, sw (i sigma u,
+// i sigma w of the inputs) are returned for a gradient term.
+__device__ __forceinline__ void rot_pk(float2& u, float2& w, float2 C, float2 S, float2 CL, float2 SL,
+                                       uint32_t m, float2& su, float2& sw) {
+  sw = iswap(w, m);
+  su = iswap(u, m);
+  u = fma2(C, u, fma2(S, sw, fma2(CL, u, mul2(SL, sw))));
+  w = fma2(C, w, fma2(S, su, fma2(CL, w, mul2(SL, su))));
+}
+__device__ __forceinline__ void rot_pk(float2& u, float2& w, float2 C, float2 S, float2 CL, float2 SL,
+                                       uint32_t m) {
+  float2 su, sw;
+  rot_pk(u, w, C, S, CL, SL, m, su, sw);
+}
+
 // x with its sign flipped when bit e of m is set (m: per-op sign mask; e is
 // a constant after unrolling, so this is a shift and two logic ops).
 __device__ __forceinline__ float sflip(float x, uint32_t m, int e) {
@@ -363,13 +413,27 @@ __device__ __forceinline__ double sflip(double x, uint32_t m, int e) {
   return __hiloint2double(__double2hiint(x) ^ (int)((m << (31 - e)) & 0x80000000u), __double2loint(x));
 }
 
-template <int A, int B, int NE, typename T2, typename R>
+// PKD: packed complex64 arithmetic (the kernel variants with the V and
+// mode-pair fast paths keep the scalar form: the register pairs the packed
+// instructions need made them spill).
+template <int A, int B, bool PKD, int NE, typename T2, typename R>
 __device__ __forceinline__ void pair_giv(T2 (&v)[NE], R c, R s, R cl, R sl, uint32_t sm) {
+  if constexpr (PKD && sizeof(R) == 4) {   // complex64: packed pair arithmetic (see rot_pk)
+    const float2 C2 = splat2(c), S2 = splat2(s), CL2 = splat2(cl), SL2 = splat2(sl);
 #pragma unroll
-  for (int e = 0; e < NE; ++e) {
-    if (((e >> A) & 1) == 0 && ((e >> B) & 1) == 1) {
-      constexpr int F = (1 << A) | (1 << B);
-      rot(v[e], v[e ^ F], c, sflip(s, sm, e), cl, sflip(sl, sm, e));
+    for (int e = 0; e < NE; ++e) {
+      if (((e >> A) & 1) == 0 && ((e >> B) & 1) == 1) {
+        constexpr int F = (1 << A) | (1 << B);
+        rot_pk(v[e], v[e ^ F], C2, S2, CL2, SL2, (sm << (31 - e)) & 0x80000000u);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < NE; ++e) {
+      if (((e >> A) & 1) == 0 && ((e >> B) & 1) == 1) {
+        constexpr int F = (1 << A) | (1 << B);
+        rot(v[e], v[e ^ F], c, sflip(s, sm, e), cl, sflip(sl, sm, e));
+      }
     }
   }
 }
@@ -402,21 +466,41 @@ __device__ __forceinline__ R pair_hop(T2 (&v)[NE], T2 (&l)[NE], R tc, uint32_t s
 // Gradient term 2 Im <lam|G_term|psi> of one hop term, then its inverse
 // factor on psi and lam (the reduction uses the values before the inverse;
 // the factor commutes with its own generator, so either order is exact).
-template <int A, int B, int NE, typename T2, typename R>
+template <int A, int B, bool PKD, int NE, typename T2, typename R>
 __device__ __forceinline__ R pair_gradinv(T2 (&v)[NE], T2 (&l)[NE], R c, R s, R cl, R sl, R tc, uint32_t sm) {
-  R part = 0;
+  if constexpr (PKD && sizeof(R) == 4) {   // complex64: packed (see rot_pk and row_hop)
+    const float2 C2 = splat2(c), S2 = splat2(s), CL2 = splat2(cl), SL2 = splat2(sl);
+    float2 acc2 = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int e = 0; e < NE; ++e) {
-    if (((e >> A) & 1) == 0 && ((e >> B) & 1) == 1) {
-      constexpr int F = (1 << A) | (1 << B);
-      const T2 u = v[e], w = v[e ^ F], lu = l[e], lw = l[e ^ F];
-      part += sflip(tc, sm, e) * ((lu.x * w.y - lu.y * w.x) + (lw.x * u.y - lw.y * u.x));
-      const R ss = sflip(s, sm, e), ssl = sflip(sl, sm, e);
-      rot(v[e], v[e ^ F], c, ss, cl, ssl);
-      rot(l[e], l[e ^ F], c, ss, cl, ssl);
+    for (int e = 0; e < NE; ++e) {
+      if (((e >> A) & 1) == 0 && ((e >> B) & 1) == 1) {
+        constexpr int F = (1 << A) | (1 << B);
+        const uint32_t m = (sm << (31 - e)) & 0x80000000u;
+        const T2 lu = l[e], lw = l[e ^ F];
+        float2 su, sw;
+        rot_pk(v[e], v[e ^ F], C2, S2, CL2, SL2, m, su, sw);
+        acc2 = fma2(lu, sw, acc2);
+        acc2 = fma2(lw, su, acc2);
+        rot_pk(l[e], l[e ^ F], C2, S2, CL2, SL2, m);
+      }
     }
+    // (lu, i sigma w) + (lw, i sigma u) over both halves: -sigma (the term)
+    return -tc * (acc2.x + acc2.y);
+  } else {
+    R part = 0;
+#pragma unroll
+    for (int e = 0; e < NE; ++e) {
+      if (((e >> A) & 1) == 0 && ((e >> B) & 1) == 1) {
+        constexpr int F = (1 << A) | (1 << B);
+        const T2 u = v[e], w = v[e ^ F], lu = l[e], lw = l[e ^ F];
+        part += sflip(tc, sm, e) * ((lu.x * w.y - lu.y * w.x) + (lw.x * u.y - lw.y * u.x));
+        const R ss = sflip(s, sm, e), ssl = sflip(sl, sm, e);
+        rot(v[e], v[e ^ F], c, ss, cl, ssl);
+        rot(l[e], l[e ^ F], c, ss, cl, ssl);
+      }
+    }
+    return part;
   }
-  return part;
 }
 
 // Case labels of the ten register slot pairs (a, b), a < b, for one
@@ -769,12 +853,12 @@ sweep_kernel(const SweepDev sw, const KernelArgs a) {
           cl = sl = 0.0;
           tc = __hiloint2double((int)w2.y, (int)w2.x);
         }
-#define HUB_GIV1(A, B) pair_giv<A, B>(v, c, s, cl, sl, sm);
+#define HUB_GIV1(A, B) pair_giv<A, B, !VP>(v, c, s, cl, sl, sm);
 #define HUB_GIV2(A, B)                                  \
-  pair_giv<A, B>(v, c, s, cl, sl, sm);                  \
-  if constexpr (NV == 2) pair_giv<A, B>(l, c, s, cl, sl, sm);
+  pair_giv<A, B, !VP>(v, c, s, cl, sl, sm);             \
+  if constexpr (NV == 2) pair_giv<A, B, !VP>(l, c, s, cl, sl, sm);
 #define HUB_GI(A, B) \
-  if constexpr (NV == 2) racc += (R)2 * pair_gradinv<A, B>(v, l, c, s, cl, sl, tc, sm);
+  if constexpr (NV == 2) racc += (R)2 * pair_gradinv<A, B, !VP>(v, l, c, s, cl, sl, tc, sm);
 #define HUB_M0(A, B) eacc += (R)2 * pair_hop<A, B, 0>(v, l, tc, sm);
 #define HUB_M1(A, B) \
   if constexpr (NV == 2) eacc += (R)2 * pair_hop<A, B, 1>(v, l, tc, sm);
