@@ -141,11 +141,59 @@ namespace {
 
 enum { RH_GIV = 0, RH_MEAS = 1, RH_LAM = 2, RH_GRAD = 3, RH_GRADINV = 4 };
 
-// One hop operation on a staged row: the pairs of its pair list, four entries
-// loaded at a time; returns this thread's share of the measured or gradient
-// term.  K and DOL are fixed per call site, so the loop carries no branches
-// on the operation kind.
+// One pair of a hop operation on a staged row (pair entry pr, as
+// SmallArgs::pairs); returns its share of the measured or gradient term.
 template <int K, bool DOL, typename R, typename T2>
+__device__ __forceinline__ R row_pair(T2* __restrict__ prow, T2* __restrict__ lrow, uint32_t pr, uint32_t rpar,
+                                      R c, R s, R cl, R sl, R tc) {
+  const int e1 = (int)(pr & 0xffffu), e2 = (int)((pr >> 16) & 0x7fffu);
+  const bool neg = ((pr >> 31) ^ rpar) != 0;
+  T2 u = prow[e1], w = prow[e2];
+  R part = 0;
+  if constexpr (K == RH_GIV) {
+    const R ss = neg ? -s : s, ssl = neg ? -sl : sl;
+    rot(u, w, c, ss, cl, ssl);
+    prow[e1] = u;
+    prow[e2] = w;
+    if constexpr (DOL) {
+      T2 lu = lrow[e1], lw = lrow[e2];
+      rot(lu, lw, c, ss, cl, ssl);
+      lrow[e1] = lu;
+      lrow[e2] = lw;
+    }
+  } else if constexpr (K == RH_GRAD || K == RH_GRADINV) {
+    const R ts = neg ? -tc : tc;
+    T2 lu = lrow[e1], lw = lrow[e2];
+    part = ts * ((lu.x * w.y - lu.y * w.x) + (lw.x * u.y - lw.y * u.x));
+    if constexpr (K == RH_GRADINV) {   // then the inverse factor on both
+      const R ss = neg ? -s : s, ssl = neg ? -sl : sl;
+      rot(u, w, c, ss, cl, ssl);
+      prow[e1] = u;
+      prow[e2] = w;
+      rot(lu, lw, c, ss, cl, ssl);
+      lrow[e1] = lu;
+      lrow[e2] = lw;
+    }
+  } else {
+    const R ts = neg ? -tc : tc;
+    part = ts * (u.x * w.x + u.y * w.y);
+    if constexpr (K == RH_LAM) {
+      T2 lu = lrow[e1], lw = lrow[e2];
+      lu.x += ts * w.x; lu.y += ts * w.y;
+      lw.x += ts * u.x; lw.y += ts * u.y;
+      lrow[e1] = lu;
+      lrow[e2] = lw;
+    }
+  }
+  return part;
+}
+
+// One hop operation on a staged row: thread tid takes entries tid, tid +
+// NT, ... of the pair list, four loaded at a time (NT is a constant, so the
+// four loads share one address); the last round is predicated.  Returns this thread's share of the measured or gradient term.
+// K and DOL are fixed per call site, so the loops carry no branches on the
+// operation kind.
+template <int K, bool DOL, int NT, typename R, typename T2>
 __device__ __forceinline__ R row_hop(T2* __restrict__ prow, T2* __restrict__ lrow,
                                      const uint32_t* __restrict__ pl, int nb, uint32_t rpar, R c, R s,
                                      R cl, R sl, R tc) {
@@ -161,45 +209,7 @@ __device__ __forceinline__ R row_hop(T2* __restrict__ prow, T2* __restrict__ lro
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (it0 + k * nth >= nb) break;
-      const uint32_t pr = prs[k];
-      const int e1 = (int)(pr & 0xffffu), e2 = (int)((pr >> 16) & 0x7fffu);
-      const bool neg = ((pr >> 31) ^ rpar) != 0;
-      T2 u = prow[e1], w = prow[e2];
-      if constexpr (K == RH_GIV) {
-        const R ss = neg ? -s : s, ssl = neg ? -sl : sl;
-        rot(u, w, c, ss, cl, ssl);
-        prow[e1] = u;
-        prow[e2] = w;
-        if constexpr (DOL) {
-          T2 lu = lrow[e1], lw = lrow[e2];
-          rot(lu, lw, c, ss, cl, ssl);
-          lrow[e1] = lu;
-          lrow[e2] = lw;
-        }
-      } else if constexpr (K == RH_GRAD || K == RH_GRADINV) {
-        const R ts = neg ? -tc : tc;
-        T2 lu = lrow[e1], lw = lrow[e2];
-        part += ts * ((lu.x * w.y - lu.y * w.x) + (lw.x * u.y - lw.y * u.x));
-        if constexpr (K == RH_GRADINV) {   // then the inverse factor on both
-          const R ss = neg ? -s : s, ssl = neg ? -sl : sl;
-          rot(u, w, c, ss, cl, ssl);
-          prow[e1] = u;
-          prow[e2] = w;
-          rot(lu, lw, c, ss, cl, ssl);
-          lrow[e1] = lu;
-          lrow[e2] = lw;
-        }
-      } else {
-        const R ts = neg ? -tc : tc;
-        part += ts * (u.x * w.x + u.y * w.y);
-        if constexpr (K == RH_LAM) {
-          T2 lu = lrow[e1], lw = lrow[e2];
-          lu.x += ts * w.x; lu.y += ts * w.y;
-          lw.x += ts * u.x; lw.y += ts * u.y;
-          lrow[e1] = lu;
-          lrow[e2] = lw;
-        }
-      }
+      part += row_pair<K, DOL>(prow, lrow, prs[k], rpar, c, s, cl, sl, tc);
     }
   }
   return part;
@@ -277,6 +287,18 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
     }
     __syncthreads();
     Tot<R> eacc, nacc;
+    // gradient terms of consecutive operations with one accumulator slot
+    // (the factors of one parameter) are summed per thread and reduced once
+    R racc = 0;
+    int rslot = -1;
+    auto add_slot = [&](int slot, R v) {
+      if (slot != rslot) {
+        if (rslot >= 0) row_add(acc, a.n_slots, rslot, racc);
+        racc = 0;
+        rslot = slot;
+      }
+      racc += v;
+    };
     for (int oi = 0; oi < n_ops; ++oi) {
       const SmallOpDev op = sops[oi];
       R part = 0, npart = 0;
@@ -298,15 +320,15 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
         const uint32_t* pl = a.pairs + op.a;
         switch (op.kind) {
           case OP_GIV:
-            if (dol) row_hop<RH_GIV, true>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc);
-            else row_hop<RH_GIV, false>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc);
+            if (dol) row_hop<RH_GIV, true, NT>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc);
+            else row_hop<RH_GIV, false, NT>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc);
             break;
-          case OP_MEAS_HOP: part = row_hop<RH_MEAS, false>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc); break;
-          case OP_LAM_HOP: part = row_hop<RH_LAM, false>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc); break;
-          case OP_GRADINV_HOP: part = row_hop<RH_GRADINV, true>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc); break;
-          default: part = row_hop<RH_GRAD, false>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc); break;
+          case OP_MEAS_HOP: part = row_hop<RH_MEAS, false, NT>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc); break;
+          case OP_LAM_HOP: part = row_hop<RH_LAM, false, NT>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc); break;
+          case OP_GRADINV_HOP: part = row_hop<RH_GRADINV, true, NT>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc); break;
+          default: part = row_hop<RH_GRAD, false, NT>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc); break;
         }
-        if (op.kind == OP_GRAD_HOP || op.kind == OP_GRADINV_HOP) row_add(acc, a.n_slots, op.slot, (R)2 * part);
+        if (op.kind == OP_GRAD_HOP || op.kind == OP_GRADINV_HOP) add_slot(op.slot, (R)2 * part);
         else if (op.kind != OP_GIV) eacc.add((R)2 * part);
       } else {   // diagonal operations
         const DiagOpDev* dp = a.diag_ops + op.a;
@@ -368,7 +390,7 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
             break;
         }
         if (op.kind == OP_GRAD_DIAG || op.kind == OP_GRADINV_DIAG) {
-          row_add(acc, a.n_slots, op.slot, (R)2 * part);
+          add_slot(op.slot, (R)2 * part);
         } else if (op.kind != OP_DIAG) {
           eacc.add(part);
           nacc.add(npart);
@@ -376,6 +398,7 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
       }
       __syncthreads();
     }
+    if (rslot >= 0) row_add(acc, a.n_slots, rslot, racc);
     if (meas) {
       row_add_tot(acc, a.n_slots, a.slot_E, eacc);
       row_add_tot(acc, a.n_slots, a.slot_N, nacc);
