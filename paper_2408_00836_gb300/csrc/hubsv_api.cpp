@@ -913,10 +913,9 @@ RowPlan* row_plan_for(hub_ansatz* a, int which, int dtype, uint32_t flags, Small
   for (const RowSegHost& g : rp->segs) {
     const int nv = (g.flags & RS_HAS_LAM) ? 2 : 1;
     const int len = g.orient == 0 ? sp->cup : sp->cdn;
+    const int nr = g.orient == 0 ? sp->cdn : sp->cup;
     const int no = g.op_end - g.op_begin;
-    const int nt = rows_threads(dtype, nv, len, a->P + 2, a->n_gates, a->n_hcol, no);
-    if ((int)rows_smem_bytes(dtype, nv, len, a->P + 2, a->n_gates, a->n_hcol, nt, no) > optin)
-      return nullptr;
+    if ((int)rows_launch(dtype, nv, len, nr, a->P + 2, a->n_gates, a->n_hcol, no).smem > optin) return nullptr;
   }
   sp_out = sp;
   return rp;
@@ -1031,13 +1030,13 @@ hub_status run_rows(hub_ansatz* a, SmallPlan* sp, RowPlan* rp, int dtype, const 
     ka.prep.sd32 = (const float*)a->d_sd32.p;
     const int nv = has_lam ? 2 : 1;
     const int no = g.op_end - g.op_begin;
-    const int nt = rows_threads(dtype, nv, ka.row_len, n_slots, a->n_gates, ka.n_hterms, no);
-    const size_t smem = rows_smem_bytes(dtype, nv, ka.row_len, n_slots, a->n_gates, ka.n_hterms, nt, no);
-    const int per_sm = std::max(1, rows_max_ctas_per_sm(dtype, nt, smem));
-    const int64_t grid = std::min<int64_t>(batch * (int64_t)ka.n_rows, (int64_t)sms * per_sm);
+    const RowLaunch rl = rows_launch(dtype, nv, ka.row_len, ka.n_rows, n_slots, a->n_gates, ka.n_hterms, no);
+    const int per_sm = std::max(1, rows_max_ctas_per_sm(dtype, rl));
+    const int64_t groups = batch * (int64_t)((ka.n_rows + rl.rr - 1) / rl.rr);
+    const int64_t grid = std::min<int64_t>(groups, (int64_t)sms * per_sm);
     hub_ansatz::ProfRec rec{};
     HUB_CUDA(record(rec, true), "cudaEventRecord");
-    HUB_CUDA(launch_rows(dtype, ka, nt, (int)grid, smem, st), "row kernel launch");
+    HUB_CUDA(launch_rows(dtype, ka, rl, (int)grid, st), "row kernel launch");
     rec.nv = 3;
     rec.dtype = dtype;
     const int io = ((g.flags & RS_PREP) ? 0 : 1) + ((g.flags & RS_WRITE_PSI) ? 1 : 0) +

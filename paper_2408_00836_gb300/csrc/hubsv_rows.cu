@@ -37,6 +37,12 @@ namespace {
 constexpr int kRowThreadsSmall = 256;
 constexpr int kRowThreadsLarge = 512;
 constexpr int kRowThreadsSolo = 1024;   // a c64 CTA alone on its SM (the longest rows with lam)
+// complex64 rows shorter than this are staged two per CTA: a hop then has
+// about one pair per thread, and staging two rows halves the per-operation
+// work and barriers per row (24 qubits: 1319 -> 1463 evals/s; at 28 qubits,
+// 3432 amplitudes a row, two rows per CTA measured 24 % slower, and c128
+// slower at both sizes).
+constexpr int kRowPairLen = 1024;
 }  // namespace
 
 // The row segments of a call kind: the operations of the on-chip plan
@@ -126,9 +132,9 @@ double row_plan_bytes(const SmallPlan* sp, const RowPlan* rp, int dtype, int* n_
 }
 
 size_t rows_smem_bytes(int dtype, int nv, int row_len, int n_slots, int n_gates, int n_hterms, int threads,
-                       int n_ops) {
+                       int n_ops, int rr) {
   const size_t amp = dtype == 0 ? 8 : 16;
-  size_t s = (size_t)nv * (size_t)row_len * amp;            // rows of psi (, lam)
+  size_t s = (size_t)rr * (size_t)nv * (size_t)row_len * amp;   // rows of psi (, lam)
   s = (s + 15) & ~(size_t)15;
   s += sizeof(SmallOpDev) * (size_t)n_ops;                  // the segment's operations
   s += 16 * (size_t)n_gates;                                // (cos, sin) of the element (see GC)
@@ -188,15 +194,17 @@ __device__ __forceinline__ R row_pair(T2* __restrict__ prow, T2* __restrict__ lr
   return part;
 }
 
-// One hop operation on a staged row: thread tid takes entries tid, tid +
-// NT, ... of the pair list, four loaded at a time (NT is a constant, so the
-// four loads share one address); the last round is predicated.  Returns this thread's share of the measured or gradient term.
-// K and DOL are fixed per call site, so the loops carry no branches on the
-// operation kind.
-template <int K, bool DOL, int NT, typename R, typename T2>
-__device__ __forceinline__ R row_hop(T2* __restrict__ prow, T2* __restrict__ lrow,
-                                     const uint32_t* __restrict__ pl, int nb, uint32_t rpar, R c, R s,
-                                     R cl, R sl, R tc) {
+// One hop operation on RR staged rows (row r at prow + r len, its lam at
+// lrow + r len): thread tid takes entries tid, tid + nth, ... of the pair
+// list, four loaded at a time, and applies each entry to every row (the
+// rows differ only in the row part of the Jordan-Wigner parity, rpar[r]).
+// Returns this thread's share of the measured or gradient term.  K and DOL
+// are fixed per call site, so the loops carry no branches on the operation
+// kind.
+template <int K, bool DOL, int NT, int RR, typename R, typename T2>
+__device__ __forceinline__ R row_hop(T2* __restrict__ prow, T2* __restrict__ lrow, int len,
+                                     const uint32_t* __restrict__ pl, int nb, const uint32_t (&rpar)[RR], R c,
+                                     R s, R cl, R sl, R tc) {
   R part = 0;
   const int tid = threadIdx.x, nth = blockDim.x;
   for (int it0 = tid; it0 < nb; it0 += 4 * nth) {
@@ -209,13 +217,18 @@ __device__ __forceinline__ R row_hop(T2* __restrict__ prow, T2* __restrict__ lro
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (it0 + k * nth >= nb) break;
-      part += row_pair<K, DOL>(prow, lrow, prs[k], rpar, c, s, cl, sl, tc);
+#pragma unroll
+      for (int r = 0; r < RR; ++r)   // one pair entry for all staged rows
+        part += row_pair<K, DOL>(prow + r * len, lrow + r * len, prs[k], rpar[r], c, s, cl, sl, tc);
     }
   }
   return part;
 }
 
-template <typename R, int NT>
+// RR: rows staged together (1 or 2, consecutive rows of one batch
+// element): every operation runs on all of them between two barriers, so
+// its per-operation work and the pair-list loads are shared.
+template <typename R, int NT, int RR>
 __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowThreadsLarge ? 2 : 1))
     rows_kernel(const RowArgs a) {
   constexpr int kRowWarps = NT / 32;
@@ -225,9 +238,9 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const bool has_lam = (a.flags & RS_HAS_LAM) != 0;
   const int len = a.row_len;
-  T2* prow = reinterpret_cast<T2*>(smem_raw);
-  T2* lrow = prow + len;
-  const size_t rows_b = (((size_t)(has_lam ? 2 : 1) * (size_t)len * sizeof(T2)) + 15) & ~(size_t)15;
+  T2* prow = reinterpret_cast<T2*>(smem_raw);   // [RR][len]
+  T2* lrow = prow + RR * len;                    // [RR][len]
+  const size_t rows_b = (((size_t)RR * (has_lam ? 2 : 1) * (size_t)len * sizeof(T2)) + 15) & ~(size_t)15;
   SmallOpDev* sops = reinterpret_cast<SmallOpDev*>(smem_raw + rows_b);
   const int n_ops = a.op_end - a.op_begin;
   using GT = typename GC<R>::T;
@@ -250,13 +263,14 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
     const int nw = n_ops * (int)(sizeof(SmallOpDev) / sizeof(int4));
     for (int i = tid; i < nw; i += nth) dst[i] = src[i];
   }
-  const int64_t total = a.batch * (int64_t)a.n_rows;
+  const int n_grp = (a.n_rows + RR - 1) / RR;   // row groups per batch element
+  const int64_t total = a.batch * (int64_t)n_grp;
   int64_t cur_b = -1;
   for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
-    const int64_t b = g / a.n_rows;
-    const int rr = (int)(g - b * a.n_rows);
+    const int64_t b = g / n_grp;
+    const int rr0 = (int)(g - b * n_grp) * RR;
     const int inst = (int)(b % a.n_inst);
-    __syncthreads();   // the previous row is stored
+    __syncthreads();   // the previous rows are stored
     if (b != cur_b) {
       if (cur_b >= 0) {   // read out the previous element's accumulators
         for (int i = tid; i < a.n_slots; i += nth) {
@@ -271,18 +285,35 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
       for (int i = tid; i < a.n_hterms; i += nth) hc[i] = (R)a.hcoef[(size_t)inst * a.n_hterms + i];
       cur_b = b;
     }
-    const uint32_t xr = a.xrow[rr];
-    const size_t base = ((size_t)b * (size_t)a.n_rows + (size_t)rr) * (size_t)len;
-    if (a.flags & RS_PREP) {
-      for (int i = tid; i < len; i += nth) prow[i] = mk<T2, R>(prep_amp<R>(a.prep, sdt, xr | a.xin[i], inst), (R)0);
-    } else {
-      for (int i = tid; i < len; i += nth) prow[i] = psi[base + i];
+    // rows of the group; a missing last row (odd row count) is staged as
+    // zeros with the first row's pattern, and not stored
+    uint32_t xr[RR];
+    bool live[RR];
+    size_t base[RR];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+      live[r] = rr0 + r < a.n_rows;
+      const int row = live[r] ? rr0 + r : rr0;
+      xr[r] = a.xrow[row];
+      base[r] = ((size_t)b * (size_t)a.n_rows + (size_t)row) * (size_t)len;
     }
-    if (has_lam) {
-      if (a.flags & RS_READ_LAM) {
-        for (int i = tid; i < len; i += nth) lrow[i] = lam[base + i];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+      T2* pr = prow + r * len;
+      T2* lr = lrow + r * len;
+      if (!live[r]) {
+        for (int i = tid; i < len; i += nth) pr[i] = mk<T2, R>((R)0, (R)0);
+      } else if (a.flags & RS_PREP) {
+        for (int i = tid; i < len; i += nth) pr[i] = mk<T2, R>(prep_amp<R>(a.prep, sdt, xr[r] | a.xin[i], inst), (R)0);
       } else {
-        for (int i = tid; i < len; i += nth) lrow[i] = mk<T2, R>((R)0, (R)0);
+        for (int i = tid; i < len; i += nth) pr[i] = psi[base[r] + i];
+      }
+      if (has_lam) {
+        if (live[r] && (a.flags & RS_READ_LAM)) {
+          for (int i = tid; i < len; i += nth) lr[i] = lam[base[r] + i];
+        } else {
+          for (int i = tid; i < len; i += nth) lr[i] = mk<T2, R>((R)0, (R)0);
+        }
       }
     }
     __syncthreads();
@@ -314,20 +345,24 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
         }
         if (op.kind != OP_GIV) tc = hc[op.hterm];
         const bool dol = (op.flags & OPF_LAM) != 0;
-        // the row's part of the Jordan-Wigner parity (the in-row part is
+        // the rows' part of the Jordan-Wigner parity (the in-row part is
         // bit 31 of the pair entry)
-        const uint32_t rpar = (uint32_t)__popc(xr & op.between) & 1u;
+        uint32_t rpar[RR];
+#pragma unroll
+        for (int r = 0; r < RR; ++r) rpar[r] = (uint32_t)__popc(xr[r] & op.between) & 1u;
         const uint32_t* pl = a.pairs + op.a;
+#define HUB_HOP(K, D) row_hop<K, D, NT, RR>(prow, lrow, len, pl, op.b, rpar, c, s, cl, sl, tc)
         switch (op.kind) {
           case OP_GIV:
-            if (dol) row_hop<RH_GIV, true, NT>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc);
-            else row_hop<RH_GIV, false, NT>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc);
+            if (dol) HUB_HOP(RH_GIV, true);
+            else HUB_HOP(RH_GIV, false);
             break;
-          case OP_MEAS_HOP: part = row_hop<RH_MEAS, false, NT>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc); break;
-          case OP_LAM_HOP: part = row_hop<RH_LAM, false, NT>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc); break;
-          case OP_GRADINV_HOP: part = row_hop<RH_GRADINV, true, NT>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc); break;
-          default: part = row_hop<RH_GRAD, false, NT>(prow, lrow, pl, op.b, rpar, c, s, cl, sl, tc); break;
+          case OP_MEAS_HOP: part = HUB_HOP(RH_MEAS, false); break;
+          case OP_LAM_HOP: part = HUB_HOP(RH_LAM, false); break;
+          case OP_GRADINV_HOP: part = HUB_HOP(RH_GRADINV, true); break;
+          default: part = HUB_HOP(RH_GRAD, false); break;
         }
+#undef HUB_HOP
         if (op.kind == OP_GRAD_HOP || op.kind == OP_GRADINV_HOP) add_slot(op.slot, (R)2 * part);
         else if (op.kind != OP_GIV) eacc.add((R)2 * part);
       } else {   // diagonal operations
@@ -341,51 +376,71 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
         switch (op.kind) {
           case OP_DIAG:
             for (int e = tid; e < len; e += nth) {
-              T2 p = dv.phase(ptab, xr | __ldg(xin + e), a.s, upm);
-              if (inv) p.y = -p.y;
-              prow[e] = cmul(prow[e], p);
-              if (dol) lrow[e] = cmul(lrow[e], p);
+              const uint32_t xi = __ldg(xin + e);
+#pragma unroll
+              for (int r = 0; r < RR; ++r) {
+                T2 p = dv.phase(ptab, xr[r] | xi, a.s, upm);
+                if (inv) p.y = -p.y;
+                prow[r * len + e] = cmul(prow[r * len + e], p);
+                if (dol) lrow[r * len + e] = cmul(lrow[r * len + e], p);
+              }
             }
             break;
           case OP_GRAD_DIAG:
             for (int e = tid; e < len; e += nth) {
-              const R v = dv.real(rtab, xr | __ldg(xin + e), a.s, upm);
-              const T2 u = prow[e], l = lrow[e];
-              part += v * (l.x * u.y - l.y * u.x);
+              const uint32_t xi = __ldg(xin + e);
+#pragma unroll
+              for (int r = 0; r < RR; ++r) {
+                const R v = dv.real(rtab, xr[r] | xi, a.s, upm);
+                const T2 u = prow[r * len + e], l = lrow[r * len + e];
+                part += v * (l.x * u.y - l.y * u.x);
+              }
             }
             break;
           case OP_GRADINV_DIAG:   // the gradient term, then the inverse phase on both
             for (int e = tid; e < len; e += nth) {
-              const uint32_t x = xr | __ldg(xin + e);
-              const R v = dv.real(rtab, x, a.s, upm);
-              T2 p = dv.phase(ptab, x, a.s, upm);
-              if (inv) p.y = -p.y;
-              const T2 u = prow[e], l = lrow[e];
-              part += v * (l.x * u.y - l.y * u.x);
-              prow[e] = cmul(u, p);
-              lrow[e] = cmul(l, p);
+              const uint32_t xi = __ldg(xin + e);
+#pragma unroll
+              for (int r = 0; r < RR; ++r) {
+                const uint32_t x = xr[r] | xi;
+                const R v = dv.real(rtab, x, a.s, upm);
+                T2 p = dv.phase(ptab, x, a.s, upm);
+                if (inv) p.y = -p.y;
+                const T2 u = prow[r * len + e], l = lrow[r * len + e];
+                part += v * (l.x * u.y - l.y * u.x);
+                prow[r * len + e] = cmul(u, p);
+                lrow[r * len + e] = cmul(l, p);
+              }
             }
             break;
           case OP_LAM_DIAG:
             for (int e = tid; e < len; e += nth) {
-              const R v = dv.real(rtab, xr | __ldg(xin + e), a.s, upm);
-              const T2 u = prow[e];
-              const R m2 = u.x * u.x + u.y * u.y;
-              part += v * m2;
-              npart += m2;
-              T2 l = lrow[e];
-              l.x += v * u.x;
-              l.y += v * u.y;
-              lrow[e] = l;
+              const uint32_t xi = __ldg(xin + e);
+#pragma unroll
+              for (int r = 0; r < RR; ++r) {
+                const R v = dv.real(rtab, xr[r] | xi, a.s, upm);
+                const T2 u = prow[r * len + e];
+                const R m2 = u.x * u.x + u.y * u.y;
+                part += v * m2;
+                npart += m2;
+                T2 l = lrow[r * len + e];
+                l.x += v * u.x;
+                l.y += v * u.y;
+                lrow[r * len + e] = l;
+              }
             }
             break;
           default:   // OP_MEAS_DIAG
             for (int e = tid; e < len; e += nth) {
-              const R v = dv.real(rtab, xr | __ldg(xin + e), a.s, upm);
-              const T2 u = prow[e];
-              const R m2 = u.x * u.x + u.y * u.y;
-              part += v * m2;
-              npart += m2;
+              const uint32_t xi = __ldg(xin + e);
+#pragma unroll
+              for (int r = 0; r < RR; ++r) {
+                const R v = dv.real(rtab, xr[r] | xi, a.s, upm);
+                const T2 u = prow[r * len + e];
+                const R m2 = u.x * u.x + u.y * u.y;
+                part += v * m2;
+                npart += m2;
+              }
             }
             break;
         }
@@ -403,10 +458,14 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
       row_add_tot(acc, a.n_slots, a.slot_E, eacc);
       row_add_tot(acc, a.n_slots, a.slot_N, nacc);
     }
-    if (a.flags & RS_WRITE_PSI)
-      for (int i = tid; i < len; i += nth) psi[base + i] = prow[i];
-    if (has_lam && (a.flags & RS_WRITE_LAM))
-      for (int i = tid; i < len; i += nth) lam[base + i] = lrow[i];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+      if (!live[r]) continue;
+      if (a.flags & RS_WRITE_PSI)
+        for (int i = tid; i < len; i += nth) psi[base[r] + i] = prow[r * len + i];
+      if (has_lam && (a.flags & RS_WRITE_LAM))
+        for (int i = tid; i < len; i += nth) lam[base[r] + i] = lrow[r * len + i];
+    }
   }
   __syncthreads();
   if (cur_b >= 0) {
@@ -446,40 +505,57 @@ __global__ void __launch_bounds__(256) transpose_kernel(const T2* __restrict__ i
 }  // namespace
 
 namespace {
-const void* rows_fn(int dtype, int threads) {
-  if (threads == kRowThreadsSolo)
-    return dtype == 0 ? (const void*)rows_kernel<float, kRowThreadsSolo>
-                      : (const void*)rows_kernel<double, kRowThreadsSolo>;
-  if (threads == kRowThreadsSmall)
-    return dtype == 0 ? (const void*)rows_kernel<float, kRowThreadsSmall>
-                      : (const void*)rows_kernel<double, kRowThreadsSmall>;
-  return dtype == 0 ? (const void*)rows_kernel<float, kRowThreadsLarge>
-                    : (const void*)rows_kernel<double, kRowThreadsLarge>;
+template <int NT, int RR>
+const void* rows_fn_nt(int dtype) {
+  return dtype == 0 ? (const void*)rows_kernel<float, NT, RR> : (const void*)rows_kernel<double, NT, RR>;
+}
+template <int RR>
+const void* rows_fn_rr(int dtype, int threads) {
+  if (threads == kRowThreadsSolo) return rows_fn_nt<kRowThreadsSolo, RR>(dtype);
+  if (threads == kRowThreadsSmall) return rows_fn_nt<kRowThreadsSmall, RR>(dtype);
+  return rows_fn_nt<kRowThreadsLarge, RR>(dtype);
+}
+const void* rows_fn(int dtype, const RowLaunch& L) {
+  return L.rr == 2 ? rows_fn_rr<2>(dtype, L.threads) : rows_fn_rr<1>(dtype, L.threads);
+}
+// Threads per CTA for a row sweep of smem(threads) bytes: 256 where three
+// such CTAs fit an SM, 512 where two fit (and for c128), else 1024.
+template <typename F>
+int pick_threads(int dtype, F smem) {
+  if (3 * (smem(kRowThreadsSmall) + 1024) <= (size_t)228 * 1024) return kRowThreadsSmall;
+  if (2 * (smem(kRowThreadsLarge) + 1024) <= (size_t)228 * 1024 || dtype != 0) return kRowThreadsLarge;
+  return kRowThreadsSolo;
 }
 }  // namespace
 
-int rows_threads(int dtype, int nv, int row_len, int n_slots, int n_gates, int n_hterms, int n_ops) {
-  const size_t s = rows_smem_bytes(dtype, nv, row_len, n_slots, n_gates, n_hterms, kRowThreadsSmall, n_ops);
-  if (3 * (s + 1024) <= (size_t)228 * 1024) return kRowThreadsSmall;
-  const size_t sl = rows_smem_bytes(dtype, nv, row_len, n_slots, n_gates, n_hterms, kRowThreadsLarge, n_ops);
-  if (2 * (sl + 1024) <= (size_t)228 * 1024 || dtype != 0) return kRowThreadsLarge;
-  return kRowThreadsSolo;
+RowLaunch rows_launch(int dtype, int nv, int row_len, int n_rows, int n_slots, int n_gates, int n_hterms,
+                      int n_ops) {
+  RowLaunch L;
+  for (int rr = (n_rows >= 2 && dtype == 0 && row_len < kRowPairLen) ? 2 : 1; rr >= 1; --rr) {
+    auto smem = [&](int nt) { return rows_smem_bytes(dtype, nv, row_len, n_slots, n_gates, n_hterms, nt, n_ops, rr); };
+    const int nt = pick_threads(dtype, smem);
+    L.threads = nt;
+    L.rr = rr;
+    L.smem = smem(nt);
+    if (L.smem + 1024 <= (size_t)228 * 1024) break;   // two rows fit one CTA, else one
+  }
+  return L;
 }
 
-cudaError_t launch_rows(int dtype, const RowArgs& a, int threads, int grid, size_t smem, cudaStream_t st) {
-  const void* f = rows_fn(dtype, threads);
-  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_rows(int dtype, const RowArgs& a, const RowLaunch& L, int grid, cudaStream_t st) {
+  const void* f = rows_fn(dtype, L);
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
   if (e != cudaSuccess) return e;
   RowArgs ac = a;
   void* args[] = {(void*)&ac};
-  return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, st);
+  return cudaLaunchKernel(f, dim3(grid), dim3(L.threads), args, L.smem, st);
 }
 
-int rows_max_ctas_per_sm(int dtype, int threads, size_t smem) {
-  const void* f = rows_fn(dtype, threads);
-  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+int rows_max_ctas_per_sm(int dtype, const RowLaunch& L) {
+  const void* f = rows_fn(dtype, L);
+  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem) != cudaSuccess) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, L.threads, L.smem) != cudaSuccess) return 0;
   return n;
 }
 

@@ -110,16 +110,23 @@ struct RowArgs {
   PrepDev prep;
 };
 
-// Shared memory of a row sweep: the rows of psi (and lam), the segment's
-// operation records, the element's Givens coefficients, the accumulator
-// rows and the -t values.
+// Shared memory of a row sweep that stages rr rows: the rows of psi (and
+// lam), the segment's operation records, the element's Givens
+// coefficients, the accumulator rows and the -t values.
 size_t rows_smem_bytes(int dtype, int nv, int row_len, int n_slots, int n_gates, int n_hterms, int threads,
-                       int n_ops);
-// Threads per CTA of a row sweep (256 where three such CTAs fit an SM, 1024
-// for a c64 CTA alone on its SM, else 512).
-int rows_threads(int dtype, int nv, int row_len, int n_slots, int n_gates, int n_hterms, int n_ops);
-cudaError_t launch_rows(int dtype, const RowArgs& a, int threads, int grid, size_t smem, cudaStream_t st);
-int rows_max_ctas_per_sm(int dtype, int threads, size_t smem);
+                       int n_ops, int rr);
+// Launch shape of a row sweep: rows staged together (2 for short complex64
+// rows where two fit one CTA, else 1), threads per CTA (256 where three
+// such CTAs fit an SM, 1024 for a c64 CTA alone on its SM, else 512) and
+// shared memory.
+struct RowLaunch {
+  int threads = 0, rr = 1;
+  size_t smem = 0;
+};
+RowLaunch rows_launch(int dtype, int nv, int row_len, int n_rows, int n_slots, int n_gates, int n_hterms,
+                      int n_ops);
+cudaError_t launch_rows(int dtype, const RowArgs& a, const RowLaunch& L, int grid, cudaStream_t st);
+int rows_max_ctas_per_sm(int dtype, const RowLaunch& L);
 // out[b][c][r] = in[b][r][c] for a [batch][n_r][n_c] matrix of amplitudes.
 cudaError_t launch_transpose(int dtype, const void* in, void* out, int64_t batch, int n_r, int n_c,
                              cudaStream_t st);
