@@ -101,6 +101,11 @@ typedef enum { HUB_PREP_SLATER = 0, HUB_PREP_NEEL = 1 } hub_prep;
                                     where another engine applies (energy_grad) */
 #define HUB_FLAG_ROWS       8u   /* skip the on-chip engine: run on the row
                                     engine where it applies (energy_grad)      */
+#define HUB_FLAG_ROW_CLUSTER 16u /* row engine: stage each row of psi and its
+                                    row of lam on a cluster of two CTAs, one
+                                    row each, even where one CTA would hold
+                                    both (the staging it uses for rows too
+                                    large for one SM; for tests and tuning)  */
 
 /* Lattice: sites 0..n_sites-1, undirected bonds (pairs of sites).  mode_up /
  * mode_dn map a site to its two qubits; both NULL = blocked order (up i -> i,

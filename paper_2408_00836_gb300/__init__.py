@@ -32,6 +32,7 @@ FLAG_PREP_FUSED = 1
 FLAG_KEEP_STATE = 2
 FLAG_SWEEPS = 4
 FLAG_ROWS = 8
+FLAG_ROW_CLUSTER = 16
 CLASS_IDS = {"h1": 0, "h2": 1, "v1": 2, "v2": 3, "even": 0, "odd": 1}
 
 
@@ -288,13 +289,16 @@ class Ansatz:
         return E
 
     def energy_grad(self, theta, psi, lam, E, grad, ckpt=None, dtype=C64, batch: int = 1,
-                    fused: bool = True, sweeps: bool = False, rows: bool = False, stream=None):
+                    fused: bool = True, sweeps: bool = False, rows: bool = False, row_cluster: bool = False,
+                    stream=None):
+        """row_cluster: HUB_FLAG_ROW_CLUSTER (rows of psi and lam on two-CTA
+        clusters wherever the row engine runs them)."""
         nb = self.workspace(1, dtype, batch, fused, False, sweeps, rows)[0]
         dense = batch * self.amp_bytes(dtype)
+        flags = self._flags(fused, False, sweeps, rows) | (FLAG_ROW_CLUSTER if row_cluster else 0)
         check(lib().energy_grad(self._h, _ptr(theta, 8 * batch * self.P, "theta"), _ptr(psi, max(nb, 1), "psi"),
                                 _ptr(lam, max(nb, 1), "lam"), _ptr(ckpt, dense, "ckpt"), _ptr(E, 8 * batch, "E"),
-                                _ptr(grad, 8 * batch * self.P, "grad"), dtype, batch,
-                                self._flags(fused, False, sweeps, rows), _stream(stream)))
+                                _ptr(grad, 8 * batch * self.P, "grad"), dtype, batch, flags, _stream(stream)))
         return E, grad
 
     def apply_h(self, psi, lam, dtype=C64, batch: int = 1, stream=None):

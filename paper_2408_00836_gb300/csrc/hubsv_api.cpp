@@ -915,14 +915,17 @@ RowPlan* row_plan_for(hub_ansatz* a, int which, int dtype, uint32_t flags, Small
     const int len = g.orient == 0 ? sp->cup : sp->cdn;
     const int nr = g.orient == 0 ? sp->cdn : sp->cup;
     const int no = g.op_end - g.op_begin;
-    if ((int)rows_launch(dtype, nv, len, nr, a->P + 2, a->n_gates, a->n_hcol, no).smem > optin) return nullptr;
+    const RowLaunch rl =
+        rows_launch(dtype, nv, len, nr, a->P + 2, a->n_gates, a->n_hcol, no, (flags & HUB_FLAG_ROW_CLUSTER) != 0);
+    if ((int)rl.smem > optin || rl.smem == 0) return nullptr;
   }
   sp_out = sp;
   return rp;
 }
 
 hub_status run_rows(hub_ansatz* a, SmallPlan* sp, RowPlan* rp, int dtype, const double* theta, void* psi,
-                    void* lam, int64_t batch, double* E, double* grad, cudaStream_t st) {
+                    void* lam, int64_t batch, double* E, double* grad, uint32_t flags, cudaStream_t st) {
+  const bool force_cluster = (flags & HUB_FLAG_ROW_CLUSTER) != 0;
   const int n_slots = a->P + 2;
   hub_status s;
   if ((s = ensure_device(a)) != HUB_OK) return s;
@@ -1030,10 +1033,18 @@ hub_status run_rows(hub_ansatz* a, SmallPlan* sp, RowPlan* rp, int dtype, const 
     ka.prep.sd32 = (const float*)a->d_sd32.p;
     const int nv = has_lam ? 2 : 1;
     const int no = g.op_end - g.op_begin;
-    const RowLaunch rl = rows_launch(dtype, nv, ka.row_len, ka.n_rows, n_slots, a->n_gates, ka.n_hterms, no);
-    const int per_sm = std::max(1, rows_max_ctas_per_sm(dtype, rl));
+    const RowLaunch rl =
+        rows_launch(dtype, nv, ka.row_len, ka.n_rows, n_slots, a->n_gates, ka.n_hterms, no, force_cluster);
     const int64_t groups = batch * (int64_t)((ka.n_rows + rl.rr - 1) / rl.rr);
-    const int64_t grid = std::min<int64_t>(groups, (int64_t)sms * per_sm);
+    int64_t grid;
+    if (rl.cl == 1) {
+      const int per_sm = std::max(1, rows_max_ctas_per_sm(dtype, rl));
+      grid = std::min<int64_t>(groups, (int64_t)sms * per_sm);
+    } else {   // whole clusters, as many as can be resident
+      const int ncl = rows_max_clusters(dtype, rl);
+      if (ncl <= 0) return fail(HUB_EUNSUPPORTED, "row engine: no cluster of two CTAs fits");
+      grid = (int64_t)rl.cl * std::min<int64_t>(groups, ncl);
+    }
     hub_ansatz::ProfRec rec{};
     HUB_CUDA(record(rec, true), "cudaEventRecord");
     HUB_CUDA(launch_rows(dtype, ka, rl, (int)grid, st), "row kernel launch");
@@ -1151,7 +1162,7 @@ extern "C" hub_status energy(ans_t a, const double* theta, void* psi, double* E,
     return run_small(a, sp, smem, dtype, theta, batch, E, nullptr, (cudaStream_t)stream);
   SmallPlan* rsp = nullptr;
   if (RowPlan* rp = row_plan_for(a, 0, dtype, flags, rsp))
-    return run_rows(a, rsp, rp, dtype, theta, psi, nullptr, batch, E, nullptr, (cudaStream_t)stream);
+    return run_rows(a, rsp, rp, dtype, theta, psi, nullptr, batch, E, nullptr, flags, (cudaStream_t)stream);
   Plan* pl;
   if ((s = get_plan(a, 0, dtype, flags & 3u, pl)) != HUB_OK) return s;
   return run_plan(a, pl, dtype, theta, psi, nullptr, nullptr, batch, E, nullptr, (cudaStream_t)stream);
@@ -1172,7 +1183,7 @@ extern "C" hub_status energy_grad(ans_t a, const double* theta, void* psi, void*
     return run_small(a, sp, smem, dtype, theta, batch, E, grad, (cudaStream_t)stream);
   SmallPlan* rsp = nullptr;
   if (RowPlan* rp = row_plan_for(a, 1, dtype, flags, rsp))
-    return run_rows(a, rsp, rp, dtype, theta, psi, lam, batch, E, grad, (cudaStream_t)stream);
+    return run_rows(a, rsp, rp, dtype, theta, psi, lam, batch, E, grad, flags, (cudaStream_t)stream);
   const uint32_t pf = (flags & 3u) | (ckpt ? kPlanCkpt : 0u);
   Plan* pl;
   if ((s = get_plan(a, 1, dtype, pf, pl)) != HUB_OK) return s;

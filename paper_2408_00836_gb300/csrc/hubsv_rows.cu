@@ -21,8 +21,12 @@
 #include <algorithm>
 #include <cstring>
 
+#include <cooperative_groups.h>
+
 #include "hubsv_host.h"
 #include "hubsv_reduce.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace hubsv {
 
@@ -196,7 +200,8 @@ __device__ __forceinline__ R row_pair(T2* __restrict__ prow, T2* __restrict__ lr
 
 // One hop operation on RR staged rows (row r at prow + r len, its lam at
 // lrow + r len): thread tid takes entries tid, tid + nth, ... of the pair
-// list, four loaded at a time, and applies each entry to every row (the
+// list (tid, nth: the thread's index and count over the CTAs sharing the
+// rows), four loaded at a time, and applies each entry to every row (the
 // rows differ only in the row part of the Jordan-Wigner parity, rpar[r]).
 // Returns this thread's share of the measured or gradient term.  K and DOL
 // are fixed per call site, so the loops carry no branches on the operation
@@ -204,9 +209,8 @@ __device__ __forceinline__ R row_pair(T2* __restrict__ prow, T2* __restrict__ lr
 template <int K, bool DOL, int NT, int RR, typename R, typename T2>
 __device__ __forceinline__ R row_hop(T2* __restrict__ prow, T2* __restrict__ lrow, int len,
                                      const uint32_t* __restrict__ pl, int nb, const uint32_t (&rpar)[RR], R c,
-                                     R s, R cl, R sl, R tc) {
+                                     R s, R cl, R sl, R tc, int tid, int nth) {
   R part = 0;
-  const int tid = threadIdx.x, nth = blockDim.x;
   for (int it0 = tid; it0 < nb; it0 += 4 * nth) {
     uint32_t prs[4];
 #pragma unroll
@@ -228,8 +232,14 @@ __device__ __forceinline__ R row_hop(T2* __restrict__ prow, T2* __restrict__ lro
 // RR: rows staged together (1 or 2, consecutive rows of one batch
 // element): every operation runs on all of them between two barriers, so
 // its per-operation work and the pair-list loads are shared.
-template <typename R, int NT, int RR>
-__global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowThreadsLarge ? 2 : 1))
+// CL = 2: a row of psi and its row of lam too large for one SM's shared
+// memory (complex128 at 32 qubits: 2 x 206 KB) are staged by a cluster of
+// two CTAs, psi in rank 0's shared memory and lam in rank 1's; both CTAs
+// work on every operation (entries and elements split between them) and
+// reach the other's row through distributed shared memory, with a cluster
+// barrier wherever one CTA would synchronise.
+template <typename R, int NT, int RR, int CL>
+__global__ void __launch_bounds__(NT, CL == 2 ? 1 : (NT == kRowThreadsSmall ? 4 : (NT == kRowThreadsLarge ? 2 : 1)))
     rows_kernel(const RowArgs a) {
   constexpr int kRowWarps = NT / 32;
   using T2 = typename CT<R>::T2;
@@ -238,9 +248,22 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const bool has_lam = (a.flags & RS_HAS_LAM) != 0;
   const int len = a.row_len;
-  T2* prow = reinterpret_cast<T2*>(smem_raw);   // [RR][len]
-  T2* lrow = prow + RR * len;                    // [RR][len]
-  const size_t rows_b = (((size_t)RR * (has_lam ? 2 : 1) * (size_t)len * sizeof(T2)) + 15) & ~(size_t)15;
+  T2* const mine = reinterpret_cast<T2*>(smem_raw);   // the rows this CTA stages
+  T2* prow = mine;                                     // [RR][len]
+  T2* lrow = prow + RR * len;                          // [RR][len]
+  int rank = 0;
+  if constexpr (CL == 2) {
+    cg::cluster_group cluster = cg::this_cluster();
+    rank = (int)cluster.block_rank();
+    prow = cluster.map_shared_rank(mine, 0);
+    lrow = cluster.map_shared_rank(mine, 1);
+  }
+  auto row_sync = [&]() {
+    if constexpr (CL == 2) cg::this_cluster().sync();
+    else __syncthreads();
+  };
+  const size_t rows_b =
+      (((size_t)RR * (has_lam && CL == 1 ? 2 : 1) * (size_t)len * sizeof(T2)) + 15) & ~(size_t)15;
   SmallOpDev* sops = reinterpret_cast<SmallOpDev*>(smem_raw + rows_b);
   const int n_ops = a.op_end - a.op_begin;
   using GT = typename GC<R>::T;
@@ -248,6 +271,7 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
   AccT* acc = reinterpret_cast<AccT*>(cs + a.n_gates);   // [kRowWarps][n_slots]
   R* hc = reinterpret_cast<R*>(acc + kRowWarps * a.n_slots);
   const int tid = threadIdx.x, nth = blockDim.x;
+  const int wtid = tid + rank * nth, wnth = CL * nth;   // work split over the cluster
   const R* rtabs = reinterpret_cast<const R*>(DT == 0 ? (const void*)a.real_tabs32 : (const void*)a.real_tabs);
   const T2* ptabs = reinterpret_cast<const T2*>(a.phase_tabs);
   const GT* coef = reinterpret_cast<const GT*>(a.coef);
@@ -266,11 +290,11 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
   const int n_grp = (a.n_rows + RR - 1) / RR;   // row groups per batch element
   const int64_t total = a.batch * (int64_t)n_grp;
   int64_t cur_b = -1;
-  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+  for (int64_t g = blockIdx.x / CL; g < total; g += gridDim.x / CL) {
     const int64_t b = g / n_grp;
     const int rr0 = (int)(g - b * n_grp) * RR;
     const int inst = (int)(b % a.n_inst);
-    __syncthreads();   // the previous rows are stored
+    row_sync();   // the previous rows are stored
     if (b != cur_b) {
       if (cur_b >= 0) {   // read out the previous element's accumulators
         for (int i = tid; i < a.n_slots; i += nth) {
@@ -299,6 +323,16 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
     }
 #pragma unroll
     for (int r = 0; r < RR; ++r) {
+      if constexpr (CL == 2) {   // rank 0 stages the psi row, rank 1 the lam row
+        if (rank == 0) {
+          for (int i = tid; i < len; i += nth) mine[i] = psi[base[r] + i];
+        } else if (a.flags & RS_READ_LAM) {
+          for (int i = tid; i < len; i += nth) mine[i] = lam[base[r] + i];
+        } else {
+          for (int i = tid; i < len; i += nth) mine[i] = mk<T2, R>((R)0, (R)0);
+        }
+        continue;
+      }
       T2* pr = prow + r * len;
       T2* lr = lrow + r * len;
       if (!live[r]) {
@@ -316,7 +350,7 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
         }
       }
     }
-    __syncthreads();
+    row_sync();
     Tot<R> eacc, nacc;
     // gradient terms of consecutive operations with one accumulator slot
     // (the factors of one parameter) are summed per thread and reduced once
@@ -351,7 +385,7 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
 #pragma unroll
         for (int r = 0; r < RR; ++r) rpar[r] = (uint32_t)__popc(xr[r] & op.between) & 1u;
         const uint32_t* pl = a.pairs + op.a;
-#define HUB_HOP(K, D) row_hop<K, D, NT, RR>(prow, lrow, len, pl, op.b, rpar, c, s, cl, sl, tc)
+#define HUB_HOP(K, D) row_hop<K, D, NT, RR>(prow, lrow, len, pl, op.b, rpar, c, s, cl, sl, tc, wtid, wnth)
         switch (op.kind) {
           case OP_GIV:
             if (dol) HUB_HOP(RH_GIV, true);
@@ -375,7 +409,7 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
         const uint32_t* __restrict__ xin = a.xin;
         switch (op.kind) {
           case OP_DIAG:
-            for (int e = tid; e < len; e += nth) {
+            for (int e = wtid; e < len; e += wnth) {
               const uint32_t xi = __ldg(xin + e);
 #pragma unroll
               for (int r = 0; r < RR; ++r) {
@@ -387,7 +421,7 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
             }
             break;
           case OP_GRAD_DIAG:
-            for (int e = tid; e < len; e += nth) {
+            for (int e = wtid; e < len; e += wnth) {
               const uint32_t xi = __ldg(xin + e);
 #pragma unroll
               for (int r = 0; r < RR; ++r) {
@@ -398,7 +432,7 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
             }
             break;
           case OP_GRADINV_DIAG:   // the gradient term, then the inverse phase on both
-            for (int e = tid; e < len; e += nth) {
+            for (int e = wtid; e < len; e += wnth) {
               const uint32_t xi = __ldg(xin + e);
 #pragma unroll
               for (int r = 0; r < RR; ++r) {
@@ -414,7 +448,7 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
             }
             break;
           case OP_LAM_DIAG:
-            for (int e = tid; e < len; e += nth) {
+            for (int e = wtid; e < len; e += wnth) {
               const uint32_t xi = __ldg(xin + e);
 #pragma unroll
               for (int r = 0; r < RR; ++r) {
@@ -431,7 +465,7 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
             }
             break;
           default:   // OP_MEAS_DIAG
-            for (int e = tid; e < len; e += nth) {
+            for (int e = wtid; e < len; e += wnth) {
               const uint32_t xi = __ldg(xin + e);
 #pragma unroll
               for (int r = 0; r < RR; ++r) {
@@ -451,7 +485,7 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
           nacc.add(npart);
         }
       }
-      __syncthreads();
+      row_sync();
     }
     if (rslot >= 0) row_add(acc, a.n_slots, rslot, racc);
     if (meas) {
@@ -460,6 +494,13 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
     }
 #pragma unroll
     for (int r = 0; r < RR; ++r) {
+      if constexpr (CL == 2) {
+        if (rank == 0 && (a.flags & RS_WRITE_PSI))
+          for (int i = tid; i < len; i += nth) psi[base[r] + i] = mine[i];
+        if (rank == 1 && (a.flags & RS_WRITE_LAM))
+          for (int i = tid; i < len; i += nth) lam[base[r] + i] = mine[i];
+        continue;
+      }
       if (!live[r]) continue;
       if (a.flags & RS_WRITE_PSI)
         for (int i = tid; i < len; i += nth) psi[base[r] + i] = prow[r * len + i];
@@ -467,7 +508,7 @@ __global__ void __launch_bounds__(NT, NT == kRowThreadsSmall ? 4 : (NT == kRowTh
         for (int i = tid; i < len; i += nth) lam[base[r] + i] = lrow[r * len + i];
     }
   }
-  __syncthreads();
+  row_sync();   // (cluster: no CTA leaves while the other may read its row)
   if (cur_b >= 0) {
     for (int i = tid; i < a.n_slots; i += nth) {
       double x = 0.0;
@@ -507,7 +548,7 @@ __global__ void __launch_bounds__(256) transpose_kernel(const T2* __restrict__ i
 namespace {
 template <int NT, int RR>
 const void* rows_fn_nt(int dtype) {
-  return dtype == 0 ? (const void*)rows_kernel<float, NT, RR> : (const void*)rows_kernel<double, NT, RR>;
+  return dtype == 0 ? (const void*)rows_kernel<float, NT, RR, 1> : (const void*)rows_kernel<double, NT, RR, 1>;
 }
 template <int RR>
 const void* rows_fn_rr(int dtype, int threads) {
@@ -516,6 +557,9 @@ const void* rows_fn_rr(int dtype, int threads) {
   return rows_fn_nt<kRowThreadsLarge, RR>(dtype);
 }
 const void* rows_fn(int dtype, const RowLaunch& L) {
+  if (L.cl == 2)
+    return dtype == 0 ? (const void*)rows_kernel<float, kRowThreadsLarge, 1, 2>
+                      : (const void*)rows_kernel<double, kRowThreadsLarge, 1, 2>;
   return L.rr == 2 ? rows_fn_rr<2>(dtype, L.threads) : rows_fn_rr<1>(dtype, L.threads);
 }
 // Threads per CTA for a row sweep of smem(threads) bytes: 256 where three
@@ -526,18 +570,43 @@ int pick_threads(int dtype, F smem) {
   if (2 * (smem(kRowThreadsLarge) + 1024) <= (size_t)228 * 1024 || dtype != 0) return kRowThreadsLarge;
   return kRowThreadsSolo;
 }
+cudaLaunchConfig_t rows_config(const RowLaunch& L, int grid, cudaStream_t st, cudaLaunchAttribute* at) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)L.threads);
+  cfg.dynamicSmemBytes = L.smem;
+  cfg.stream = st;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)L.cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cfg;
+}
 }  // namespace
 
 RowLaunch rows_launch(int dtype, int nv, int row_len, int n_rows, int n_slots, int n_gates, int n_hterms,
-                      int n_ops) {
+                      int n_ops, bool force_cluster) {
   RowLaunch L;
-  for (int rr = (n_rows >= 2 && dtype == 0 && row_len < kRowPairLen) ? 2 : 1; rr >= 1; --rr) {
+  for (int rr = (n_rows >= 2 && dtype == 0 && row_len < kRowPairLen) ? 2 : 1; rr >= 1 && !(force_cluster && nv == 2);
+       --rr) {
     auto smem = [&](int nt) { return rows_smem_bytes(dtype, nv, row_len, n_slots, n_gates, n_hterms, nt, n_ops, rr); };
     const int nt = pick_threads(dtype, smem);
     L.threads = nt;
     L.rr = rr;
     L.smem = smem(nt);
-    if (L.smem + 1024 <= (size_t)228 * 1024) break;   // two rows fit one CTA, else one
+    if (L.smem + 1024 <= (size_t)228 * 1024) return L;   // two rows fit one CTA, else one
+  }
+  L = RowLaunch();   // smem = 0: no launch shape fits
+  if (nv == 2) {   // psi and lam rows on a cluster of two CTAs, one row each
+    const size_t s1 = rows_smem_bytes(dtype, 1, row_len, n_slots, n_gates, n_hterms, kRowThreadsLarge, n_ops, 1);
+    if (s1 + 1024 <= (size_t)228 * 1024) {
+      L.threads = kRowThreadsLarge;
+      L.rr = 1;
+      L.cl = 2;
+      L.smem = s1;
+    }
   }
   return L;
 }
@@ -548,14 +617,33 @@ cudaError_t launch_rows(int dtype, const RowArgs& a, const RowLaunch& L, int gri
   if (e != cudaSuccess) return e;
   RowArgs ac = a;
   void* args[] = {(void*)&ac};
-  return cudaLaunchKernel(f, dim3(grid), dim3(L.threads), args, L.smem, st);
+  if (L.cl == 1) return cudaLaunchKernel(f, dim3(grid), dim3(L.threads), args, L.smem, st);
+  cudaLaunchAttribute at[1];
+  const cudaLaunchConfig_t cfg = rows_config(L, grid, st, at);
+  return cudaLaunchKernelExC(&cfg, f, args);
 }
 
+// CTAs of one launch that run at the same time per SM (cluster launches:
+// per SM on average, from the number of clusters that fit the device).
 int rows_max_ctas_per_sm(int dtype, const RowLaunch& L) {
   const void* f = rows_fn(dtype, L);
   if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem) != cudaSuccess) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, L.threads, L.smem) != cudaSuccess) return 0;
+  if (L.cl == 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, L.threads, L.smem) != cudaSuccess) return 0;
+    return n;
+  }
+  return 1;
+}
+
+// Clusters of a cluster launch that can be resident at once (0 if none).
+int rows_max_clusters(int dtype, const RowLaunch& L) {
+  const void* f = rows_fn(dtype, L);
+  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem) != cudaSuccess) return 0;
+  cudaLaunchAttribute at[1];
+  const cudaLaunchConfig_t cfg = rows_config(L, 2 * L.cl, nullptr, at);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, f, &cfg) != cudaSuccess) return 0;
   return n;
 }
 

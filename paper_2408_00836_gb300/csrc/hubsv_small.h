@@ -119,14 +119,17 @@ size_t rows_smem_bytes(int dtype, int nv, int row_len, int n_slots, int n_gates,
 // rows where two fit one CTA, else 1), threads per CTA (256 where three
 // such CTAs fit an SM, 1024 for a c64 CTA alone on its SM, else 512) and
 // shared memory.
+// Where a row of psi and its row of lam do not fit one CTA, a cluster of
+// two CTAs (cl = 2) stages them, one row each, in 512-thread CTAs.
 struct RowLaunch {
-  int threads = 0, rr = 1;
-  size_t smem = 0;
+  int threads = 0, rr = 1, cl = 1;
+  size_t smem = 0;   // per CTA
 };
 RowLaunch rows_launch(int dtype, int nv, int row_len, int n_rows, int n_slots, int n_gates, int n_hterms,
-                      int n_ops);
+                      int n_ops, bool force_cluster = false);
 cudaError_t launch_rows(int dtype, const RowArgs& a, const RowLaunch& L, int grid, cudaStream_t st);
 int rows_max_ctas_per_sm(int dtype, const RowLaunch& L);
+int rows_max_clusters(int dtype, const RowLaunch& L);
 // out[b][c][r] = in[b][r][c] for a [batch][n_r][n_c] matrix of amplitudes.
 cudaError_t launch_transpose(int dtype, const void* in, void* out, int64_t batch, int n_r, int n_c,
                              cudaStream_t st);

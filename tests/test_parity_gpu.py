@@ -23,8 +23,10 @@ DT = {H.C64: torch.complex64, H.C128: torch.complex128}
 def _run(prob, theta, dtype, batch=1, grad=True, prep_kind=H.PREP_SLATER, neel_up=None,
          keep_state=False, engine="auto"):
     """engine: "auto" (the library's choice: on chip where the sector fits
-    one CTA), "rows" (the row engine) or "sweeps" (dense HBM sweeps)."""
-    sweeps, rows = engine == "sweeps", engine == "rows"
+    one CTA), "rows" (the row engine), "rows_cluster" (the row engine with
+    each psi row and lam row on a two-CTA cluster) or "sweeps" (dense HBM
+    sweeps)."""
+    sweeps, rows, cluster = engine == "sweeps", engine.startswith("rows"), engine == "rows_cluster"
     dev = "cuda"
     a = prob.ans
     a.state_prepare(prep_kind, prob.perturb, neel_up, None, dtype, batch)
@@ -34,7 +36,7 @@ def _run(prob, theta, dtype, batch=1, grad=True, prep_kind=H.PREP_SLATER, neel_u
     if grad:
         lam = torch.empty_like(psi)
         g = torch.empty((batch, a.P), dtype=torch.float64, device=dev)
-        a.energy_grad(th, psi, lam, E, g, dtype=dtype, batch=batch, sweeps=sweeps, rows=rows)
+        a.energy_grad(th, psi, lam, E, g, dtype=dtype, batch=batch, sweeps=sweeps, rows=rows, row_cluster=cluster)
         H.sync()
         return E.cpu().numpy(), g.cpu().numpy(), None
     a.energy(th, psi, E, dtype=dtype, batch=batch, keep_state=keep_state, sweeps=sweeps, rows=rows)
@@ -87,7 +89,7 @@ def _disordered_2x3(modes="blocked", V=0.4):
     return t, U, Vm
 
 
-@pytest.mark.parametrize("engine", ["auto", "rows", "sweeps"])
+@pytest.mark.parametrize("engine", ["auto", "rows", "rows_cluster", "sweeps"])
 @pytest.mark.parametrize("modes", ["blocked", "interleaved"])
 @pytest.mark.parametrize("dtype", [H.C128, H.C64])
 def test_disordered_extended_2x3_all_group_kinds(modes, dtype, engine):
@@ -179,7 +181,7 @@ def test_neel_start(dtype, engine):
     assert np.max(np.abs(gg[0] - go)) < TOL[dtype] * max(1.0, np.max(np.abs(go)))
 
 
-@pytest.mark.parametrize("engine", ["auto", "rows", "sweeps"])
+@pytest.mark.parametrize("engine", ["auto", "rows", "rows_cluster", "sweeps"])
 @pytest.mark.parametrize("dtype", [H.C64, H.C128])
 def test_grid2x4_batched_instances(dtype, engine):
     """Workload 2 shape (16 qubits, snake order, perturbed orbitals, four U
@@ -232,14 +234,15 @@ def _problem_24q(number):
     return _PROB24[number]
 
 
-@pytest.mark.parametrize("engine", ["auto", "sweeps"])
+@pytest.mark.parametrize("engine", ["auto", "rows_cluster", "sweeps"])
 @pytest.mark.parametrize("number", [3, 6])
 @pytest.mark.parametrize("dtype", [H.C64, H.C128])
 def test_grid3x4_24_qubits_against_oracle(dtype, number, engine):
     """Workload 3 (24 qubits, inhomogeneous t and U, V = 0.5 phases) and
     workload 6 (24 qubits, uniform t = 1, U = 8), on the library's choice
-    (the row engine) and on the dense 2^24 sweeps, energy and gradient
-    against the oracle at the stated bounds."""
+    (the row engine), on the row engine with two-CTA clusters and on the
+    dense 2^24 sweeps, energy and gradient against the oracle at the stated
+    bounds."""
     prob, theta, (Eo, go) = _problem_24q(number)
     E, g, _ = _run(prob, theta, dtype, engine=engine)
     log_errors(f"workload{number}_24q", dtype, engine, energy=energy_err(E[0], Eo), grad=grad_err(g[0], go))
