@@ -497,14 +497,21 @@ def run_gpu(args, rank, world, dist):
         torch.cuda.empty_cache()
     if args.c128 and dtype == H.C64 and rank == 0:
         out["c128"] = run_c128(args, w, a, H, torch, dev, theta, ms_step)
-        # the c64 / c128 ratio on one engine: dense sweeps at this size (the
-        # row engine cannot hold a c128 row with lam here), rows at 28 qubits
+        # the c64 / c128 ratio on one engine: the headline engine, and the
+        # dense sweeps beside it; rows at 28 qubits
         c128_eng = out["c128"].get("engine")
         prec = {}
-        if c128_eng == "sweeps" and "dense_sweeps" in out:
-            prec["sweeps_" + str(w.n_qubits) + "q"] = {
-                "c64_evals_per_s": out["dense_sweeps"]["value"], "c128_evals_per_s": out["c128"]["value"],
-                "c64_speedup_same_engine": round(out["dense_sweeps"]["value"] / out["c128"]["value"], 3)}
+        key = "_" + str(w.n_qubits) + "q"
+        if c128_eng == "rows" and rows_engine and "value" in out["c128"]:
+            prec["rows" + key] = {"c64_evals_per_s": round(value / world, 4), "c128_evals_per_s": out["c128"]["value"],
+                                  "c64_speedup_same_engine": round(value / world / out["c128"]["value"], 3)}
+        if "dense_sweeps" in out:
+            c128s = out["c128"] if c128_eng == "sweeps" else run_c128(args, w, a, H, torch, dev, theta, ms_step,
+                                                                       sweeps=True)
+            if "value" in c128s:
+                prec["sweeps" + key] = {
+                    "c64_evals_per_s": out["dense_sweeps"]["value"], "c128_evals_per_s": c128s["value"],
+                    "c64_speedup_same_engine": round(out["dense_sweeps"]["value"] / c128s["value"], 3)}
         if args.workload == 5:
             prec["rows_28q"] = run_precision_28q(H, torch, dev)
         out["precision"] = prec
@@ -610,27 +617,29 @@ def run_np_leg(H, torch, dev, layers=12, steps=1):
             "hbm_tbs": round(by / (ms / 1e3) / 1e12, 3), "energy": float(E[0].item())}
 
 
-def run_c128(args, w, a, H, torch, dev, theta, ms_c64):
-    """The same evaluation in complex128 (psi + lam = 2 x 68.7 GB at 32
-    qubits), fewer steps: it is FP64-bound on this part."""
+def run_c128(args, w, a, H, torch, dev, theta, ms_c64, sweeps=None):
+    """The same evaluation in complex128 on the library's engine (or the
+    dense sweeps: psi + lam = 2 x 68.7 GB at 32 qubits), fewer steps: it is
+    FP64-bound on this part."""
+    sweeps = args.sweeps if sweeps is None else sweeps
     free, _ = torch.cuda.mem_get_info(dev)
-    need = 2 * a.amp_bytes(H.C128) * w.batch
+    need = 2 * a.workspace(1, H.C128, w.batch, sweeps=sweeps)[0]
     if need > free * 0.95:
         return {"skipped": f"needs {need / 1e9:.1f} GB, {free / 1e9:.1f} GB free"}
     a.state_prepare(H.PREP_SLATER, w.orbital_perturbation(), None, None, H.C128, w.batch)
-    _, eng = a.workspace(1, H.C128, w.batch, sweeps=args.sweeps)
+    _, eng = a.workspace(1, H.C128, w.batch, sweeps=sweeps)
     eng_name = ["on-chip", "rows", "sweeps"][eng]
-    psi = H.workspace_tensor(a, 1, H.C128, w.batch, device=dev, sweeps=args.sweeps)
-    lam = H.workspace_tensor(a, 1, H.C128, w.batch, device=dev, sweeps=args.sweeps)
+    psi = H.workspace_tensor(a, 1, H.C128, w.batch, device=dev, sweeps=sweeps)
+    lam = H.workspace_tensor(a, 1, H.C128, w.batch, device=dev, sweeps=sweeps)
     E = torch.empty(w.batch, dtype=torch.float64, device=dev)
     g = torch.empty((w.batch, a.P), dtype=torch.float64, device=dev)
-    a.energy_grad(theta, psi, lam, E, g, dtype=H.C128, batch=w.batch, sweeps=args.sweeps)   # warm-up
+    a.energy_grad(theta, psi, lam, E, g, dtype=H.C128, batch=w.batch, sweeps=sweeps)   # warm-up
     torch.cuda.synchronize()
     steps = max(1, args.c128_steps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(steps):
-        a.energy_grad(theta, psi, lam, E, g, dtype=H.C128, batch=w.batch, sweeps=args.sweeps)
+        a.energy_grad(theta, psi, lam, E, g, dtype=H.C128, batch=w.batch, sweeps=sweeps)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
