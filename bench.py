@@ -343,7 +343,8 @@ def run_gpu(args, rank, world, dist):
     stream = torch.cuda.current_stream()
 
     def call():
-        a.energy_grad(theta, psi, lam, E, g, dtype=dtype, batch=batch, sweeps=args.sweeps, rows=args.rows)
+        a.energy_grad(theta, psi, lam, E, g, dtype=dtype, batch=batch, sweeps=args.sweeps, rows=args.rows,
+                      row_cluster=args.row_cluster)
 
     step = call
     graph = None
@@ -481,6 +482,8 @@ def run_gpu(args, rank, world, dist):
            "clocks": ck}
     if args.graph:
         out["config"]["cuda_graph"] = "each step is one replay of a captured graph"
+    if args.row_cluster:
+        out["config"]["row_cluster"] = "psi and lam rows on two-CTA clusters"
     if tune:
         out["autotune"] = tune
     elif args.tile:
@@ -670,6 +673,8 @@ def main():
     ap.add_argument("--runs", type=int, default=0, help="log2 contiguous amplitudes per HBM run (0 = default)")
     ap.add_argument("--graph", action="store_true", help="time replays of the step captured in a CUDA graph")
     ap.add_argument("--rows", action="store_true", help="skip the on-chip engine (row engine where it applies)")
+    ap.add_argument("--row-cluster", action="store_true",
+                    help="row engine: rows of psi and lam on two-CTA clusters (HUB_FLAG_ROW_CLUSTER)")
     ap.add_argument("--sweeps", action="store_true",
                     help="run the HBM sweep engine even where the sector fits on chip")
     args = ap.parse_args()
