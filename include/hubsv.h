@@ -332,6 +332,16 @@ HUB_API hub_status ans_set_tile(ans_t ans, int32_t dtype, int32_t log2_tile);
  * sweeps) at the cost of less contiguous HBM traffic.                       */
 HUB_API hub_status ans_set_runs(ans_t ans, int32_t dtype, int32_t log2_run);
 
+/* Threads per CTA override of a sector engine (used by the autotuner).
+ * engine HUB_ENGINE_ONCHIP: 256 or 512 (0 = automatic: 512); engine
+ * HUB_ENGINE_ROWS: 256, 512 or 1024 (0 = automatic: 256 where three CTAs fit
+ * an SM, 1024 for a complex64 CTA alone on its SM, else 512; a row sweep
+ * that the override cannot stage, or that runs on a two-CTA cluster, keeps
+ * the automatic choice).  HUB_EINVAL for other values.                     */
+#define HUB_ENGINE_ONCHIP 0
+#define HUB_ENGINE_ROWS 1
+HUB_API hub_status ans_set_threads(ans_t ans, int32_t dtype, int32_t engine, int32_t threads);
+
 /* Wait for the stream and report any asynchronous device error.            */
 HUB_API hub_status hub_sync(hub_stream_t stream);
 

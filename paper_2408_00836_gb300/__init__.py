@@ -33,6 +33,7 @@ FLAG_KEEP_STATE = 2
 FLAG_SWEEPS = 4
 FLAG_ROWS = 8
 FLAG_ROW_CLUSTER = 16
+ENGINE_ONCHIP, ENGINE_ROWS = 0, 1
 CLASS_IDS = {"h1": 0, "h2": 1, "v1": 2, "v2": 3, "even": 0, "odd": 1}
 
 
@@ -361,6 +362,11 @@ class Ansatz:
     def set_runs(self, dtype: int, log2_run: int):
         """log2 of the contiguous amplitudes per HBM run (0 = automatic)."""
         check(lib().ans_set_runs(self._h, dtype, log2_run))
+
+    def set_threads(self, dtype: int, engine: int, threads: int):
+        """Threads per CTA of a sector engine (ENGINE_ONCHIP: 256 or 512;
+        ENGINE_ROWS: 256, 512 or 1024; 0 = automatic)."""
+        check(lib().ans_set_threads(self._h, dtype, engine, threads))
 
 
 def sync(stream=None):

@@ -22,7 +22,7 @@ EXPORTS = [
     "ans_destroy", "ans_num_params", "ans_num_qubits", "state_prepare", "energy",
     "energy_grad", "hub_apply_h", "ans_plan_stats", "ans_set_tile", "ans_set_runs", "hub_sync",
     "hub_last_error", "ans_plan_describe", "ans_profile", "ans_profile_read", "energy_noalloc",
-    "overlap_grad", "spin_correlation", "ans_workspace_bytes",
+    "overlap_grad", "spin_correlation", "ans_workspace_bytes", "ans_set_threads",
 ]
 
 
@@ -81,6 +81,7 @@ def lib():
                                      POINTER(c_int32)]),
         "ans_plan_stats": (st, [c_void_p, c_int32, c_int32, c_uint32, POINTER(c_int32), POINTER(c_double)]),
         "ans_set_tile": (st, [c_void_p, c_int32, c_int32]),
+        "ans_set_threads": (st, [c_void_p, c_int32, c_int32, c_int32]),
         "ans_set_runs": (st, [c_void_p, c_int32, c_int32]),
         "ans_plan_describe": (st, [c_void_p, c_int32, c_int32, c_uint32, POINTER(c_int64), c_int32,
                                    POINTER(c_int32)]),

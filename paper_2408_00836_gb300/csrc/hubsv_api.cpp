@@ -617,6 +617,23 @@ extern "C" hub_status ans_set_tile(ans_t a, int32_t dtype, int32_t log2_tile) {
   return HUB_OK;
 }
 
+extern "C" hub_status ans_set_threads(ans_t a, int32_t dtype, int32_t engine, int32_t threads) {
+  if (!a || (dtype != HUB_C64 && dtype != HUB_C128)) return fail(HUB_EINVAL, "ans_set_threads: bad arguments");
+  if (engine == HUB_ENGINE_ONCHIP) {
+    if (threads != 0 && threads != 256 && threads != 512)
+      return fail(HUB_EINVAL, "ans_set_threads: on-chip threads must be 0, 256 or 512");
+    a->small_threads[dtype] = threads;
+    return HUB_OK;
+  }
+  if (engine == HUB_ENGINE_ROWS) {
+    if (threads != 0 && threads != 256 && threads != 512 && threads != 1024)
+      return fail(HUB_EINVAL, "ans_set_threads: row threads must be 0, 256, 512 or 1024");
+    a->row_threads[dtype] = threads;
+    return HUB_OK;
+  }
+  return fail(HUB_EINVAL, "ans_set_threads: engine must be HUB_ENGINE_ONCHIP or HUB_ENGINE_ROWS");
+}
+
 extern "C" hub_status ans_set_runs(ans_t a, int32_t dtype, int32_t log2_run) {
   if (!a || (dtype != HUB_C64 && dtype != HUB_C128)) return fail(HUB_EINVAL, "ans_set_runs: bad arguments");
   if (log2_run != 0 && (log2_run < 1 || log2_run > 5))
@@ -800,7 +817,7 @@ SmallPlan* small_plan_for(hub_ansatz* a, int which, int dtype, uint32_t flags, s
   const uint64_t C = (uint64_t)sp->cup * (uint64_t)sp->cdn;
   if (C * (uint64_t)std::max(sp->cup, sp->cdn) >= (1ull << 32)) return nullptr;
   smem = small_smem_bytes(dtype, sp->cup, sp->cdn, (int)sp->pairs.size(), a->P + 2, a->n_gates,
-                          a->n_hcol);
+                          a->n_hcol, a->small_threads[dtype] ? a->small_threads[dtype] : kSmallThreadsDefault);
   if ((int)smem > sweep_max_smem_optin()) return nullptr;
   return sp;
 }
@@ -870,7 +887,8 @@ hub_status run_small(hub_ansatz* a, SmallPlan* sp, size_t smem, int dtype, const
   ka.prep.sd32 = (const float*)a->d_sd32.p;
   const int sms = device_sm_count();
   if (sms <= 0) return fail(HUB_ECUDA, "no CUDA device");
-  const int per_sm = std::max(1, small_max_ctas_per_sm(dtype, smem));
+  const int nt = a->small_threads[dtype] ? a->small_threads[dtype] : kSmallThreadsDefault;
+  const int per_sm = std::max(1, small_max_ctas_per_sm(dtype, nt, smem));
   const int64_t grid = std::min<int64_t>(batch, (int64_t)sms * per_sm);
   hub_ansatz::ProfRec rec{};
   if (a->prof) {
@@ -878,7 +896,7 @@ hub_status run_small(hub_ansatz* a, SmallPlan* sp, size_t smem, int dtype, const
     HUB_CUDA(cudaEventCreate(&rec.e1), "cudaEventCreate");
     HUB_CUDA(cudaEventRecord(rec.e0, st), "cudaEventRecord");
   }
-  HUB_CUDA(launch_small(dtype, ka, (int)grid, smem, st), "on-chip kernel launch");
+  HUB_CUDA(launch_small(dtype, ka, nt, (int)grid, smem, st), "on-chip kernel launch");
   if (a->prof) {
     HUB_CUDA(cudaEventRecord(rec.e1, st), "cudaEventRecord");
     rec.nv = 0;   // on-chip: shared-memory amplitude traffic, no vector in HBM
@@ -916,7 +934,8 @@ RowPlan* row_plan_for(hub_ansatz* a, int which, int dtype, uint32_t flags, Small
     const int nr = g.orient == 0 ? sp->cdn : sp->cup;
     const int no = g.op_end - g.op_begin;
     const RowLaunch rl =
-        rows_launch(dtype, nv, len, nr, a->P + 2, a->n_gates, a->n_hcol, no, (flags & HUB_FLAG_ROW_CLUSTER) != 0);
+        rows_launch(dtype, nv, len, nr, a->P + 2, a->n_gates, a->n_hcol, no, (flags & HUB_FLAG_ROW_CLUSTER) != 0,
+                    a->row_threads[dtype]);
     if ((int)rl.smem > optin || rl.smem == 0) return nullptr;
   }
   sp_out = sp;
@@ -1034,7 +1053,8 @@ hub_status run_rows(hub_ansatz* a, SmallPlan* sp, RowPlan* rp, int dtype, const 
     const int nv = has_lam ? 2 : 1;
     const int no = g.op_end - g.op_begin;
     const RowLaunch rl =
-        rows_launch(dtype, nv, ka.row_len, ka.n_rows, n_slots, a->n_gates, ka.n_hterms, no, force_cluster);
+        rows_launch(dtype, nv, ka.row_len, ka.n_rows, n_slots, a->n_gates, ka.n_hterms, no, force_cluster,
+                    a->row_threads[dtype]);
     const int64_t groups = batch * (int64_t)((ka.n_rows + rl.rr - 1) / rl.rr);
     int64_t grid;
     if (rl.cl == 1) {

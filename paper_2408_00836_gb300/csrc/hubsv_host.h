@@ -112,6 +112,8 @@ struct hub_model {
 struct hub_ansatz {
   std::vector<hub_model*> models;
   int n_inst = 0, L = 0, n = 0, P = 0, s = 0, layout = 0;
+  int small_threads[2] = {0, 0};         // ans_set_threads overrides per dtype (0 = automatic)
+  int row_threads[2] = {0, 0};
   uint64_t upmask = 0;
   std::vector<hubsv::SeqOp> fwd;         // forward factors in order
   std::vector<int> layer_begin;          // index in fwd of each layer's first factor
@@ -157,11 +159,13 @@ struct hub_ansatz {
 namespace hubsv {
 // Default tile and run bits (log2 of the amplitudes per tile, and of the
 // contiguous amplitudes a warp reads or writes as one piece), chosen by
-// timing the 32-qubit energy + gradient on GB300: c64 tiles of 2^12 (two
-// CTAs of 256 threads per SM) with 64-byte runs; c128 tiles of 2^10 (CTAs
-// of 128 threads) with 32-byte runs.  c128 is bound by FP64 arithmetic, so
-// it gains most from the plan that visits the fewest live amplitudes.
-inline int default_tile_bits(int dtype) { return dtype == HUB_C64 ? 12 : 10; }
+// timing energy + gradient on GB300: c64 tiles of 2^13 from 28 qubits (one
+// 512-thread CTA per SM: fewer sweeps; 32 qubits 1.00 vs 0.85 evals/s, 28
+// qubits 10.2 vs 8.9) and 2^12 below (two CTAs of 256 threads per SM; 24
+// qubits 250 vs 223), with 64-byte runs; c128 tiles of 2^10 (CTAs of 128
+// threads) with 32-byte runs.  c128 is bound by FP64 arithmetic, so it
+// gains most from the plan that visits the fewest live amplitudes.
+inline int default_tile_bits(int dtype, int n) { return dtype == HUB_C64 ? (n >= 28 ? 13 : 12) : 10; }
 inline int default_run_bits(int dtype) { return dtype == HUB_C64 ? 3 : 1; }
 uint64_t diag_support(const hub_ansatz* a, int di);
 hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*& out);

@@ -281,7 +281,7 @@ std::vector<SeqOp> op_sequence(const hub_ansatz* a, int which, uint32_t flags) {
 hub_status make_plan(hub_ansatz* a, int which, int dtype, uint32_t flags, Plan*& out) {
   const int n = a->n;
   if (n < kLaneBits + 1) return fail(HUB_EUNSUPPORTED, "need at least 6 qubits (3 sites)");
-  int k = a->tile_override[dtype] ? a->tile_override[dtype] : default_tile_bits(dtype);
+  int k = a->tile_override[dtype] ? a->tile_override[dtype] : default_tile_bits(dtype, n);
   // threads = 32 << (k - 5 - r) must stay <= 512 for every sweep
   k = std::min(k, kLaneBits + 4 + std::min(max_reg_bits(dtype, 1), max_reg_bits(dtype, 2)));
   k = std::min(k, n);

@@ -587,12 +587,12 @@ cudaLaunchConfig_t rows_config(const RowLaunch& L, int grid, cudaStream_t st, cu
 }  // namespace
 
 RowLaunch rows_launch(int dtype, int nv, int row_len, int n_rows, int n_slots, int n_gates, int n_hterms,
-                      int n_ops, bool force_cluster) {
+                      int n_ops, bool force_cluster, int threads) {
   RowLaunch L;
   for (int rr = (n_rows >= 2 && dtype == 0 && row_len < kRowPairLen) ? 2 : 1; rr >= 1 && !(force_cluster && nv == 2);
        --rr) {
     auto smem = [&](int nt) { return rows_smem_bytes(dtype, nv, row_len, n_slots, n_gates, n_hterms, nt, n_ops, rr); };
-    const int nt = pick_threads(dtype, smem);
+    const int nt = threads ? threads : pick_threads(dtype, smem);
     L.threads = nt;
     L.rr = rr;
     L.smem = smem(nt);

@@ -199,17 +199,14 @@ hub_status make_small_plan(hub_ansatz* a, int which, SmallPlan*& out) {
 
 uint32_t small_magic(int d) { return d <= 1 ? 0u : (uint32_t)((((uint64_t)1 << 32) + (uint64_t)d - 1) / (uint64_t)d); }
 
-namespace {
-constexpr int kSmallThreads = 512;
-constexpr int kSmallWarps = kSmallThreads / 32;
-}  // namespace
-
-size_t small_smem_bytes(int dtype, int cup, int cdn, int n_pairs, int n_slots, int n_gates, int n_hterms) {
+size_t small_smem_bytes(int dtype, int cup, int cdn, int n_pairs, int n_slots, int n_gates, int n_hterms,
+                        int threads) {
+  const int warps = threads / 32;
   const size_t amp = dtype == 0 ? 8 : 16;
   const size_t c = (size_t)(cup | 1) * (size_t)cdn;       // rows of odd pitch
   size_t s = 2 * c * amp;                                   // psi, lam
   s += 16 * (size_t)n_gates;                                // (cos, sin) of the element (see GC)
-  s += 8 * (size_t)kSmallWarps * (size_t)n_slots;          // accumulators, one row per warp
+  s += 8 * (size_t)warps * (size_t)n_slots;                // accumulators, one row per warp
   s += amp / 2 * (size_t)n_hterms;                          // -t of the element's instance
   s += 4 * ((size_t)cup + (size_t)cdn + (size_t)n_pairs);   // patterns, pair lists
   return (s + 15) & ~(size_t)15;
@@ -231,8 +228,9 @@ __device__ __forceinline__ uint32_t div_magic(uint32_t n, uint32_t m) { return m
 // warp touches a row (down hops) or a column (up hops) of the element
 // matrix; the odd row pitch ld keeps the column accesses free of bank
 // conflicts.
-template <typename R>
-__global__ void __launch_bounds__(kSmallThreads, sizeof(R) == 4 ? 2 : 1) small_kernel(const SmallArgs a) {
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1) * (512 / NT)) small_kernel(const SmallArgs a) {
+  constexpr int kSmallWarps = NT / 32;
   using T2 = typename CT<R>::T2;
   constexpr int DT = CT<R>::DT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -395,20 +393,27 @@ __global__ void __launch_bounds__(kSmallThreads, sizeof(R) == 4 ? 2 : 1) small_k
 
 }  // namespace
 
-cudaError_t launch_small(int dtype, const SmallArgs& a, int grid, size_t smem, cudaStream_t st) {
-  const void* f = dtype == 0 ? (const void*)small_kernel<float> : (const void*)small_kernel<double>;
+namespace {
+const void* small_fn(int dtype, int threads) {
+  if (threads == 256) return dtype == 0 ? (const void*)small_kernel<float, 256> : (const void*)small_kernel<double, 256>;
+  return dtype == 0 ? (const void*)small_kernel<float, 512> : (const void*)small_kernel<double, 512>;
+}
+}  // namespace
+
+cudaError_t launch_small(int dtype, const SmallArgs& a, int threads, int grid, size_t smem, cudaStream_t st) {
+  const void* f = small_fn(dtype, threads);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   SmallArgs ac = a;
   void* args[] = {(void*)&ac};
-  return cudaLaunchKernel(f, dim3(grid), dim3(kSmallThreads), args, smem, st);
+  return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, st);
 }
 
-int small_max_ctas_per_sm(int dtype, size_t smem) {
-  const void* f = dtype == 0 ? (const void*)small_kernel<float> : (const void*)small_kernel<double>;
+int small_max_ctas_per_sm(int dtype, int threads, size_t smem) {
+  const void* f = small_fn(dtype, threads);
   if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kSmallThreads, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) != cudaSuccess) return 0;
   return n;
 }
 

@@ -54,12 +54,15 @@ struct SmallArgs {
 // Shared memory of one CTA: psi and lam (ld x C_dn each), the element's
 // Givens coefficients, the accumulators, the -t of its instance, and the
 // pattern and pair tables.
-size_t small_smem_bytes(int dtype, int cup, int cdn, int n_pairs, int n_slots, int n_gates, int n_hterms);
+size_t small_smem_bytes(int dtype, int cup, int cdn, int n_pairs, int n_slots, int n_gates, int n_hterms,
+                        int threads);
+// Threads per CTA of the on-chip kernel: 512, or 256 (ans_set_threads).
+constexpr int kSmallThreadsDefault = 512;
 // ceil(2^32 / d) for d > 1, 0 for d = 1: the multiplier of the kernel's
 // division n / d, exact for n * d < 2^32.
 uint32_t small_magic(int d);
-cudaError_t launch_small(int dtype, const SmallArgs& a, int grid, size_t smem, cudaStream_t st);
-int small_max_ctas_per_sm(int dtype, size_t smem);
+cudaError_t launch_small(int dtype, const SmallArgs& a, int threads, int grid, size_t smem, cudaStream_t st);
+int small_max_ctas_per_sm(int dtype, int threads, size_t smem);
 
 // ---------------------------------------------------------------------------
 // Row engine (hubsv_rows.cu): the sector amplitudes of each batch element
@@ -125,8 +128,9 @@ struct RowLaunch {
   int threads = 0, rr = 1, cl = 1;
   size_t smem = 0;   // per CTA
 };
+// threads: a CTA size to use instead of the automatic one (0: automatic).
 RowLaunch rows_launch(int dtype, int nv, int row_len, int n_rows, int n_slots, int n_gates, int n_hterms,
-                      int n_ops, bool force_cluster = false);
+                      int n_ops, bool force_cluster = false, int threads = 0);
 cudaError_t launch_rows(int dtype, const RowArgs& a, const RowLaunch& L, int grid, cudaStream_t st);
 int rows_max_ctas_per_sm(int dtype, const RowLaunch& L);
 int rows_max_clusters(int dtype, const RowLaunch& L);

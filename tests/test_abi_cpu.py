@@ -159,9 +159,9 @@ def test_schedules_are_valid(number, which):
     groups = H.hva_groups(bonds, cls, w.n_sites, w.layers, w.classes)
     a = H.Ansatz(m, groups, w.layers)
     seq = _sequence(groups, bonds, w.n_sites, which)
-    # default tiles and runs: c64 2^12 amplitudes, runs of 8 (c = 3);
-    # c128 2^10 amplitudes, runs of 2 (c = 1)
-    for dtype, k, c in [(H.C64, 12, 3), (H.C128, 10, 1)]:
+    # default tiles and runs: c64 2^12 amplitudes (2^13 from 28 qubits),
+    # runs of 8 (c = 3); c128 2^10 amplitudes, runs of 2 (c = 1)
+    for dtype, k, c in [(H.C64, 13 if w.n_qubits >= 28 else 12, 3), (H.C128, 10, 1)]:
         k = min(k, w.n_qubits)
         plan = a.plan_describe(which, dtype)
         _check_schedule(plan, seq, w.n_qubits, k, min(c, k), set(range(w.n_qubits)))
@@ -175,7 +175,7 @@ def test_schedules_are_valid(number, which):
     for runs in (2, 3, 5):
         a.set_runs(H.C64, runs)
         plan = a.plan_describe(which, H.C64)
-        k_eff = min(12, w.n_qubits)
+        k_eff = min(13 if w.n_qubits >= 28 else 12, w.n_qubits)
         _check_schedule(plan, seq, w.n_qubits, k_eff, min(runs, k_eff), set(range(w.n_qubits)))
 
 
@@ -295,3 +295,24 @@ def test_np_ansatz_4x4_12_layers_builds_and_plans():
     # EP: 4 Nx Ny + 2 (2 Nx Ny - 1) l
     e = H.Ansatz(m, H.ep_groups(32, 3), 1)
     assert e.P == 4 * 16 + 2 * 31 * 3
+
+
+def test_cta_size_override_arguments():
+    """ans_set_threads accepts 0 (automatic) and the instantiated CTA sizes
+    of each sector engine, and refuses anything else (no GPU needed)."""
+    bonds, cls, t = _model()
+    m = H.Model(6, bonds, t, np.full(6, 4.0), None, 3, 3)
+    a = H.Ansatz([m], H.hva_groups(bonds, cls, 6, 1, ["U", "h1"]), 1)
+    for dtype in (H.C64, H.C128):
+        for th in (0, 256, 512):
+            a.set_threads(dtype, H.ENGINE_ONCHIP, th)
+        for th in (0, 256, 512, 1024):
+            a.set_threads(dtype, H.ENGINE_ROWS, th)
+    for engine, th in [(H.ENGINE_ONCHIP, 1024), (H.ENGINE_ONCHIP, 128), (H.ENGINE_ROWS, 300), (H.ENGINE_ROWS, -1),
+                       (2, 256)]:
+        with pytest.raises(H.HubError) as e:
+            a.set_threads(H.C64, engine, th)
+        assert e.value.status == _lib.HUB_EINVAL
+    with pytest.raises(H.HubError) as e:
+        a.set_threads(7, H.ENGINE_ROWS, 256)
+    assert e.value.status == _lib.HUB_EINVAL

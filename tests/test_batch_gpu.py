@@ -102,7 +102,8 @@ def test_energy_fn_autograd_matches_oracle_gradient(dtype):
 
 def test_engine_autotuner_and_graph_captured_batch():
     """The engine autotuner on the 4096-state batch times the library's
-    choice, the row engine and the dense sweeps, and leaves a valid choice;
+    choice, the on-chip and row engines at each CTA size and the dense
+    sweeps, and leaves a valid choice;
     the whole batched evaluation captured in a CUDA graph and replayed
     gives the direct call's results."""
     from paper_2408_00836_gb300.autotune import autotune_engine
@@ -113,10 +114,12 @@ def test_engine_autotuner_and_graph_captured_batch():
     a.state_prepare(H.PREP_SLATER, prob.perturb, None, None, H.C64, batch)
     best, times = autotune_engine(a, H.C64, batch=batch, which=1, theta=w.theta(), tiles=(12,), reps=1,
                                   warmup=1)
-    assert {"auto", "rows", "sweeps_tile12"} <= set(times)
+    assert {"auto", "onchip_t256", "onchip_t512", "rows_t256", "rows_t512", "sweeps_tile12"} <= set(times)
     assert best["name"] == min(times, key=times.get)
     assert best["engine"] in ("on-chip", "rows", "sweeps")
     a.set_tile(H.C64, 0)
+    a.set_threads(H.C64, H.ENGINE_ONCHIP, 0)
+    a.set_threads(H.C64, H.ENGINE_ROWS, 0)
     fn = EnergyGradGraph(a, dtype=H.C64, batch=batch, use_graph=True, sweeps=best["sweeps"], rows=best["rows"])
     direct = EnergyGradGraph(a, dtype=H.C64, batch=batch, use_graph=False, sweeps=best["sweeps"],
                              rows=best["rows"])

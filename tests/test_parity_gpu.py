@@ -204,6 +204,28 @@ def test_grid2x4_batched_instances(dtype, engine):
     assert np.max(np.abs(E2 - E)) < TOL[dtype] * max(1.0, np.max(np.abs(E)))
 
 
+@pytest.mark.parametrize("engine,threads", [("auto", 256), ("rows", 256), ("rows", 512), ("rows", 1024)])
+@pytest.mark.parametrize("dtype", [H.C64, H.C128])
+def test_cta_size_overrides(dtype, engine, threads):
+    """ans_set_threads: the on-chip kernel at 256 threads and the row kernel
+    at every CTA size, on the workload 2 shape (8 states, four instances),
+    against the oracle."""
+    w = W.workload(2, batch_sets=2)
+    bonds, _ = H.square_lattice(2, 4, "snake")
+    inst = [(t, U, None) for (t, U, V) in (w.coefficients(bonds, r) for r in range(4))]
+    prob = Problem(2, 4, order="snake", layers=4, classes=w.classes, perturb=w.orbital_perturbation(),
+                   instances=inst)
+    prob.ans.set_threads(dtype, H.ENGINE_ONCHIP if engine == "auto" else H.ENGINE_ROWS, threads)
+    theta = w.theta()
+    E, g, _ = _run(prob, theta, dtype, batch=w.batch, engine=engine)
+    for b in range(w.batch):
+        Eo, go = prob.oracle_energy_grad(theta[b], r=b % 4)
+        log_errors(f"cta_{engine}_{threads}[{b}]", dtype, engine, energy=energy_err(E[b], Eo),
+                   grad=grad_err(g[b], go))
+        assert abs(E[b] - Eo) < TOL[dtype] * max(1.0, abs(Eo)), b
+        assert grad_err(g[b], go) < TOL[dtype], (b, grad_err(g[b], go))
+
+
 def test_apply_h_elementwise():
     t, U, Vm = _disordered_2x3()
     prob = Problem(2, 3, t=t, U=U, V=Vm, layers=1, classes=("h1",))
