@@ -159,3 +159,32 @@ def test_32q_c64_energy_gradient_against_c128_and_fd():
     # central difference error ~ h^2 |E'''| / 6 plus c128 rounding / h; c64 gradient relative 1e-6
     assert abs(float(g64 @ d) - fd) < 1e-5 * max(1.0, np.linalg.norm(g64))
     assert abs(float(g64c @ d) - fd) < 1e-5 * max(1.0, np.linalg.norm(g64c))
+
+
+def test_32q_c128_gradient_on_row_clusters_against_dense_sweeps():
+    """Workload 5 in complex128: the row engine stages each psi row and its
+    lam row (2 x 206 KB) on a two-CTA cluster; its energy and gradient agree
+    with the dense 2^32 sweeps' at the complex128 bound."""
+    w, a, om = _setup(5)
+    theta = w.theta()[0]
+    assert a.workspace(1, H.C128, 1)[1] == 1          # the row engine takes the call
+    a.state_prepare(H.PREP_SLATER, w.orbital_perturbation(), None, None, H.C128, 1)
+    th = torch.tensor(theta[None, :], device="cuda")
+    E = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty((1, a.P), dtype=torch.float64, device="cuda")
+    psi = H.workspace_tensor(a, 1, H.C128, 1)
+    lam = H.workspace_tensor(a, 1, H.C128, 1)
+    a.energy_grad(th, psi, lam, E, g, dtype=H.C128, batch=1)
+    H.sync()
+    e_rows, g_rows = float(E[0]), g.cpu().numpy()[0]
+    del psi, lam
+    torch.cuda.empty_cache()
+    psi = torch.empty((1, 1 << w.n_qubits), dtype=torch.complex128, device="cuda")
+    lam = torch.empty_like(psi)
+    a.energy_grad(th, psi, lam, E, g, dtype=H.C128, batch=1, sweeps=True)
+    H.sync()
+    e_sw, g_sw = float(E[0]), g.cpu().numpy()[0]
+    del psi, lam
+    torch.cuda.empty_cache()
+    assert abs(e_rows - e_sw) < TOL[H.C128] * max(1.0, abs(e_sw))
+    assert np.max(np.abs(g_rows - g_sw)) < TOL[H.C128] * max(1.0, np.max(np.abs(g_sw)))
