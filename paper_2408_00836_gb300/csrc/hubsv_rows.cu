@@ -518,30 +518,46 @@ __global__ void __launch_bounds__(NT, CL == 2 ? 1 : (NT == kRowThreadsSmall ? 4 
   }
 }
 
-// out[b][c][r] = in[b][r][c], 32 x 32 tiles through shared memory (one
-// padding column keeps the column reads free of bank conflicts).
-template <typename T2>
+// out[b][c][r] = in[b][r][c], TS x TS tiles through shared memory (one
+// padding column keeps the column reads free of bank conflicts); 32 x 8
+// threads, each moving TS / 32 x TS / 8 elements, all loads issued before
+// the first shared-memory store.
+template <typename T2, int TS>
 __global__ void __launch_bounds__(256) transpose_kernel(const T2* __restrict__ in, T2* __restrict__ out,
                                                         int64_t batch, int n_r, int n_c) {
-  __shared__ T2 tile[32][33];
+  __shared__ T2 tile[TS][TS + 1];
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
-  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int c0 = blockIdx.x * TS, r0 = blockIdx.y * TS;
   const size_t mat = (size_t)n_r * (size_t)n_c;
   for (int64_t b = blockIdx.z; b < batch; b += gridDim.z) {
     const T2* src = in + (size_t)b * mat;
     T2* dst = out + (size_t)b * mat;
-    for (int j = ty; j < 32; j += 8) {
-      const int r = r0 + j, c = c0 + tx;
-      if (r < n_r && c < n_c) tile[j][tx] = src[(size_t)r * n_c + c];
-    }
+    T2 v[TS / 8][TS / 32];
+#pragma unroll
+    for (int j = 0; j < TS / 8; ++j)
+#pragma unroll
+      for (int i = 0; i < TS / 32; ++i) {
+        const int r = r0 + ty + 8 * j, c = c0 + tx + 32 * i;
+        if (r < n_r && c < n_c) v[j][i] = src[(size_t)r * n_c + c];
+      }
+#pragma unroll
+    for (int j = 0; j < TS / 8; ++j)
+#pragma unroll
+      for (int i = 0; i < TS / 32; ++i) tile[ty + 8 * j][tx + 32 * i] = v[j][i];
     __syncthreads();
-    for (int j = ty; j < 32; j += 8) {
-      const int c = c0 + j, r = r0 + tx;
-      if (r < n_r && c < n_c) dst[(size_t)c * n_r + r] = tile[tx][j];
-    }
+#pragma unroll
+    for (int j = 0; j < TS / 8; ++j)
+#pragma unroll
+      for (int i = 0; i < TS / 32; ++i) {
+        const int c = c0 + ty + 8 * j, r = r0 + tx + 32 * i;
+        if (r < n_r && c < n_c) dst[(size_t)c * n_r + r] = tile[tx + 32 * i][ty + 8 * j];
+      }
     __syncthreads();
   }
 }
+
+// complex64 tiles of 64 x 64 (33 KB of shared memory), complex128 32 x 32
+constexpr int kTransposeTile64 = 64;
 
 }  // namespace
 
@@ -650,12 +666,17 @@ int rows_max_clusters(int dtype, const RowLaunch& L) {
 cudaError_t launch_transpose(int dtype, const void* in, void* out, int64_t batch, int n_r, int n_c,
                              cudaStream_t st) {
   if (batch <= 0 || n_r <= 0 || n_c <= 0) return cudaSuccess;
-  const dim3 grid((unsigned)((n_c + 31) / 32), (unsigned)((n_r + 31) / 32),
+  const int ts = dtype == 0 ? kTransposeTile64 : 32;
+  const dim3 grid((unsigned)((n_c + ts - 1) / ts), (unsigned)((n_r + ts - 1) / ts),
                   (unsigned)std::min<int64_t>(batch, 1024));
-  if (dtype == 0)
-    transpose_kernel<float2><<<grid, dim3(32, 8), 0, st>>>((const float2*)in, (float2*)out, batch, n_r, n_c);
-  else
-    transpose_kernel<double2><<<grid, dim3(32, 8), 0, st>>>((const double2*)in, (double2*)out, batch, n_r, n_c);
+  if (dtype == 0) {
+    if (ts == 64)
+      transpose_kernel<float2, 64><<<grid, dim3(32, 8), 0, st>>>((const float2*)in, (float2*)out, batch, n_r, n_c);
+    else
+      transpose_kernel<float2, 32><<<grid, dim3(32, 8), 0, st>>>((const float2*)in, (float2*)out, batch, n_r, n_c);
+  } else {
+    transpose_kernel<double2, 32><<<grid, dim3(32, 8), 0, st>>>((const double2*)in, (double2*)out, batch, n_r, n_c);
+  }
   return cudaGetLastError();
 }
 
