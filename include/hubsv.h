@@ -207,7 +207,9 @@ HUB_API hub_status energy(ans_t ans, const double* theta, void* psi, double* E,
  * call runs (1) on chip, one CTA per batch element, when psi and lam of
  * that size fit one CTA's shared memory (not with HUB_FLAG_ROWS); else
  * (2) on the row engine, when a row of the C_dn x C_up sector matrix (with
- * lam where the call builds it) fits shared memory and 2 C <= 2^n: the
+ * lam where the call builds it) fits shared memory, or a row of psi and its
+ * row of lam fit the shared memory of a two-CTA cluster (one each; complex128
+ * at 32 qubits), and 2 C <= 2^n: the
  * sector matrices and their transposes then live in the first
  * 2 * batch * C amplitudes of each of psi and lam, and ckpt is unused;
  * else (3) as HBM sweeps over the dense psi (and lam, ckpt).  Results agree

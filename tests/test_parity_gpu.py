@@ -226,6 +226,30 @@ def test_cta_size_overrides(dtype, engine, threads):
         assert grad_err(g[b], go) < TOL[dtype], (b, grad_err(g[b], go))
 
 
+@pytest.mark.parametrize("engine", ["rows", "rows_cluster"])
+@pytest.mark.parametrize("dtype", [H.C64, H.C128])
+def test_odd_row_counts_chain1x7(dtype, engine):
+    """A 7-site chain with N = 3 + 2: 21 rows of 35 patterns and, after each
+    transpose, 35 rows of 21 -- odd row counts, so the row engine's last
+    two-row group (short complex64 rows are staged two per CTA) holds one
+    row; ragged per-CTA splits; a random start of every parameter."""
+    rng = np.random.default_rng(41)
+    bonds, _ = H.square_lattice(1, 7)
+    t = np.zeros((7, 7))
+    for (i, j) in bonds:
+        t[i, j] = t[j, i] = 1.0 + 0.3 * rng.standard_normal()
+    U = 4.0 + rng.uniform(-1, 1, 7)
+    prob = Problem(1, 7, t=t, U=U, V=None, n_up=3, n_dn=2, layers=3, classes=("U", "h1", "h2"))
+    theta = rng.uniform(-math.pi, math.pi, prob.P)
+    Eo, go = prob.oracle_energy_grad(theta)
+    E, g, _ = _run(prob, theta, dtype, engine=engine)
+    log_errors("chain1x7_odd_rows", dtype, engine, energy=energy_err(E[0], Eo), grad=grad_err(g[0], go))
+    assert abs(E[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
+    assert grad_err(g[0], go) < TOL[dtype], grad_err(g[0], go)
+    E2, _, _ = _run(prob, theta, dtype, grad=False, engine=engine)
+    assert abs(E2[0] - Eo) < TOL[dtype] * max(1.0, abs(Eo))
+
+
 def test_apply_h_elementwise():
     t, U, Vm = _disordered_2x3()
     prob = Problem(2, 3, t=t, U=U, V=Vm, layers=1, classes=("h1",))
