@@ -520,6 +520,8 @@ def run_gpu(args, rank, world, dist):
         out["precision"] = prec
     if args.np_leg and rank == 0 and args.workload == 5:
         out["np_ansatz"] = run_np_leg(H, torch, dev)
+    if args.f3_leg and rank == 0 and args.workload == 5:
+        out["overlap_and_correlations"] = run_f3_leg(H, torch, dev)
     return out
 
 
@@ -620,6 +622,59 @@ def run_np_leg(H, torch, dev, layers=12, steps=1):
             "hbm_tbs": round(by / (ms / 1e3) / 1e12, 3), "energy": float(E[0].item())}
 
 
+def run_f3_leg(H, torch, dev, steps=3):
+    """Overlap loss, fidelity and spin correlations (Eq. 5, Sec. 3) on the
+    grid2x7 workload (28 qubits, dense sweeps): the overlap loss with its
+    adjoint gradient against a reference state (the ansatz state at nearby
+    parameters), and C_ij of a state."""
+    import numpy as np
+    w, a = build_problem(4, H)
+    n = w.n_qubits
+    a.state_prepare(H.PREP_SLATER, w.orbital_perturbation(), None, None, H.C64, 1)
+    th_ref = np.asarray(w.theta(), dtype=np.float64).reshape(1, -1)
+    th = th_ref + 0.05 * np.random.default_rng(9).standard_normal(th_ref.shape)
+    th_ref, th = torch.tensor(th_ref, device=dev), torch.tensor(th, device=dev)
+    ref = torch.empty((1, 1 << n), dtype=torch.complex64, device=dev)
+    E = torch.empty(1, dtype=torch.float64, device=dev)
+    a.energy(th_ref, ref, E, dtype=H.C64, keep_state=True)
+    psi = torch.empty_like(ref)
+    lam = torch.empty_like(ref)
+    F = torch.empty(1, dtype=torch.float64, device=dev)
+    f = torch.empty(1, dtype=torch.float64, device=dev)
+    g = torch.empty((1, a.P), dtype=torch.float64, device=dev)
+    C = torch.empty((1, n // 2, n // 2), dtype=torch.float64, device=dev)
+    a.overlap_grad(th, ref, psi, lam, F, f, g, dtype=H.C64)   # warm-up (plans)
+    a.spin_correlation(ref, C, dtype=H.C64)
+    torch.cuda.synchronize()
+    H.profile(a, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        a.overlap_grad(th, ref, psi, lam, F, f, g, dtype=H.C64)
+    e1.record()
+    torch.cuda.synchronize()
+    recs = H.profile_read(a)
+    H.profile(a, False)
+    ms = e0.elapsed_time(e1) / steps
+    by = sum(r[2] for r in recs) / steps
+    e0.record()
+    for _ in range(steps):
+        a.spin_correlation(ref, C, dtype=H.C64)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_c = e0.elapsed_time(e1) / steps
+    out = {"workload": WORKLOAD_TEXT[4],
+           "engine": "sweeps",
+           "overlap_grad": {"evals_per_s": round(1e3 / ms, 3), "ms_per_step": round(ms, 3),
+                            "sweep_bytes_per_eval": by, "hbm_tbs": round(by / (ms / 1e3) / 1e12, 3),
+                            "F": float(F[0].item()), "f": float(f[0].item())},
+           "spin_correlation": {"ms_per_state": round(ms_c, 3),
+                                "hbm_tbs": round((1 << n) * 8 / (ms_c / 1e3) / 1e12, 3)}}
+    del ref, psi, lam
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_c128(args, w, a, H, torch, dev, theta, ms_c64, sweeps=None):
     """The same evaluation in complex128 on the library's engine (or the
     dense sweeps: psi + lam = 2 x 68.7 GB at 32 qubits), fewer steps: it is
@@ -673,6 +728,8 @@ def main():
     ap.add_argument("--runs", type=int, default=0, help="log2 contiguous amplitudes per HBM run (0 = default)")
     ap.add_argument("--graph", action="store_true", help="time replays of the step captured in a CUDA graph")
     ap.add_argument("--rows", action="store_true", help="skip the on-chip engine (row engine where it applies)")
+    ap.add_argument("--no-f3", dest="f3_leg", action="store_false",
+                    help="skip the 28-qubit overlap-loss and spin-correlation entry")
     ap.add_argument("--row-cluster", action="store_true",
                     help="row engine: rows of psi and lam on two-CTA clusters (HUB_FLAG_ROW_CLUSTER)")
     ap.add_argument("--sweeps", action="store_true",
