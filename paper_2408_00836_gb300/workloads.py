@@ -159,3 +159,26 @@ def workload(number: int, batch_sets: int | None = None) -> Workload:
 def random_theta(seed: int, batch: int, P: int, scale: float = math.pi) -> np.ndarray:
     """Extra seeded parameter sets for tests: U(-scale, scale) [batch, P]."""
     return np.random.default_rng(seed).uniform(-scale, scale, (batch, P))
+
+
+def disordered_grid(nx: int, ny: int, seed: int):
+    """Seeded couplings of an nx x ny grid for the NP-ansatz tests: t_ij =
+    1 + 0.1 N(0, 1) on every site pair (callers keep the bonds' entries),
+    U_i = 4 (1 + 0.1 N(0, 1)), and a diagonal orbital perturbation of
+    1e-3 x site index that splits degenerate levels of the Slater start.
+    Drawn for all pairs in index order, so the values do not depend on the
+    order in which a lattice lists its bonds."""
+    L = nx * ny
+    rng = np.random.default_rng(seed)
+    tt = 1.0 + 0.1 * rng.standard_normal((L, L))
+    U = 4.0 * (1.0 + 0.1 * rng.standard_normal(L))
+    return tt, U, np.diag(1e-3 * np.arange(L))
+
+
+def bond_matrix(tt: np.ndarray, bonds) -> np.ndarray:
+    """t_ij = tt[min(i,j), max(i,j)] on the listed bonds, 0 elsewhere."""
+    t = np.zeros_like(tt)
+    for (i, j) in bonds:
+        a, b = min(i, j), max(i, j)
+        t[i, j] = t[j, i] = tt[a, b]
+    return t

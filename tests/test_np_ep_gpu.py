@@ -92,3 +92,39 @@ def test_np_ep_energy_gradient_and_state(dtype, case):
     got = psi.cpu().numpy()[0]
     assert rel_err(got, full) < TOL[dtype]
     assert abs(float(E[0]) - Eo) < TOL[dtype] * max(1.0, abs(Eo))
+
+
+def _golden_np3x4():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "np3x4_24q.txt")
+    with open(path) as f:
+        row = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")][0]
+    return float(row[1]), np.array([float(x) for x in row[2:]])
+
+
+@pytest.mark.parametrize("dtype", [H.C64, H.C128])
+def test_np3x4_24_qubits_against_golden(dtype):
+    """The NP ansatz at 24 qubits (3x4, one layer, 116 parameters, spin
+    mixing: dense sweeps over all 4096 tiles) against the oracle's energy
+    and gradient stored by tests/golden/make_np3x4_golden.py from the same
+    seeded inputs."""
+    from paper_2408_00836_gb300 import workloads as W
+    Eo, go = _golden_np3x4()
+    tt, U, perturb = W.disordered_grid(3, 4, 71)
+    bonds, cls = H.square_lattice(3, 4)
+    model = H.Model(12, bonds, W.bond_matrix(tt, bonds), U, None, 6, 6)
+    ans = H.Ansatz(model, H.np_groups(bonds, cls, 12, 1), 1)
+    assert ans.P == len(go) == 116
+    theta = W.random_theta(72, 1, ans.P, 1.0)
+    ans.state_prepare(H.PREP_SLATER, perturb, None, None, dtype, 1)
+    th = torch.tensor(theta, device="cuda")
+    psi = torch.empty((1, 1 << 24), dtype=DT[dtype], device="cuda")
+    lam = torch.empty_like(psi)
+    E = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty((1, ans.P), dtype=torch.float64, device="cuda")
+    ans.energy_grad(th, psi, lam, E, g, dtype=dtype)
+    H.sync()
+    e, gg = float(E[0]), g.cpu().numpy()[0]
+    log_errors("np3x4_24q_golden", dtype, "sweeps", energy=energy_err(e, Eo), grad=grad_err(gg, go))
+    assert abs(e - Eo) < TOL[dtype] * max(1.0, abs(Eo))
+    assert grad_err(gg, go) < TOL[dtype], grad_err(gg, go)
