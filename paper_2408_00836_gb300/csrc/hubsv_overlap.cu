@@ -173,6 +173,129 @@ __global__ void __launch_bounds__(128) occ_corr_kernel(const typename OT<R>::T2*
   }
 }
 
+// The same M for n >= KW, one warp per run of 2^KW = 1024 contiguous
+// amplitudes: lane = index bits 0-4, register slot r = bits 5-9, so each
+// load instruction of the warp reads 32 consecutive amplitudes.  Per lane,
+// the sums over its 32 slots whose slot bits are set are unrolled (the bit
+// pattern of r is a constant), in the working precision.  Moments that involve only the
+// low 10 bits are kept per lane across all of the warp's runs and reduced
+// once; per run, the weight S and the ten low-bit moments m_j are reduced
+// over the warp and added, by the lanes in parallel, to M[j][a] and
+// M[a][b] for the run's set high bits a < b.
+constexpr int KW = 10;
+
+__device__ __forceinline__ double warp_allsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) occ_corr_warp_kernel(const typename OT<R>::T2* __restrict__ psi, int n,
+                                                            int64_t batch, double* __restrict__ M) {
+  __shared__ double sm[kMaxQubits * kMaxQubits];
+  const int lane = threadIdx.x & 31;
+  const uint64_t len = 1ull << n;
+  const uint64_t runs = len >> KW;
+  const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) sm[i] = 0.0;
+    __syncthreads();
+    const typename OT<R>::T2* p = psi + (uint64_t)b * len;
+    double s_acc = 0.0, ms_acc[5], qs_acc[10];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) ms_acc[k] = 0.0;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) qs_acc[k] = 0.0;
+    for (uint64_t run = wid; run < runs; run += nw) {
+      const typename OT<R>::T2* pr = p + (run << KW) + lane;
+      // a lane's 32 terms summed in the working precision (complex64: FP32,
+      // about 1e-7 relative for 32 terms), everything beyond in FP64
+      R sr = 0, msr[5] = {0, 0, 0, 0, 0}, qsr[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        const typename OT<R>::T2 u = pr[r * 32];
+        const R w = u.x * u.x + u.y * u.y;
+        sr += w;
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+          if ((r >> k) & 1) msr[k] += w;
+        int t = 0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+#pragma unroll
+          for (int k2 = k + 1; k2 < 5; ++k2, ++t)
+            if (((r >> k) & 1) && ((r >> k2) & 1)) qsr[t] += w;
+      }
+      const double s = (double)sr;
+      double ms[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) ms[k] = (double)msr[k];
+#pragma unroll
+      for (int k = 0; k < 10; ++k) qs_acc[k] += (double)qsr[k];
+      s_acc += s;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) ms_acc[k] += ms[k];
+      const uint32_t hm = (uint32_t)((run << KW) & 0xffffffffull);   // the run's set high bits
+      if (hm == 0) continue;
+      // the run's weight and its ten low-bit moments, on every lane
+      double m[KW];
+#pragma unroll
+      for (int j = 0; j < 5; ++j) m[j] = warp_allsum(((lane >> j) & 1) ? s : 0.0);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) m[5 + k] = warp_allsum(ms[k]);
+      const double S = warp_allsum(s);
+      if (S == 0.0) continue;
+      const int h = __popc(hm);
+      for (int u = lane; u < (KW + 1) * h; u += 32) {   // (j, a) += m_j; (a, a) += S
+        const int ia = u / (KW + 1), c = u - ia * (KW + 1);
+        const int a = (int)__fns(hm, 0, ia + 1);
+        double v = S;
+#pragma unroll
+        for (int j = 0; j < KW; ++j)
+          if (c == j) v = m[j];
+        atomicAdd(&sm[(c == KW ? a : c) * n + a], v);
+      }
+      for (int u = lane; u < h * h; u += 32) {   // (a, b) += S for set high bits a < b
+        const int ia = u / h, ib = u - ia * h;
+        if (ia < ib) atomicAdd(&sm[(int)__fns(hm, 0, ia + 1) * n + (int)__fns(hm, 0, ib + 1)], S);
+      }
+    }
+    // the low block, reduced once over the warp: bits 0-4 from the lanes,
+    // bits 5-9 from the slots
+    double lo[KW], q[KW * (KW - 1) / 2];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) lo[j] = warp_allsum(((lane >> j) & 1) ? s_acc : 0.0);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) lo[5 + k] = warp_allsum(ms_acc[k]);
+    int t = 0, tt = 0;
+#pragma unroll
+    for (int j = 0; j < KW; ++j)
+#pragma unroll
+      for (int j2 = j + 1; j2 < KW; ++j2, ++t) {
+        double v;
+        if (j2 < 5) v = ((lane >> j) & 1) && ((lane >> j2) & 1) ? s_acc : 0.0;   // lane, lane
+        else if (j < 5) v = ((lane >> j) & 1) ? ms_acc[j2 - 5] : 0.0;             // lane, slot
+        else v = qs_acc[tt++];                                                     // slot, slot
+        q[t] = warp_allsum(v);
+      }
+    if (lane == 0) {
+      int t2 = 0;
+#pragma unroll
+      for (int j = 0; j < KW; ++j) {
+        atomicAdd(&sm[j * n + j], lo[j]);
+#pragma unroll
+        for (int j2 = j + 1; j2 < KW; ++j2, ++t2) atomicAdd(&sm[j * n + j2], q[t2]);
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x)
+      if (sm[i] != 0.0) atomicAdd(&M[(uint64_t)b * n * n + i], sm[i]);
+    __syncthreads();
+  }
+}
+
 // C[b][i][j] = (1/4) (<(n_iu - n_id)(n_ju - n_jd)> - <n_iu - n_id><n_ju - n_jd>)
 // from the upper triangle of M.
 __global__ void spin_corr_kernel(const double* __restrict__ M, int n, const int32_t* __restrict__ up,
@@ -231,6 +354,16 @@ cudaError_t launch_overlap_finalize(const double* acc, int n_slots, int P, const
 }
 
 cudaError_t launch_occ_corr(int dtype, const void* psi, int n, int64_t batch, double* M, cudaStream_t st) {
+  if (n >= KW) {   // one warp per run of 2^KW amplitudes
+    const uint64_t runs = 1ull << (n - KW);
+    const uint64_t bx = std::min<uint64_t>((runs + 7) / 8, 4 * 152);
+    const dim3 g((unsigned)bx, (unsigned)std::min<int64_t>(batch, 65535));
+    if (dtype == 0)
+      occ_corr_warp_kernel<float><<<g, 256, 0, st>>>((const float2*)psi, n, batch, M);
+    else
+      occ_corr_warp_kernel<double><<<g, 256, 0, st>>>((const double2*)psi, n, batch, M);
+    return cudaGetLastError();
+  }
   const int kr = n < KR ? n : KR;
   const uint64_t runs = 1ull << (n - kr);
   const uint64_t bx = std::min<uint64_t>((runs + 127) / 128, 2 * 152);

@@ -29,13 +29,14 @@ _CACHE = {}
 def _case(name):
     if name in _CACHE:
         return _CACHE[name]
-    if name == "2x3":
-        rng = np.random.default_rng(61)
-        bonds, _ = H.square_lattice(2, 3)
-        t = np.zeros((6, 6))
+    if name in ("2x3", "2x2"):
+        ny = 3 if name == "2x3" else 2
+        rng = np.random.default_rng(61 if ny == 3 else 64)
+        bonds, _ = H.square_lattice(2, ny)
+        t = np.zeros((2 * ny, 2 * ny))
         for (i, j) in bonds:
             t[i, j] = t[j, i] = 1.0 + 0.1 * rng.standard_normal()
-        prob = Problem(2, 3, t=t, U=np.full(6, 8.0), V=None, layers=3, classes=("U", "h1", "v1", "h2", "v2"))
+        prob = Problem(2, ny, t=t, U=np.full(2 * ny, 8.0), V=None, layers=3, classes=("U", "h1", "v1", "h2", "v2"))
         _, ref = O.lanczos_ground(prob.Hmat())
         thetas = rng.uniform(-1, 1, (2, prob.P))
     else:
@@ -100,9 +101,11 @@ def test_overlap_loss_and_gradient_against_oracle(dtype, case, fused):
         assert np.max(np.abs(F2.cpu().numpy() - Fv)) < TOL[dtype]
 
 
-@pytest.mark.parametrize("case", ["2x3", "3x4"])
+@pytest.mark.parametrize("case", ["2x2", "2x3", "3x4"])
 @pytest.mark.parametrize("dtype", [H.C64, H.C128])
 def test_spin_correlation_against_oracle(dtype, case):
+    """C_ij against the oracle: 8 qubits (runs of 2^8 amplitudes per
+    thread), 12 and 24 qubits (runs of 2^10 per warp)."""
     prob, thetas, refs, _ = _case(case)
     a = prob.ans
     L, n = prob.L, prob.n
