@@ -643,20 +643,29 @@ def run_f3_leg(H, torch, dev, steps=3):
     f = torch.empty(1, dtype=torch.float64, device=dev)
     g = torch.empty((1, a.P), dtype=torch.float64, device=dev)
     C = torch.empty((1, n // 2, n // 2), dtype=torch.float64, device=dev)
-    a.overlap_grad(th, ref, psi, lam, F, f, g, dtype=H.C64)   # warm-up (plans)
+    def time_overlap(sweeps):
+        a.state_prepare(H.PREP_SLATER, w.orbital_perturbation(), None, None, H.C64, 1)
+        a.overlap_grad(th, ref, psi, lam, F, f, g, dtype=H.C64, sweeps=sweeps)   # warm-up (plans)
+        torch.cuda.synchronize()
+        H.profile(a, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            a.overlap_grad(th, ref, psi, lam, F, f, g, dtype=H.C64, sweeps=sweeps)
+        e1.record()
+        torch.cuda.synchronize()
+        recs = H.profile_read(a)
+        H.profile(a, False)
+        ms = e0.elapsed_time(e1) / steps
+        by = sum(r[2] for r in recs) / steps
+        return {"evals_per_s": round(1e3 / ms, 3), "ms_per_step": round(ms, 3), "hbm_bytes_per_eval": by,
+                "hbm_tbs": round(by / (ms / 1e3) / 1e12, 3), "F": float(F[0].item()), "f": float(f[0].item())}
+
+    rows = time_overlap(False)
+    sweeps = time_overlap(True)
     a.spin_correlation(ref, C, dtype=H.C64)
     torch.cuda.synchronize()
-    H.profile(a, True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        a.overlap_grad(th, ref, psi, lam, F, f, g, dtype=H.C64)
-    e1.record()
-    torch.cuda.synchronize()
-    recs = H.profile_read(a)
-    H.profile(a, False)
-    ms = e0.elapsed_time(e1) / steps
-    by = sum(r[2] for r in recs) / steps
     e0.record()
     for _ in range(steps):
         a.spin_correlation(ref, C, dtype=H.C64)
@@ -664,10 +673,7 @@ def run_f3_leg(H, torch, dev, steps=3):
     torch.cuda.synchronize()
     ms_c = e0.elapsed_time(e1) / steps
     out = {"workload": WORKLOAD_TEXT[4],
-           "engine": "sweeps",
-           "overlap_grad": {"evals_per_s": round(1e3 / ms, 3), "ms_per_step": round(ms, 3),
-                            "sweep_bytes_per_eval": by, "hbm_tbs": round(by / (ms / 1e3) / 1e12, 3),
-                            "F": float(F[0].item()), "f": float(f[0].item())},
+           "overlap_grad": {"rows": rows, "sweeps": sweeps},
            "spin_correlation": {"ms_per_state": round(ms_c, 3),
                                 "hbm_tbs": round((1 << n) * 8 / (ms_c / 1e3) / 1e12, 3)}}
     del ref, psi, lam

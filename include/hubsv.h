@@ -268,11 +268,13 @@ HUB_API hub_status hub_apply_h(ans_t ans, const void* psi, void* lam, int32_t dt
  * p of 2 Im <lam_g|G_g|psi_g>, df/dtheta = -dF/dtheta / ((1 - F) ln 10).
  * psi_ref: device [ref_batch][2^n] amplitudes of the call's dtype,
  * normalised (ref_batch = 1: one reference for every batch element, or
- * batch).  psi: as energy() (initial state unless HUB_FLAG_PREP_FUSED, the
- * only flag accepted; clobbered).  lam: device workspace of psi's size, or
- * NULL when grad is NULL.  F, f: device double [batch] or NULL; grad: device
- * double [batch][P] or NULL.  Runs as dense sweeps (the paper optimises the
- * overlap on lattices of up to 24 qubits).  f is -inf when F = 1.          */
+ * batch).  psi: as energy() (initial state unless HUB_FLAG_PREP_FUSED;
+ * clobbered).  lam: device workspace of psi's size, or NULL when grad is
+ * NULL.  F, f: device double [batch] or NULL; grad: device double [batch][P]
+ * or NULL.  With HUB_FLAG_PREP_FUSED and factors that conserve N_up and
+ * N_dn, the passes run on the row engine (the overlap and lam_K formed on
+ * the sector amplitudes, psi_ref read at the sector's indices only); else,
+ * or with HUB_FLAG_SWEEPS, as dense sweeps.  f is -inf when F = 1.         */
 HUB_API hub_status overlap_grad(ans_t ans, const double* theta, const void* psi_ref,
                                 int64_t ref_batch, void* psi, void* lam, double* F,
                                 double* f, double* grad, int32_t dtype, int64_t batch,

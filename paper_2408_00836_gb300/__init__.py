@@ -309,10 +309,11 @@ class Ansatz:
         return lam
 
     def overlap_grad(self, theta, psi_ref, psi, lam=None, F=None, f=None, grad=None, dtype=C64,
-                     batch: int = 1, fused: bool = True, stream=None):
+                     batch: int = 1, fused: bool = True, sweeps: bool = False, stream=None):
         """Fidelity F = |<psi_ref|psi(theta)>|^2, the overlap loss of Eq. 5
         f = log10(1 - F) and (grad given) df/dtheta; psi_ref holds one
-        reference or one per batch element."""
+        reference or one per batch element.  sweeps: the dense sweeps even
+        where the row engine applies."""
         nb = batch * self.amp_bytes(dtype)
         ref_batch = psi_ref.numel() * psi_ref.element_size() // self.amp_bytes(dtype)
         if ref_batch not in (1, batch):
@@ -321,7 +322,8 @@ class Ansatz:
                                  _ptr(psi_ref, ref_batch * self.amp_bytes(dtype), "psi_ref"), ref_batch,
                                  _ptr(psi, nb, "psi"), _ptr(lam, nb, "lam"), _ptr(F, 8 * batch, "F"),
                                  _ptr(f, 8 * batch, "f"), _ptr(grad, 8 * batch * self.P, "grad"), dtype, batch,
-                                 FLAG_PREP_FUSED if fused else 0, _stream(stream)))
+                                 (FLAG_PREP_FUSED if fused else 0) | (FLAG_SWEEPS if sweeps else 0),
+                                 _stream(stream)))
         return F, f, grad
 
     def spin_correlation(self, psi, C, dtype=C64, batch: int = 1, stream=None):

@@ -942,8 +942,18 @@ RowPlan* row_plan_for(hub_ansatz* a, int which, int dtype, uint32_t flags, Small
   return rp;
 }
 
+// Where the sector matrices are between row-engine calls of one evaluation
+// (the overlap loss runs a forward and a backward plan): the region of
+// psi / lam that holds them, their orientation (-1: none yet), and whether
+// lam holds data.
+struct RowRun {
+  int cur = 0, orient = -1;
+  bool lam_live = false;
+};
+
 hub_status run_rows(hub_ansatz* a, SmallPlan* sp, RowPlan* rp, int dtype, const double* theta, void* psi,
-                    void* lam, int64_t batch, double* E, double* grad, uint32_t flags, cudaStream_t st) {
+                    void* lam, int64_t batch, double* E, double* grad, uint32_t flags, cudaStream_t st,
+                    RowRun* state = nullptr, bool finalize = true) {
   const bool force_cluster = (flags & HUB_FLAG_ROW_CLUSTER) != 0;
   const int n_slots = a->P + 2;
   hub_status s;
@@ -978,8 +988,9 @@ hub_status run_rows(hub_ansatz* a, SmallPlan* sp, RowPlan* rp, int dtype, const 
   const size_t mat = (size_t)batch * (size_t)sp->cup * (size_t)sp->cdn;   // amplitudes
   unsigned char* preg[2] = {(unsigned char*)psi, (unsigned char*)psi + mat * r2};
   unsigned char* lreg[2] = {(unsigned char*)lam, lam ? (unsigned char*)lam + mat * r2 : nullptr};
-  int cur = 0, orient = rp->segs.empty() ? 0 : rp->segs[0].orient;
-  bool lam_live = false;
+  int cur = state ? state->cur : 0;
+  int orient = (state && state->orient >= 0) ? state->orient : (rp->segs.empty() ? 0 : rp->segs[0].orient);
+  bool lam_live = state ? state->lam_live : false;
   const int sms = device_sm_count();
   if (sms <= 0) return fail(HUB_ECUDA, "no CUDA device");
   auto record = [&](hub_ansatz::ProfRec& rec, bool start) -> cudaError_t {
@@ -1076,7 +1087,13 @@ hub_status run_rows(hub_ansatz* a, SmallPlan* sp, RowPlan* rp, int dtype, const 
     HUB_CUDA(record(rec, false), "cudaEventRecord");
     lam_live = lam_live || (has_lam && (g.flags & RS_WRITE_LAM));
   }
-  HUB_CUDA(launch_finalize((const double*)a->d_acc.p, n_slots, a->P, a->P, E, grad, batch, st), "finalize kernel");
+  if (state) {
+    state->cur = cur;
+    state->orient = orient;
+    state->lam_live = lam_live;
+  }
+  if (finalize)
+    HUB_CUDA(launch_finalize((const double*)a->d_acc.p, n_slots, a->P, a->P, E, grad, batch, st), "finalize kernel");
   return HUB_OK;
 }
 
@@ -1254,11 +1271,51 @@ extern "C" hub_status overlap_grad(ans_t a, const double* theta, const void* psi
   if (lam && (lam == psi || lam == psi_ref)) return fail(HUB_EINVAL, "overlap_grad: lam must be a separate buffer");
   if (psi == psi_ref) return fail(HUB_EINVAL, "overlap_grad: psi and psi_ref must be distinct");
   if (ref_batch != 1 && ref_batch != batch) return fail(HUB_EINVAL, "overlap_grad: ref_batch must be 1 or batch");
-  if (flags & ~(uint32_t)HUB_FLAG_PREP_FUSED) return fail(HUB_EINVAL, "overlap_grad: unknown flags");
+  if (flags & ~(uint32_t)(HUB_FLAG_PREP_FUSED | HUB_FLAG_SWEEPS))
+    return fail(HUB_EINVAL, "overlap_grad: unknown flags");
   const bool fused = (flags & HUB_FLAG_PREP_FUSED) != 0;
   if (fused && a->prep_kind < 0)
     return fail(HUB_EINVAL, "overlap_grad: HUB_FLAG_PREP_FUSED needs a prior state_prepare");
   cudaStream_t st = (cudaStream_t)stream;
+  // the row engine, where both passes have a row plan (a prepared state,
+  // N_up and N_dn conserved): the forward pass leaves the sector matrices
+  // of psi_K in psi, the overlap and lam_K = a psi_ref are formed on them,
+  // and the backward pass starts from there
+  if (fused && !(flags & HUB_FLAG_SWEEPS)) {
+    SmallPlan *spf = nullptr, *spb = nullptr;
+    RowPlan* rpf = row_plan_for(a, 4, dtype, HUB_FLAG_PREP_FUSED, spf);
+    RowPlan* rpb = (rpf && grad) ? row_plan_for(a, 5, dtype, HUB_FLAG_PREP_FUSED, spb) : nullptr;
+    if (rpf && (!grad || rpb)) {
+      RowRun rr;
+      if ((s = run_rows(a, spf, rpf, dtype, theta, psi, nullptr, batch, nullptr, nullptr, 0u, st, &rr, false)) !=
+          HUB_OK)
+        return s;
+      if ((s = a->d_ovl.ensure(16 * (size_t)batch, "overlaps")) != HUB_OK) return s;
+      double* ov = (double*)a->d_ovl.p;
+      HUB_CUDA(launch_zero(ov, 2 * batch, st), "zero overlaps");
+      const size_t r2 = dtype == HUB_C64 ? 8 : 16;
+      const size_t off = (size_t)rr.cur * (size_t)batch * (size_t)spf->cup * (size_t)spf->cdn * r2;
+      const uint32_t* xrow = (const uint32_t*)(rr.orient == 0 ? spf->d_xdn.p : spf->d_xup.p);
+      const uint32_t* xin = (const uint32_t*)(rr.orient == 0 ? spf->d_xup.p : spf->d_xdn.p);
+      const int n_rows = rr.orient == 0 ? spf->cdn : spf->cup, row_len = rr.orient == 0 ? spf->cup : spf->cdn;
+      HUB_CUDA(launch_sector_overlap(dtype, (const unsigned char*)psi + off, xrow, xin, n_rows, row_len, psi_ref,
+                                     ref_batch, a->n, batch, ov, st),
+               "sector overlap kernel");
+      const double* acc = nullptr;
+      if (grad) {
+        HUB_CUDA(launch_sector_scale_ref(dtype, psi_ref, ref_batch, xrow, xin, n_rows, row_len, a->n, batch, ov,
+                                         (unsigned char*)lam + off, st),
+                 "sector reference scaling kernel");
+        rr.lam_live = true;
+        if ((s = run_rows(a, spb, rpb, dtype, theta, psi, lam, batch, nullptr, nullptr, 0u, st, &rr, false)) !=
+            HUB_OK)
+          return s;
+        acc = (const double*)a->d_acc.p;
+      }
+      HUB_CUDA(launch_overlap_finalize(acc, a->P + 2, a->P, ov, F, f, grad, batch, st), "overlap finalize kernel");
+      return HUB_OK;
+    }
+  }
   // forward circuit, psi_K kept in psi
   Plan* pf;
   if ((s = get_plan(a, 4, dtype, (fused ? HUB_FLAG_PREP_FUSED : 0u) | HUB_FLAG_KEEP_STATE, pf)) != HUB_OK) return s;

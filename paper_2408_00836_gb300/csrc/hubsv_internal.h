@@ -289,6 +289,14 @@ cudaError_t launch_overlap(int dtype, const void* psi, const void* ref, int64_t 
                            double* a, cudaStream_t st);
 cudaError_t launch_scale_ref(int dtype, const void* ref, int64_t ref_batch, void* lam, int n, int64_t batch,
                              const double* a, cudaStream_t st);
+// The overlap and lam_K = a psi_ref on the row engine's sector matrices
+// (element (r, c) has the full index xrow[r] | xin[c]).
+cudaError_t launch_sector_overlap(int dtype, const void* mat, const uint32_t* xrow, const uint32_t* xin, int n_rows,
+                                  int row_len, const void* ref, int64_t ref_batch, int n, int64_t batch, double* a,
+                                  cudaStream_t st);
+cudaError_t launch_sector_scale_ref(int dtype, const void* ref, int64_t ref_batch, const uint32_t* xrow,
+                                    const uint32_t* xin, int n_rows, int row_len, int n, int64_t batch,
+                                    const double* a, void* lam, cudaStream_t st);
 cudaError_t launch_overlap_finalize(const double* acc, int n_slots, int P, const double* a, double* F, double* f,
                                     double* grad, int64_t batch, cudaStream_t st);
 cudaError_t launch_occ_corr(int dtype, const void* psi, int n, int64_t batch, double* M, cudaStream_t st);

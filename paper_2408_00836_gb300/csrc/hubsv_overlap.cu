@@ -108,6 +108,70 @@ __global__ void overlap_finalize_kernel(const double* __restrict__ acc, int n_sl
   }
 }
 
+// The overlap on the row engine's sector matrices: mat[b][r][c] is the
+// amplitude of the full index x = xrow[r] | xin[c] (rows and columns in
+// either orientation).  a[b] += sum conj(ref[b % ref_batch][x]) mat[b][r][c]
+// (blocks along the elements, batch along y; the reference is read at the
+// sector's indices only), and lam[b][r][c] = a_b ref[b % ref_batch][x].
+template <typename R>
+__global__ void __launch_bounds__(256) sector_overlap_kernel(const typename OT<R>::T2* __restrict__ mat,
+                                                             const uint32_t* __restrict__ xrow,
+                                                             const uint32_t* __restrict__ xin, int n_rows,
+                                                             int row_len, const typename OT<R>::T2* __restrict__ ref,
+                                                             int64_t ref_batch, int n, int64_t batch,
+                                                             double* __restrict__ a) {
+  __shared__ double sre[8], sim[8];
+  const uint64_t C = (uint64_t)n_rows * (uint64_t)row_len;
+  for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+    const typename OT<R>::T2* p = mat + (uint64_t)b * C;
+    const typename OT<R>::T2* r = ref + ((uint64_t)(b % ref_batch) << n);
+    double re = 0.0, im = 0.0;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < C; e += (uint64_t)gridDim.x * blockDim.x) {
+      const uint64_t row = e / (uint64_t)row_len;
+      const uint32_t x = __ldg(xrow + row) | __ldg(xin + (e - row * (uint64_t)row_len));
+      const typename OT<R>::T2 u = p[e], w = r[x];
+      re += (double)(w.x * u.x + w.y * u.y);
+      im += (double)(w.x * u.y - w.y * u.x);
+    }
+    re = warp_sum_d(re);
+    im = warp_sum_d(im);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sre[wid] = re; sim[wid] = im; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tr = 0.0, ti = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tr += sre[w]; ti += sim[w]; }
+      atomicAdd(&a[2 * b], tr);
+      atomicAdd(&a[2 * b + 1], ti);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) sector_scale_ref_kernel(const typename OT<R>::T2* __restrict__ ref,
+                                                               int64_t ref_batch, const uint32_t* __restrict__ xrow,
+                                                               const uint32_t* __restrict__ xin, int n_rows,
+                                                               int row_len, int n, int64_t batch,
+                                                               const double* __restrict__ a,
+                                                               typename OT<R>::T2* __restrict__ lam) {
+  const uint64_t C = (uint64_t)n_rows * (uint64_t)row_len;
+  for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+    const typename OT<R>::T2* r = ref + ((uint64_t)(b % ref_batch) << n);
+    const R ar = (R)a[2 * b], ai = (R)a[2 * b + 1];
+    typename OT<R>::T2* l = lam + (uint64_t)b * C;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < C; e += (uint64_t)gridDim.x * blockDim.x) {
+      const uint64_t row = e / (uint64_t)row_len;
+      const uint32_t x = __ldg(xrow + row) | __ldg(xin + (e - row * (uint64_t)row_len));
+      const typename OT<R>::T2 w = r[x];
+      typename OT<R>::T2 v;
+      v.x = ar * w.x - ai * w.y;
+      v.y = ar * w.y + ai * w.x;
+      l[e] = v;
+    }
+  }
+}
+
 // M[b][k][l] (k <= l) += sum_x |psi[b][x]|^2 n_k(x) n_l(x).  Runs of 2^KR
 // amplitudes share their high bits h; per run the thread keeps s = sum p,
 // m_j = sum p bit_j and q_jk = sum p bit_j bit_k over the KR low bits in
@@ -350,6 +414,32 @@ cudaError_t launch_overlap_finalize(const double* acc, int n_slots, int P, const
   const int64_t total = batch * (P + 1);
   const int grid = (int)std::min<int64_t>((total + 255) / 256, 1024);
   overlap_finalize_kernel<<<grid, 256, 0, st>>>(acc, n_slots, P, a, F, f, grad, batch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sector_overlap(int dtype, const void* mat, const uint32_t* xrow, const uint32_t* xin, int n_rows,
+                                  int row_len, const void* ref, int64_t ref_batch, int n, int64_t batch, double* a,
+                                  cudaStream_t st) {
+  const dim3 g = vec_grid((uint64_t)n_rows * (uint64_t)row_len, batch);
+  if (dtype == 0)
+    sector_overlap_kernel<float><<<g, 256, 0, st>>>((const float2*)mat, xrow, xin, n_rows, row_len,
+                                                    (const float2*)ref, ref_batch, n, batch, a);
+  else
+    sector_overlap_kernel<double><<<g, 256, 0, st>>>((const double2*)mat, xrow, xin, n_rows, row_len,
+                                                     (const double2*)ref, ref_batch, n, batch, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sector_scale_ref(int dtype, const void* ref, int64_t ref_batch, const uint32_t* xrow,
+                                    const uint32_t* xin, int n_rows, int row_len, int n, int64_t batch,
+                                    const double* a, void* lam, cudaStream_t st) {
+  const dim3 g = vec_grid((uint64_t)n_rows * (uint64_t)row_len, batch);
+  if (dtype == 0)
+    sector_scale_ref_kernel<float><<<g, 256, 0, st>>>((const float2*)ref, ref_batch, xrow, xin, n_rows, row_len, n,
+                                                      batch, a, (float2*)lam);
+  else
+    sector_scale_ref_kernel<double><<<g, 256, 0, st>>>((const double2*)ref, ref_batch, xrow, xin, n_rows, row_len,
+                                                       n, batch, a, (double2*)lam);
   return cudaGetLastError();
 }
 

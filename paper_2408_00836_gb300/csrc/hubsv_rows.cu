@@ -57,7 +57,10 @@ hub_status make_row_plan(const hub_ansatz* a, int which, const SmallPlan* sp, Ro
   for (const RowSched& rs : sched)
     if (rs.orient < 0) return fail(HUB_EUNSUPPORTED, "row engine: no schedule");
   RowPlan* rp = new RowPlan();
-  bool lam_live = false;
+  // call kind 5 (the backward pass of the overlap loss) starts from psi and
+  // lam in the caller's buffers; kind 4 (the forward pass alone) leaves
+  // psi_K there
+  bool lam_live = which == 5;
   for (const RowSched& rs : sched) {
     RowSegHost g;
     g.op_begin = (int)rp->ops.size();
@@ -92,7 +95,7 @@ hub_status make_row_plan(const hub_ansatz* a, int which, const SmallPlan* sp, Ro
     }
     g.op_end = (int)rp->ops.size();
     uint32_t f = 0;
-    if (rp->segs.empty()) f |= RS_PREP | RS_WRITE_PSI;
+    if (rp->segs.empty() && which != 5) f |= RS_PREP | RS_WRITE_PSI;
     if (mod_psi) f |= RS_WRITE_PSI;
     if (lam_live || makes_lam) f |= RS_HAS_LAM;
     if (lam_live) f |= RS_READ_LAM;
@@ -108,7 +111,7 @@ hub_status make_row_plan(const hub_ansatz* a, int which, const SmallPlan* sp, Ro
     rp->segs.push_back(g);
   }
   if (rp->ops.empty()) rp->ops.push_back(SmallOpDev{});
-  rp->segs.back().flags &= ~(uint32_t)(RS_WRITE_PSI | RS_WRITE_LAM);   // nothing reads them
+  if (which != 4) rp->segs.back().flags &= ~(uint32_t)(RS_WRITE_PSI | RS_WRITE_LAM);   // nothing reads them
   out = rp;
   return HUB_OK;
 }

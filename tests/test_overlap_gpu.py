@@ -54,11 +54,15 @@ def _case(name):
     return _CACHE[name]
 
 
-@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("fused,engine", [(True, "rows"), (True, "sweeps"), (False, "sweeps")])
 @pytest.mark.parametrize("case", ["2x3", "3x4"])
 @pytest.mark.parametrize("dtype", [H.C64, H.C128])
-def test_overlap_loss_and_gradient_against_oracle(dtype, case, fused):
+def test_overlap_loss_and_gradient_against_oracle(dtype, case, fused, engine):
+    """F, f and df/dtheta against the oracle, on the row engine (a prepared
+    state: the overlap and lam_K formed on the sector amplitudes) and on the
+    dense sweeps (also from a caller-given state)."""
     prob, thetas, refs, oracle = _case(case)
+    sweeps = engine == "sweeps"
     a = prob.ans
     batch = 2
     n = prob.n
@@ -80,12 +84,12 @@ def test_overlap_loss_and_gradient_against_oracle(dtype, case, fused):
         F = torch.empty(batch, dtype=torch.float64, device="cuda")
         f = torch.empty_like(F)
         g = torch.empty((batch, a.P), dtype=torch.float64, device="cuda")
-        a.overlap_grad(th, ref, psi, lam, F, f, g, dtype=dtype, batch=batch, fused=fused)
+        a.overlap_grad(th, ref, psi, lam, F, f, g, dtype=dtype, batch=batch, fused=fused, sweeps=sweeps)
         H.sync()
         Fv, fv, gv = F.cpu().numpy(), f.cpu().numpy(), g.cpu().numpy()
         for b in range(batch):
             Fo, fo, go = exp[b]
-            log_errors(f"overlap_{case}_{mode}", dtype, "sweeps", F=abs(Fv[b] - Fo), f=abs(fv[b] - fo) / max(1, abs(fo)),
+            log_errors(f"overlap_{case}_{mode}", dtype, engine, F=abs(Fv[b] - Fo), f=abs(fv[b] - fo) / max(1, abs(fo)),
                        grad=grad_err(gv[b], go))
             assert abs(Fv[b] - Fo) < TOL[dtype], (b, Fv[b], Fo)
             assert abs(fv[b] - fo) < TOL[dtype] * max(1.0, abs(fo))
@@ -96,7 +100,7 @@ def test_overlap_loss_and_gradient_against_oracle(dtype, case, fused):
         else:
             a.state_prepare(H.PREP_SLATER, None, None, psi, dtype, batch)
         F2 = torch.empty(batch, dtype=torch.float64, device="cuda")
-        a.overlap_grad(th, ref, psi, None, F2, None, None, dtype=dtype, batch=batch, fused=fused)
+        a.overlap_grad(th, ref, psi, None, F2, None, None, dtype=dtype, batch=batch, fused=fused, sweeps=sweeps)
         H.sync()
         assert np.max(np.abs(F2.cpu().numpy() - Fv)) < TOL[dtype]
 
