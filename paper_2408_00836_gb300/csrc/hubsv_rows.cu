@@ -242,7 +242,9 @@ __device__ __forceinline__ R row_hop(T2* __restrict__ prow, T2* __restrict__ lro
 // reach the other's row through distributed shared memory, with a cluster
 // barrier wherever one CTA would synchronise.
 template <typename R, int NT, int RR, int CL>
-__global__ void __launch_bounds__(NT, CL == 2 ? 1 : (NT == kRowThreadsSmall ? 4 : (NT == kRowThreadsLarge ? 2 : 1)))
+__global__ void __launch_bounds__(NT, CL == 2 ? 1
+                                            : (NT == kRowThreadsSmall ? 4
+                                                                      : (NT == kRowThreadsLarge ? (sizeof(R) == 8 ? 1 : 2) : 1)))
     rows_kernel(const RowArgs a) {
   constexpr int kRowWarps = NT / 32;
   using T2 = typename CT<R>::T2;
