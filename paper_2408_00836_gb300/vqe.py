@@ -94,10 +94,28 @@ class VQEResult:
     seconds: float = 0.0
 
 
-def lbfgs(fun, x0, max_iter=1000, m=10, e_tol=1e-7, g_tol=1e-6, c1=1e-4, max_ls=30):
+def save_state(path, state: dict):
+    """Writes an L-BFGS iteration state (from lbfgs_steps' on_iter) to an
+    .npz file: the point, its value and gradient, the curvature pairs, the
+    value history and the iteration count."""
+    P = len(state["x"])
+    np.savez(path, x=state["x"], f=state["f"], g=state["g"], it=state["it"],
+             S=np.array(state["S"]).reshape(-1, P), Y=np.array(state["Y"]).reshape(-1, P),
+             hist=np.array(state["hist"]))
+
+
+def load_state(path) -> dict:
+    """The state save_state wrote, for lbfgs_steps(..., resume=state)."""
+    z = np.load(path)
+    return {"x": z["x"], "f": float(z["f"]), "g": z["g"], "it": int(z["it"]), "S": list(z["S"]),
+            "Y": list(z["Y"]), "hist": list(z["hist"])}
+
+
+def lbfgs(fun, x0, max_iter=1000, m=10, e_tol=1e-7, g_tol=1e-6, c1=1e-4, max_ls=30, resume=None, on_iter=None):
     """Minimise fun(x) -> (f, grad) by L-BFGS (two-loop recursion) with a
-    backtracking line search (Armijo condition); stops as in Sec. 2.1."""
-    gen = lbfgs_steps(x0, max_iter, m, e_tol, g_tol, c1, max_ls)
+    backtracking line search (Armijo condition); stops as in Sec. 2.1.
+    resume / on_iter: as lbfgs_steps."""
+    gen = lbfgs_steps(x0, max_iter, m, e_tol, g_tol, c1, max_ls, resume=resume, on_iter=on_iter)
     x = next(gen)
     try:
         while True:
@@ -106,17 +124,28 @@ def lbfgs(fun, x0, max_iter=1000, m=10, e_tol=1e-7, g_tol=1e-6, c1=1e-4, max_ls=
         return stop.value
 
 
-def lbfgs_steps(x0, max_iter=1000, m=10, e_tol=1e-7, g_tol=1e-6, c1=1e-4, max_ls=30):
+def lbfgs_steps(x0, max_iter=1000, m=10, e_tol=1e-7, g_tol=1e-6, c1=1e-4, max_ls=30, resume=None,
+                on_iter=None):
     """L-BFGS as a generator: yields each point it needs evaluated, receives
     (f, grad) there, and returns (x, f, g, iterations, reason, history).
     Several of these run side by side in multistart(), whose every round is
-    one batched evaluation of all their requested points."""
-    x = np.array(x0, dtype=np.float64)
-    f, g = yield x
-    S, Y, hist = [], [], [f]
+    one batched evaluation of all their requested points.  on_iter(state)
+    is called after every accepted step with the iteration state (x, f, g,
+    curvature pairs S and Y, history, iteration count); resume=state
+    continues from such a state (save_state / load_state), taking the same
+    steps the uninterrupted run would."""
+    if resume is None:
+        x = np.array(x0, dtype=np.float64)
+        f, g = yield x
+        S, Y, hist = [], [], [f]
+        it0 = 0
+    else:
+        x, f, g = np.array(resume["x"], dtype=np.float64), float(resume["f"]), np.array(resume["g"])
+        S, Y, hist = [np.array(v) for v in resume["S"]], [np.array(v) for v in resume["Y"]], list(resume["hist"])
+        it0 = int(resume["it"])
     reason = "max_iter"
-    it = 0
-    for it in range(1, max_iter + 1):
+    it = it0
+    for it in range(it0 + 1, max_iter + 1):
         if np.max(np.abs(g)) < g_tol:
             reason = "gradient"
             it -= 1
@@ -155,6 +184,8 @@ def lbfgs_steps(x0, max_iter=1000, m=10, e_tol=1e-7, g_tol=1e-6, c1=1e-4, max_ls
         df = abs(fn - f)
         x, f, g = xn, fn, gn
         hist.append(f)
+        if on_iter is not None:
+            on_iter({"x": x, "f": f, "g": g, "S": list(S), "Y": list(Y), "hist": list(hist), "it": it})
         if df < e_tol:
             reason = "energy"
             break
@@ -255,9 +286,11 @@ def run_overlap_vqe(ans: Ansatz, psi_ref, starts, dtype: int = C64, max_iter: in
 
 
 def run_vqe(ans: Ansatz, theta0, dtype: int = C64, max_iter: int = 200, ckpt: bool = False,
-            use_graph: bool = True) -> VQEResult:
+            use_graph: bool = True, checkpoint_path=None, resume_path=None) -> VQEResult:
     """Energy-based VQE (Sec. 2.1) for one parameter set (batch 1): the
-    ansatz's initial state must have been set with state_prepare."""
+    ansatz's initial state must have been set with state_prepare.
+    checkpoint_path: the optimiser state is written there after every step;
+    resume_path: continue a run from such a file."""
     fn = EnergyGradGraph(ans, dtype=dtype, batch=1, ckpt=ckpt, use_graph=use_graph)
 
     def fun(x):
@@ -265,7 +298,9 @@ def run_vqe(ans: Ansatz, theta0, dtype: int = C64, max_iter: int = 200, ckpt: bo
         return float(E[0]), g[0]
 
     t0 = time.perf_counter()
-    x, f, g, it, reason, hist = lbfgs(fun, theta0, max_iter=max_iter)
+    resume = load_state(resume_path) if resume_path else None
+    on_iter = (lambda st: save_state(checkpoint_path, st)) if checkpoint_path else None
+    x, f, g, it, reason, hist = lbfgs(fun, theta0, max_iter=max_iter, resume=resume, on_iter=on_iter)
     sec = time.perf_counter() - t0
     return VQEResult(x, f, float(np.max(np.abs(g))), it, fn.evals, reason, hist, sec)
 
@@ -286,6 +321,9 @@ def _main():
     ap.add_argument("--workload", type=int, default=4)
     ap.add_argument("--iters", type=int, default=200)
     ap.add_argument("--dtypes", default="c64,c128")
+    ap.add_argument("--checkpoint", default=None,
+                    help="write the optimiser state to <path>.<dtype>.npz after every step")
+    ap.add_argument("--resume", default=None, help="continue from <path>.<dtype>.npz written by --checkpoint")
     args = ap.parse_args()
     torch.cuda.init()
     w = W.workload(args.workload, batch_sets=1)
@@ -298,7 +336,9 @@ def _main():
     for name in args.dtypes.split(","):
         dt = C64 if name == "c64" else C128
         ans.state_prepare(PREP_SLATER, w.orbital_perturbation(), None, None, dt, 1)
-        r = run_vqe(ans, theta0, dtype=dt, max_iter=args.iters)
+        r = run_vqe(ans, theta0, dtype=dt, max_iter=args.iters,
+                    checkpoint_path=f"{args.checkpoint}.{name}.npz" if args.checkpoint else None,
+                    resume_path=f"{args.resume}.{name}.npz" if args.resume else None)
         out[name] = {"energy": r.energy, "grad_max": r.grad_norm, "iterations": r.iterations,
                      "evaluations": r.evaluations, "reason": r.reason, "seconds": round(r.seconds, 2),
                      "evals_per_s": round(r.evaluations / r.seconds, 3), "E_first": r.history[0]}
