@@ -38,6 +38,9 @@ hub_status DevBuf::ensure(size_t n, const char* what) {
   cudaError_t e = cudaMalloc(&p, n);
   if (e != cudaSuccess) {
     p = nullptr;
+    // an allocation failure is not sticky: clear it so that the next call's
+    // check for earlier asynchronous errors does not report it again
+    (void)cudaGetLastError();
     return fail(HUB_ENOMEM, std::string("cudaMalloc failed for ") + what);
   }
   bytes = n;
