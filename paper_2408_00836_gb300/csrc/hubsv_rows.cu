@@ -275,7 +275,11 @@ __global__ void __launch_bounds__(NT, CL == 2 ? 1
   GT* cs = reinterpret_cast<GT*>(sops + n_ops);
   AccT* acc = reinterpret_cast<AccT*>(cs + a.n_gates);   // [kRowWarps][n_slots]
   R* hc = reinterpret_cast<R*>(acc + kRowWarps * a.n_slots);
-  const int tid = threadIdx.x, nth = blockDim.x;
+  // The launch has exactly NT threads (launch_rows checks it).  Complex64
+  // takes the loop strides as compile-time constants (immediate offsets, no
+  // stride arithmetic); complex128 keeps them in registers, which spills
+  // less in its 64-register variants.
+  const int tid = threadIdx.x, nth = sizeof(R) == 4 ? NT : (int)blockDim.x;
   const int wtid = tid + rank * nth, wnth = CL * nth;   // work split over the cluster
   const R* rtabs = reinterpret_cast<const R*>(DT == 0 ? (const void*)a.real_tabs32 : (const void*)a.real_tabs);
   const T2* ptabs = reinterpret_cast<const T2*>(a.phase_tabs);
@@ -633,6 +637,11 @@ RowLaunch rows_launch(int dtype, int nv, int row_len, int n_rows, int n_slots, i
 }
 
 cudaError_t launch_rows(int dtype, const RowArgs& a, const RowLaunch& L, int grid, cudaStream_t st) {
+  // the kernel's loops assume blockDim.x == its NT
+  const bool nt_ok = L.cl == 2 ? L.threads == kRowThreadsLarge
+                               : (L.threads == kRowThreadsSolo || L.threads == kRowThreadsSmall ||
+                                  L.threads == kRowThreadsLarge);
+  if (!nt_ok) return cudaErrorInvalidValue;
   const void* f = rows_fn(dtype, L);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
   if (e != cudaSuccess) return e;
