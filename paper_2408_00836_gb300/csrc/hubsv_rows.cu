@@ -376,8 +376,11 @@ __global__ void __launch_bounds__(NT, CL == 2 ? 1
     for (int oi = 0; oi < n_ops; ++oi) {
       const SmallOpDev op = sops[oi];
       R part = 0, npart = 0;
-      if (op.kind == OP_GIV || op.kind == OP_MEAS_HOP || op.kind == OP_LAM_HOP || op.kind == OP_GRAD_HOP ||
-          op.kind == OP_GRADINV_HOP) {
+      static_assert(OP_GIV % 2 == 0 && OP_MEAS_HOP % 2 == 0 && OP_LAM_HOP % 2 == 0 && OP_GRAD_HOP % 2 == 0 &&
+                        OP_GRADINV_HOP % 2 == 0 && OP_DIAG % 2 == 1 && OP_MEAS_DIAG % 2 == 1 &&
+                        OP_LAM_DIAG % 2 == 1 && OP_GRAD_DIAG % 2 == 1 && OP_GRADINV_DIAG % 2 == 1,
+                    "hop kinds are even, diagonal kinds odd");
+      if ((op.kind & 1) == 0) {   // hop operations
         R c = 0, s = 0, cl = 0, sl = 0, tc = 0;
         if (op.kind == OP_GIV || op.kind == OP_GRADINV_HOP) {
           const GT gq = cs[op.gate];
