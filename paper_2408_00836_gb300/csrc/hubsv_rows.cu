@@ -236,6 +236,35 @@ __device__ __forceinline__ R row_hop(T2* __restrict__ prow, T2* __restrict__ lro
   return part;
 }
 
+// Row staging: n elements from global memory into shared memory with
+// cp.async (the copies take no registers, so all of a thread's copies are
+// in flight at once; a CTA alone on its SM otherwise waits out the HBM
+// latency several times per row).  16-byte copies where both addresses are
+// 16-byte aligned (the last complex64 element of an odd count: 8 bytes),
+// else 8-byte copies (element arrays are at least 8-byte aligned).
+// Completed by stage_wait() in every thread, then a barrier.
+template <typename T2>
+__device__ __forceinline__ void stage_async(T2* dst, const T2* src, int n, int tid, int nth) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  const size_t g = __cvta_generic_to_global(src);
+  const size_t bytes = (size_t)n * sizeof(T2);   // a multiple of 8
+  if (((d | g) & 15u) == 0) {
+    const int n16 = (int)(bytes >> 4);
+    for (int i = tid; i < n16; i += nth)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16u * (uint32_t)i), "l"(g + 16 * (size_t)i)
+                   : "memory");
+    if ((bytes & 8) && tid == 0)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d + (uint32_t)(bytes - 8)), "l"(g + bytes - 8)
+                   : "memory");
+  } else {
+    const int n8 = (int)(bytes >> 3);
+    for (int i = tid; i < n8; i += nth)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d + 8u * (uint32_t)i), "l"(g + 8 * (size_t)i)
+                   : "memory");
+  }
+}
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // RR: rows staged together (1 or 2, consecutive rows of one batch
 // element): every operation runs on all of them between two barriers, so
 // its per-operation work and the pair-list loads are shared.
@@ -353,16 +382,17 @@ __global__ void __launch_bounds__(NT, CL == 2 ? 1
       } else if (a.flags & RS_PREP) {
         for (int i = tid; i < len; i += nth) pr[i] = mk<T2, R>(prep_amp<R>(a.prep, sdt, xr[r] | a.xin[i], inst), (R)0);
       } else {
-        for (int i = tid; i < len; i += nth) pr[i] = psi[base[r] + i];
+        stage_async(pr, psi + base[r], len, tid, nth);
       }
       if (has_lam) {
         if (live[r] && (a.flags & RS_READ_LAM)) {
-          for (int i = tid; i < len; i += nth) lr[i] = lam[base[r] + i];
+          stage_async(lr, lam + base[r], len, tid, nth);
         } else {
           for (int i = tid; i < len; i += nth) lr[i] = mk<T2, R>((R)0, (R)0);
         }
       }
     }
+    if constexpr (CL == 1) stage_wait();
     row_sync();
     Tot<R> eacc, nacc;
     // gradient terms of consecutive operations with one accumulator slot
