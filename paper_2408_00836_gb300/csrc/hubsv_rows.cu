@@ -367,9 +367,9 @@ __global__ void __launch_bounds__(NT, CL == 2 ? 1
     for (int r = 0; r < RR; ++r) {
       if constexpr (CL == 2) {   // rank 0 stages the psi row, rank 1 the lam row
         if (rank == 0) {
-          for (int i = tid; i < len; i += nth) mine[i] = psi[base[r] + i];
+          stage_async(mine, psi + base[r], len, tid, nth);
         } else if (a.flags & RS_READ_LAM) {
-          for (int i = tid; i < len; i += nth) mine[i] = lam[base[r] + i];
+          stage_async(mine, lam + base[r], len, tid, nth);
         } else {
           for (int i = tid; i < len; i += nth) mine[i] = mk<T2, R>((R)0, (R)0);
         }
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(NT, CL == 2 ? 1
         }
       }
     }
-    if constexpr (CL == 1) stage_wait();
+    stage_wait();
     row_sync();
     Tot<R> eacc, nacc;
     // gradient terms of consecutive operations with one accumulator slot
