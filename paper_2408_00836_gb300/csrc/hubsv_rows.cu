@@ -381,12 +381,15 @@ __global__ void __launch_bounds__(NT, CL == 2 ? 1
         for (int i = tid; i < len; i += nth) pr[i] = mk<T2, R>((R)0, (R)0);
       } else if (a.flags & RS_PREP) {
         for (int i = tid; i < len; i += nth) pr[i] = mk<T2, R>(prep_amp<R>(a.prep, sdt, xr[r] | a.xin[i], inst), (R)0);
-      } else {
+      } else if constexpr (sizeof(R) == 4) {
         stage_async(pr, psi + base[r], len, tid, nth);
+      } else {   // (complex128 CTAs share their SM with others: plain loads, fewer spills)
+        for (int i = tid; i < len; i += nth) pr[i] = psi[base[r] + i];
       }
       if (has_lam) {
         if (live[r] && (a.flags & RS_READ_LAM)) {
-          stage_async(lr, lam + base[r], len, tid, nth);
+          if constexpr (sizeof(R) == 4) stage_async(lr, lam + base[r], len, tid, nth);
+          else for (int i = tid; i < len; i += nth) lr[i] = lam[base[r] + i];
         } else {
           for (int i = tid; i < len; i += nth) lr[i] = mk<T2, R>((R)0, (R)0);
         }
