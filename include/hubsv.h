@@ -51,7 +51,10 @@
  * the device are reported by the next call or by hub_sync.  The library
  * never aborts and never prints.  Amplitudes: HUB_C64 = interleaved float
  * (re, im), HUB_C128 = interleaved double; batch b occupies amplitudes
- * [b * 2^n, (b+1) * 2^n).  theta, energies and gradients are double in both
+ * [b * 2^n, (b+1) * 2^n).  Amplitude buffers are aligned to their element
+ * size (8 bytes for HUB_C64, 16 for HUB_C128; any device allocation is);
+ * calls given one that is not return HUB_EINVAL before launching anything.
+ * theta, energies and gradients are double in both
  * precisions; reductions accumulate in double.
  */
 #ifndef HUBSV_H

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <string>
 #include <vector>
@@ -1100,11 +1101,19 @@ hub_status run_rows(hub_ansatz* a, SmallPlan* sp, RowPlan* rp, int dtype, const 
   return HUB_OK;
 }
 
-hub_status check_call(hub_ansatz* a, int32_t dtype, int64_t batch) {
+// amps: the call's amplitude buffers (NULL entries are checked by the
+// caller), each of which must be aligned to its element size (8 bytes for
+// complex64, 16 for complex128): the kernels access whole elements.
+hub_status check_call(hub_ansatz* a, int32_t dtype, int64_t batch, std::initializer_list<const void*> amps = {}) {
   if (!a) return fail(HUB_EINVAL, "NULL ansatz");
   if (dtype != HUB_C64 && dtype != HUB_C128) return fail(HUB_EINVAL, "dtype must be HUB_C64 or HUB_C128");
   if (batch < 1) return fail(HUB_EINVAL, "batch must be >= 1");
   if (a->n + 63 - __builtin_clzll((unsigned long long)batch) > 62) return fail(HUB_EINVAL, "batch too large");
+  const uintptr_t align = dtype == HUB_C64 ? 8 : 16;
+  for (const void* p : amps)
+    if (((uintptr_t)p & (align - 1)) != 0)
+      return fail(HUB_EINVAL, dtype == HUB_C64 ? "amplitude buffers must be 8-byte aligned (complex64)"
+                                               : "amplitude buffers must be 16-byte aligned (complex128)");
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "earlier asynchronous error");
   return HUB_OK;
@@ -1114,7 +1123,7 @@ hub_status check_call(hub_ansatz* a, int32_t dtype, int64_t batch) {
 
 extern "C" hub_status state_prepare(ans_t a, int32_t kind, const double* orb_perturb, const int32_t* neel_up,
                                     void* psi, int32_t dtype, int64_t batch, hub_stream_t stream) {
-  hub_status s = check_call(a, dtype, batch);
+  hub_status s = check_call(a, dtype, batch, {psi});
   if (s != HUB_OK) return s;
   const int L = a->L;
   const hub_model* m0 = a->models[0];
@@ -1192,7 +1201,7 @@ extern "C" hub_status state_prepare(ans_t a, int32_t kind, const double* orb_per
 // ---------------------------------------------------------------------------
 extern "C" hub_status energy(ans_t a, const double* theta, void* psi, double* E, int32_t dtype, int64_t batch,
                              uint32_t flags, hub_stream_t stream) {
-  hub_status s = check_call(a, dtype, batch);
+  hub_status s = check_call(a, dtype, batch, {psi});
   if (s != HUB_OK) return s;
   if (!psi || !E || (a->P > 0 && !theta)) return fail(HUB_EINVAL, "energy: NULL buffer");
   if ((flags & HUB_FLAG_PREP_FUSED) && a->prep_kind < 0)
@@ -1211,7 +1220,7 @@ extern "C" hub_status energy(ans_t a, const double* theta, void* psi, double* E,
 extern "C" hub_status energy_grad(ans_t a, const double* theta, void* psi, void* lam, void* ckpt, double* E,
                                   double* grad, int32_t dtype, int64_t batch, uint32_t flags,
                                   hub_stream_t stream) {
-  hub_status s = check_call(a, dtype, batch);
+  hub_status s = check_call(a, dtype, batch, {psi, lam, ckpt});
   if (s != HUB_OK) return s;
   if (!psi || !lam || !E || !grad || (a->P > 0 && !theta)) return fail(HUB_EINVAL, "energy_grad: NULL buffer");
   if (psi == lam) return fail(HUB_EINVAL, "energy_grad: psi and lam must be distinct");
@@ -1232,7 +1241,7 @@ extern "C" hub_status energy_grad(ans_t a, const double* theta, void* psi, void*
 
 extern "C" hub_status hub_apply_h(ans_t a, const void* psi, void* lam, int32_t dtype, int64_t batch,
                                   hub_stream_t stream) {
-  hub_status s = check_call(a, dtype, batch);
+  hub_status s = check_call(a, dtype, batch, {psi, lam});
   if (s != HUB_OK) return s;
   if (!psi || !lam || psi == lam) return fail(HUB_EINVAL, "hub_apply_h: bad buffers");
   Plan* pl;
@@ -1267,7 +1276,7 @@ extern "C" hub_status ans_workspace_bytes(ans_t a, int32_t which, int32_t dtype,
 extern "C" hub_status overlap_grad(ans_t a, const double* theta, const void* psi_ref, int64_t ref_batch,
                                    void* psi, void* lam, double* F, double* f, double* grad, int32_t dtype,
                                    int64_t batch, uint32_t flags, hub_stream_t stream) {
-  hub_status s = check_call(a, dtype, batch);
+  hub_status s = check_call(a, dtype, batch, {psi_ref, psi, lam});
   if (s != HUB_OK) return s;
   if (!psi_ref || !psi || (a->P > 0 && !theta)) return fail(HUB_EINVAL, "overlap_grad: NULL buffer");
   if (grad && !lam) return fail(HUB_EINVAL, "overlap_grad: the gradient needs lam");
@@ -1343,7 +1352,7 @@ extern "C" hub_status overlap_grad(ans_t a, const double* theta, const void* psi
 
 extern "C" hub_status spin_correlation(ans_t a, const void* psi, double* C, int32_t dtype, int64_t batch,
                                        hub_stream_t stream) {
-  hub_status s = check_call(a, dtype, batch);
+  hub_status s = check_call(a, dtype, batch, {psi});
   if (s != HUB_OK) return s;
   if (!psi || !C) return fail(HUB_EINVAL, "spin_correlation: NULL buffer");
   const int n = a->n, L = a->L;

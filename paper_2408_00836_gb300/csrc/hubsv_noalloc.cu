@@ -69,6 +69,8 @@ extern "C" hub_status energy_noalloc(ans_t a, const double* theta, void* psi, do
   if (dtype != HUB_C64 && dtype != HUB_C128) return fail(HUB_EINVAL, "energy_noalloc: bad dtype");
   if (batch < 1) return fail(HUB_EINVAL, "energy_noalloc: batch must be >= 1");
   if (!psi || !E || (a->P > 0 && !theta)) return fail(HUB_EINVAL, "energy_noalloc: NULL buffer");
+  if (((uintptr_t)psi & (dtype == HUB_C64 ? 7u : 15u)) != 0)
+    return fail(HUB_EINVAL, "energy_noalloc: psi must be aligned to its element size (8 or 16 bytes)");
   if (flags & ~(uint32_t)(HUB_FLAG_PREP_FUSED | HUB_FLAG_KEEP_STATE))
     return fail(HUB_EINVAL, "energy_noalloc: unknown flags");
   const bool fused = (flags & HUB_FLAG_PREP_FUSED) != 0;

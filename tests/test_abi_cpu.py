@@ -316,3 +316,32 @@ def test_cta_size_override_arguments():
     with pytest.raises(H.HubError) as e:
         a.set_threads(7, H.ENGINE_ROWS, 256)
     assert e.value.status == _lib.HUB_EINVAL
+
+
+def test_misaligned_amplitude_buffers_are_refused():
+    """Every call that takes amplitude buffers refuses one that is not
+    aligned to its element size (8 bytes for complex64, 16 for complex128)
+    with HUB_EINVAL, before it launches or dereferences anything (the
+    pointers below are never read; no GPU needed)."""
+    bonds, cls, t = _model()
+    m = H.Model(6, bonds, t, np.full(6, 4.0), None, 3, 3)
+    a = H.Ansatz([m], H.hva_groups(bonds, cls, 6, 1, ["U", "h1"]), 1)
+    L = _lib.lib()
+    ok = ctypes.c_void_p(1 << 20)   # stands in for the other (valid) buffers
+    for dtype, off in ((H.C64, 4), (H.C128, 8)):
+        bad = ctypes.c_void_p((1 << 20) + off)
+        calls = {
+            "state_prepare": lambda: L.state_prepare(a._h, 0, None, None, bad, dtype, 1, None),
+            "energy": lambda: L.energy(a._h, ok, bad, ok, dtype, 1, 0, None),
+            "energy_noalloc": lambda: L.energy_noalloc(a._h, ok, bad, ok, dtype, 1, 0, None),
+            "energy_grad psi": lambda: L.energy_grad(a._h, ok, bad, ok, None, ok, ok, dtype, 1, 0, None),
+            "energy_grad lam": lambda: L.energy_grad(a._h, ok, ok, bad, None, ok, ok, dtype, 1, 0, None),
+            "energy_grad ckpt": lambda: L.energy_grad(a._h, ok, ok, ok, bad, ok, ok, dtype, 1, 0, None),
+            "hub_apply_h": lambda: L.hub_apply_h(a._h, ok, bad, dtype, 1, None),
+            "overlap_grad ref": lambda: L.overlap_grad(a._h, ok, bad, 1, ok, None, ok, ok, None, dtype, 1, 0, None),
+            "overlap_grad psi": lambda: L.overlap_grad(a._h, ok, ok, 1, bad, None, ok, ok, None, dtype, 1, 0, None),
+            "spin_correlation": lambda: L.spin_correlation(a._h, bad, ok, dtype, 1, None),
+        }
+        for name, call in calls.items():
+            assert call() == _lib.HUB_EINVAL, name
+            assert b"aligned" in L.hub_last_error(), name
