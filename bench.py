@@ -94,6 +94,7 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.skip = 0
         self.path = os.path.join(tempfile.gettempdir(), f"hubsv_clocks_{os.getpid()}.csv")
 
     def start(self):
@@ -108,6 +109,19 @@ class Clocks:
                  "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # nvidia-smi takes a moment to start: wait (at most 5 s) for its first
+        # sample, and count only the samples taken after this point, so that a
+        # short timed region still gets its own samples and none from before it
+        self.skip = 0
+        t_end = time.time() + 5.0
+        while time.time() < t_end and self.proc.poll() is None:
+            with open(self.path) as f:
+                n = sum(1 for _ in f)
+            if n > 0:
+                self.skip = n
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -121,7 +135,9 @@ class Clocks:
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
-            for line in f:
+            for i, line in enumerate(f):
+                if i < self.skip:
+                    continue
                 parts = [p.strip() for p in line.split(",")]
                 if len(parts) < 9:
                     continue
@@ -717,7 +733,7 @@ def run_c128(args, w, a, H, torch, dev, theta, ms_c64, sweeps=None):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=5, choices=[2, 3, 4, 5, 6])
