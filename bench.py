@@ -767,17 +767,21 @@ def main():
         import oracle  # noqa: F401
         # measured first: full evaluations at 24 qubits, one core and all cores
         measured = oracle_measured(6, evals=5, all_cores=True)
-        ests = []
+        ests, walls = [], []
         desc = ""
         for i in range(args.warmup + args.steps):
-            est, desc, _ = oracle_sample(args.workload)
+            est, desc, wall = oracle_sample(args.workload)
             if i >= args.warmup:
                 ests.append(est)
+                walls.append(wall)
         sec = statistics.mean(ests)
         v = 1.0 / sec
         estimate = args.workload in (4, 5)
+        # a step is one bounded sample of the evaluation: ms_per_step is its
+        # wall time; value scales the sample to whole evaluations
         out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
-               "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(walls) * 1e3,
+               "ms_per_eval": sec * 1e3,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
                "data": "synthetic (seeded inputs of the named workload)",
                "config": {"workload": WORKLOAD_TEXT.get(args.workload, str(args.workload))},
