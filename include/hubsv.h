@@ -248,7 +248,8 @@ HUB_API hub_status ans_workspace_bytes(ans_t ans, int32_t which, int32_t dtype, 
  * holds until the process exits.  Arguments and results are those of
  * energy().  Problems whose tables do not fit return HUB_EINVAL with the
  * size needed.  The first call on a device looks up the array's device
- * address; later calls reuse it.  Every
+ * address (with that device current); later calls reuse it.  Make that
+ * first call on each device before any stream capture begins.  Every
  * call shares the array (it clears the accumulators it uses), so calls that
  * overlap on the GPU -- on different streams or threads -- race.  The
  * initial-state tables come from the last state_prepare call, which, being

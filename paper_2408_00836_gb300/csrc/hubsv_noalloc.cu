@@ -11,7 +11,8 @@
 //
 // The array lives in every GPU that loads the library until the process
 // exits.  Each device's address of it is looked up once, on the first call
-// made with that device current.  All calls share the array: each call
+// made with that device current; that first call belongs before any stream
+// capture begins.  All calls share the array: each call
 // rewrites the tables it uses and clears the accumulators, and two calls
 // that overlap on the GPU (different streams, or different threads) race on
 // it.
